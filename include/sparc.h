@@ -1,0 +1,199 @@
+/*
+ * sparc.h — C ABI of the GB300 CheFSI library (libsparc.so).
+ *
+ * One Chebyshev-filtered subspace iteration (CheFSI) step of real-space
+ * Kohn-Sham DFT, as in Algorithm 1 of "GPU acceleration of local and semilocal
+ * density functional calculations in the SPARC electronic structure code"
+ * (arXiv 2302.09708): Chebyshev filtering, projection, subspace
+ * diagonalisation and rotation, with the matrix-free Hamiltonian of Sec. II A
+ *
+ *   H X = -1/2 Lap X + Veff o X + sum_J chi_J Gamma_J h^3 chi_J^T X ,
+ *
+ * Lap the 12th-order (radius 6) central finite-difference Laplacian on a
+ * uniform grid (periodic or Dirichlet per axis), Veff a diagonal potential and
+ * chi_J the Kleinman-Bylander projectors of atom J on its support points.
+ *
+ * Conventions shared by every call
+ *  - Every function returns an int status (sparc_status below); no C++
+ *    exception crosses the ABI.  sparc_last_error() gives a message.
+ *  - Grid point (i, j, k) has linear index i + nx (j + ny k) (x fastest).
+ *  - An orbital block X is an Nd x Ns column-major matrix (one orbital per
+ *    column) with leading dimension ld >= Nd elements, of element type dtype
+ *    (SPARC_F64 or SPARC_F32); rows Nd..ld-1 are ignored and never written.
+ *    Blocks passed to the calls are owned by the caller.  Device pointers
+ *    (cudaMalloc, torch.empty(..., device="cuda")) run without staging; where a
+ *    call says "device or host", a host pointer is copied through a library
+ *    buffer inside the call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; calls return without waiting unless stated.
+ *  - All inputs given at create time are copied; the caller may free them.
+ *  - The library owns its workspace (two Nd x ns_max blocks of the working
+ *    precision plus the Ns x Ns subspace buffers), sized at create time.
+ */
+#ifndef SPARC_H
+#define SPARC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPARC_OK = 0,
+  SPARC_ERR_INVALID_ARG = 1, /* bad shape, pointer, bound or option           */
+  SPARC_ERR_CUDA = 2,        /* a CUDA runtime call failed                     */
+  SPARC_ERR_OOM = 3,         /* device allocation failed                       */
+  SPARC_ERR_NOT_SPD = 4,     /* the overlap Ms is not positive definite        */
+  SPARC_ERR_NUMERIC = 5,     /* NaN/Inf or a non-converging iteration          */
+  SPARC_ERR_TIMEOUT = 6      /* a bounded device wait ran out                  */
+} sparc_status;
+
+enum { SPARC_PERIODIC = 0, SPARC_DIRICHLET = 1 };
+enum { SPARC_F64 = 0, SPARC_F32 = 1 };
+enum { SPARC_PREC_FP64 = 0, SPARC_PREC_MIXED = 1 };
+
+typedef struct sparc_context* sparc_handle;
+
+/* Uniform grid: nx, ny, nz >= 1 points, spacing h > 0 (bohr), bc[d] per axis. */
+typedef struct {
+  int nx, ny, nz;
+  double h;
+  int bc[3];
+} sparc_grid;
+
+/*
+ * Nonlocal projectors, per atom J = 0..natoms-1 (Sec. II A: "stored as a dense
+ * matrix" per atom and applied to the components of X on its support):
+ *  supp_ptr[J]..supp_ptr[J+1]-1  range of atom J's support points in supp_idx
+ *  supp_idx[]                    linear grid indices (0 <= idx < Nd)
+ *  nproj[J]                      number of projectors of atom J (>= 0)
+ *  chi_ptr[J]                    offset of atom J's column-major
+ *                                n_supp x nproj[J] block in chi[]
+ *  proj_ptr[J]                   offset of atom J's nproj[J] energies in gamma[]
+ *  gamma[]                       projector energies Gamma (Ha)
+ * natoms = 0 (all pointers may be NULL) gives a purely local Hamiltonian.
+ */
+typedef struct {
+  int natoms;
+  const int64_t* supp_ptr;
+  const int32_t* supp_idx;
+  const int32_t* nproj;
+  const int64_t* chi_ptr;
+  const double* chi;
+  const int64_t* proj_ptr;
+  const double* gamma;
+} sparc_nonlocal;
+
+typedef struct {
+  int precision; /* SPARC_PREC_FP64: FP64 everywhere.  SPARC_PREC_MIXED: FP32
+                    orbital storage and filtering, split-precision tensor-core
+                    projection/rotation, FP64 bounds/Cholesky/eigensolve.      */
+  int ns_max;    /* largest Ns passed to any call on this handle (>= 1)        */
+  int device;    /* CUDA device ordinal                                        */
+  int reserved[5];
+} sparc_options;
+
+/* Stage times (ms) of the last sparc_chefsi_step on the handle (CUDA events). */
+typedef struct {
+  float bounds_ms, filter_ms, hx_ms, project_ms, eig_ms, rotate_ms, total_ms;
+} sparc_timings;
+
+/*
+ * sparc_create — build a handle for one Hamiltonian (Sec. II A).
+ * veff: Nd host doubles.  nl may be NULL (no projectors).  opt may be NULL
+ * (FP64, ns_max = 1, device 0).  Validates: n >= 1 per axis, h > 0, bc in
+ * {PERIODIC, DIRICHLET}, support indices in range, nonnegative counts.
+ * Errors: INVALID_ARG, OOM, CUDA.  On error *out is NULL.
+ */
+int sparc_create(const sparc_grid* g, const double* veff, const sparc_nonlocal* nl,
+                 const sparc_options* opt, sparc_handle* out);
+
+/* sparc_destroy — free the handle and all its device memory; NULL is a no-op. */
+int sparc_destroy(sparc_handle h);
+
+/* Last error message of the handle (or of the last failed create if h is NULL). */
+const char* sparc_last_error(sparc_handle h);
+
+/*
+ * sparc_hpsi — Y = H X for ns columns (Sec. II A, the filtering kernel HX).
+ * X, Y: device blocks of type dtype with leading dimension ld (>= Nd); X and Y
+ * must not overlap (INVALID_ARG if X == Y).  1 <= ns <= ns_max.  Asynchronous.
+ */
+int sparc_hpsi(sparc_handle h, const void* X, void* Y, int ns, int64_t ld, int dtype,
+               void* stream);
+
+/*
+ * sparc_spectrum_bounds — Lanczos estimate of the spectrum ends (Algorithm 1
+ * needs lambda_Nd, the largest eigenvalue of H).  `iters` Lanczos steps in FP64
+ * from the start vector v_i = u(seed, i) - 1/2, u the counter-based splitmix64
+ * uniform.  Writes *a0 = smallest Ritz value, *b = largest Ritz value + |beta_k|
+ * (an upper bound of the spectrum).  Synchronous (waits for the stream).
+ * 2 <= iters <= 512.
+ */
+int sparc_spectrum_bounds(sparc_handle h, int iters, uint64_t seed, double* a0, double* b,
+                          void* stream);
+
+/*
+ * sparc_cheb_filter — X <- p_m((H - c)/e) X / p_m((a0 - c)/e) (Algorithm 1,
+ * filtering) with c = (b + a)/2, e = (b - a)/2, m = degree, by the scaled
+ * three-term Chebyshev recurrence.  a is the filter cut-off lambda_c, b an upper
+ * bound of the spectrum, a0 an estimate of its lower end; requires
+ * a0 < a < b and degree >= 1 (INVALID_ARG otherwise).  X: device or host block
+ * of type dtype (SPARC_F64 on FP64 handles, SPARC_F32 on mixed handles),
+ * overwritten with the result.  Asynchronous for device X.
+ */
+int sparc_cheb_filter(sparc_handle h, void* X, int ns, int64_t ld, int dtype, int degree,
+                      double a, double b, double a0, void* stream);
+
+/*
+ * sparc_project — Hs = Xt^T Yt and Ms = Xt^T Xt (Algorithm 1, projection).
+ * Xt, Yt: device blocks (dtype, ld).  Hs, Ms: device ns x ns FP64 column-major
+ * outputs.  Both are symmetrised from their upper triangles.  Asynchronous.
+ */
+int sparc_project(sparc_handle h, const void* Xt, const void* Yt, int ns, int64_t ld,
+                  int dtype, double* Hs, double* Ms, void* stream);
+
+/*
+ * sparc_subspace_eig — solve Hs Z = Ms Z D (Algorithm 1, diagonalisation) in
+ * FP64: Cholesky Ms = L L^T, A = L^-1 Hs L^-T, A = V D V^T, Z = L^-T V.
+ * Hs, Ms: device ns x ns column-major (symmetric; read only).  lam: device ns
+ * doubles, ascending.  Z: device ns x ns column-major, Z^T Ms Z = I, each
+ * column's largest-magnitude entry positive.  Returns NOT_SPD if the Cholesky
+ * meets a non-positive pivot and NUMERIC on NaN/Inf; synchronous (reads the
+ * status word back).
+ */
+int sparc_subspace_eig(sparc_handle h, const double* Hs, const double* Ms, int ns, double* lam,
+                       double* Z, void* stream);
+
+/*
+ * sparc_rotate — Xout = Xt Z (Algorithm 1, rotation).  Xt, Xout: device
+ * blocks (dtype, ld), not overlapping.  Z: device ns x ns FP64 column-major.
+ * Asynchronous.
+ */
+int sparc_rotate(sparc_handle h, const void* Xt, void* Xout, const double* Z, int ns, int64_t ld,
+                 int dtype, void* stream);
+
+/*
+ * sparc_chefsi_step — one full CheFSI step (Algorithm 1): filter X, Yt = H Xt,
+ * project, diagonalise, rotate; X is replaced by Xt Z.
+ * bounds: {a, b, a0} host doubles, or NULL: then b and a0 come from a cached
+ * 32-step Lanczos run (seed 0) made on the first such call, and a is the
+ * largest Ritz value of the previous step on this handle (first step:
+ * a0 + 0.1 (b - a0)).  eig: ns Ritz values, ascending, written to host memory
+ * if eig_on_host is nonzero (the call then waits for the stream), else to
+ * device memory (may be NULL).  X: device or host block.
+ * Errors: INVALID_ARG, NOT_SPD, NUMERIC, CUDA, OOM.
+ */
+int sparc_chefsi_step(sparc_handle h, void* X, int ns, int64_t ld, int dtype, int degree,
+                      const double* bounds, double* eig, int eig_on_host, void* stream);
+
+/* Stage times of the last sparc_chefsi_step (waits for its events). */
+int sparc_get_timings(sparc_handle h, sparc_timings* t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPARC_H */

@@ -1,0 +1,607 @@
+// C ABI of libsparc.so (declared in include/sparc.h): handle set-up, argument
+// validation and the orchestration of Algorithm 1 (filtering, projection,
+// diagonalisation, rotation) over the kernels of stencil.cu, dense.cu,
+// eig.cu and tc_gemm.cu.  All compute runs in those kernels; this file only
+// validates, allocates, builds index tables and enqueues work.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace sparc;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+// 12th-order central second-derivative weights (Fornberg 1988, radius 6):
+// w0 = -5369/1800, w1..w6 = 12/7, -15/56, 10/189, -1/112, 2/1925, -1/16632.
+const double kW[kRadius + 1] = {-5369.0 / 1800.0, 12.0 / 7.0,   -15.0 / 56.0,  10.0 / 189.0,
+                                -1.0 / 112.0,     2.0 / 1925.0, -1.0 / 16632.0};
+
+struct Fail {
+  int code;
+};
+
+int cuda_status(cudaError_t e) {
+  return e == cudaErrorMemoryAllocation ? SPARC_ERR_OOM : SPARC_ERR_CUDA;
+}
+
+#define CK(ctx, expr)                                                               \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      (ctx)->err = std::string(#expr) + ": " + cudaGetErrorString(e_);              \
+      return cuda_status(e_);                                                       \
+    }                                                                               \
+  } while (0)
+
+#define ARG(ctx, cond, msg)                         \
+  do {                                              \
+    if (!(cond)) {                                  \
+      (ctx)->err = std::string("invalid argument: ") + (msg); \
+      return SPARC_ERR_INVALID_ARG;                 \
+    }                                               \
+  } while (0)
+
+size_t elem_size(int dtype) { return dtype == SPARC_F32 ? 4 : 8; }
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int upload(sparc_context* c, const T* host, size_t count, T** dev) {
+  *dev = nullptr;
+  if (count == 0) count = 1;
+  CK(c, cudaMalloc((void**)dev, count * sizeof(T)));
+  c->nl_mem[c->nl_nmem++] = *dev;
+  if (host) CK(c, cudaMemcpy(*dev, host, count * sizeof(T), cudaMemcpyHostToDevice));
+  return SPARC_OK;
+}
+
+int check_block(sparc_context* c, const void* X, int ns, int64_t ld, int dtype) {
+  ARG(c, X != nullptr, "null orbital block");
+  ARG(c, ns >= 1 && ns <= c->ns_max, "ns must be in [1, ns_max]");
+  ARG(c, ld >= c->nd, "ld must be >= Nd");
+  int want = c->precision == SPARC_PREC_MIXED ? SPARC_F32 : SPARC_F64;
+  ARG(c, dtype == want, "dtype must be SPARC_F64 on FP64 handles and SPARC_F32 on mixed handles");
+  return SPARC_OK;
+}
+
+// Nonlocal coefficients of x followed by y = s_h (H - shift) x + s_p prev.
+template <typename T>
+int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
+          int64_t ldp, int ns, double shift, double s_h, double s_p, cudaStream_t st) {
+  const Nonlocal<T>& nl = std::is_same<T, double>::value
+                              ? reinterpret_cast<const Nonlocal<T>&>(c->nl64)
+                              : reinterpret_cast<const Nonlocal<T>&>(c->nl32);
+  const T* veff = std::is_same<T, double>::value ? (const T*)c->veff64 : (const T*)c->veff32;
+  T* D = (T*)c->D;
+  CK(c, nl_coefficients<T>(nl, c->h * c->h * c->h, x, ldx, ns, D, st));
+  CK(c, apply_h<T>(c->grid, c->lap, veff, nl, D, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
+                   st));
+  return SPARC_OK;
+}
+
+// Chebyshev filter (Algorithm 1, scaled three-term recurrence).  Y_0 = X (ldx);
+// Y_i goes to outs[i] (X, W1 or W2).  Returns the buffer holding Y_m.
+template <typename T>
+int run_filter(sparc_context* c, T* X, int64_t ldx, int ns, int m, double a, double b, double a0,
+               bool land_in_workspace, T** result, int64_t* ldr, cudaStream_t st) {
+  const double e = (b - a) / 2.0, cc = (b + a) / 2.0;
+  double sigma = e / (a0 - cc);
+  const double sigma1 = sigma, tau = 2.0 / sigma1;
+  T* W1 = (T*)c->W1;
+  T* W2 = (T*)c->W2;
+  // buffer plan: never write the buffer holding Y_{i-1}; writing over Y_{i-2}
+  // is allowed (pointwise update).
+  std::vector<T*> buf(m + 1);
+  std::vector<int64_t> lds(m + 1);
+  buf[0] = X;
+  lds[0] = ldx;
+  for (int i = 1; i <= m; ++i) {
+    T* out;
+    if (land_in_workspace) {
+      if (m % 2 == 1) out = (i % 2 == 1) ? W1 : X;
+      else out = (i % 2 == 1) ? W1 : W2;
+    } else {
+      out = (i % 2 == 1) ? W1 : X;
+    }
+    buf[i] = out;
+    lds[i] = out == X ? ldx : c->ld;
+  }
+  for (int i = 1; i <= m; ++i) {
+    int rc;
+    if (i == 1) {
+      rc = hstep<T>(c, buf[0], lds[0], buf[1], lds[1], nullptr, 0, ns, cc, sigma1 / e, 0.0, st);
+    } else {
+      double sigma_new = 1.0 / (tau - sigma);
+      rc = hstep<T>(c, buf[i - 1], lds[i - 1], buf[i], lds[i], buf[i - 2], lds[i - 2], ns, cc,
+                    2.0 * sigma_new / e, -sigma * sigma_new, st);
+      sigma = sigma_new;
+    }
+    if (rc) return rc;
+  }
+  *result = buf[m];
+  *ldr = lds[m];
+  return SPARC_OK;
+}
+
+int lanczos(sparc_context* c, int iters, uint64_t seed, double* a0, double* b, cudaStream_t st) {
+  const int64_t nd = c->nd;
+  double* v = c->lz;
+  double* w = v + nd;
+  double* vp = w + nd;
+  double* ab = vp + nd;
+  double* partial = ab + 1024;
+  double* out2 = partial + 320;
+  CK(c, fill_uniform_f64(v, nd, seed, st));
+  CK(c, cudaMemsetAsync(vp, 0, nd * sizeof(double), st));
+  CK(c, lanczos_normalize(v, w, vp, ab, -1, nd, partial, st));
+  for (int j = 0; j < iters; ++j) {
+    const Nonlocal<double>& nl = c->nl64;
+    CK(c, nl_coefficients<double>(nl, c->h * c->h * c->h, v, nd, 1, c->lz + 3 * nd + 1024 + 384,
+                                  st));
+    CK(c, apply_h<double>(c->grid, c->lap, c->veff64, nl, c->lz + 3 * nd + 1024 + 384, v, nd, w,
+                          nd, nullptr, 0, 1, 0.0, 1.0, 0.0, st));
+    CK(c, lanczos_update(w, v, vp, ab, j, nd, st));
+    CK(c, lanczos_normalize(v, w, vp, ab, j, nd, partial, st));
+  }
+  CK(c, lanczos_bounds(ab, iters, out2, st));
+  double hb[2];
+  CK(c, cudaMemcpyAsync(hb, out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(c, cudaStreamSynchronize(st));
+  if (!std::isfinite(hb[0]) || !std::isfinite(hb[1])) {
+    c->err = "Lanczos produced a non-finite bound";
+    return SPARC_ERR_NUMERIC;
+  }
+  *a0 = hb[0];
+  *b = hb[1];
+  return SPARC_OK;
+}
+
+int read_status(sparc_context* c, cudaStream_t st) {
+  int hs[2] = {0, 0};
+  CK(c, cudaMemcpyAsync(hs, c->eig.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(c, cudaStreamSynchronize(st));
+  if (hs[0] == SPARC_ERR_NOT_SPD) {
+    c->err = "subspace overlap Ms is not positive definite";
+    return SPARC_ERR_NOT_SPD;
+  }
+  if (hs[0] || hs[1]) {
+    c->err = "non-finite value in the subspace eigensolve";
+    return SPARC_ERR_NUMERIC;
+  }
+  return SPARC_OK;
+}
+
+template <typename T>
+int do_project(sparc_context* c, const T* Xt, int64_t ldx, const T* Yt, int64_t ldy, int ns,
+               double* Hs, double* Ms, cudaStream_t st) {
+  // both operands share a leading dimension in the SIMT kernel
+  if (ldx != ldy) {
+    c->err = "projection operands must share a leading dimension";
+    return SPARC_ERR_INVALID_ARG;
+  }
+  int nsplit = project_nsplit(c->nd, ns);
+  CK(c, project_simt<T>(Xt, Yt, ldx, c->nd, ns, Hs, Ms, c->proj_work, nsplit, st));
+  return SPARC_OK;
+}
+
+template <typename T>
+int do_step(sparc_context* c, T* X, int64_t ldx, int ns, int m, double a, double b, double a0,
+            double* eig, int eig_on_host, cudaStream_t st) {
+  CK(c, cudaEventRecord(c->ev[1], st));
+  T* Xt;
+  int64_t ldt;
+  int rc = run_filter<T>(c, X, ldx, ns, m, a, b, a0, true, &Xt, &ldt, st);
+  if (rc) return rc;
+  CK(c, cudaEventRecord(c->ev[2], st));
+  T* Yt = Xt == (T*)c->W1 ? (T*)c->W2 : (T*)c->W1;
+  rc = hstep<T>(c, Xt, ldt, Yt, c->ld, nullptr, 0, ns, 0.0, 1.0, 0.0, st);
+  if (rc) return rc;
+  CK(c, cudaEventRecord(c->ev[3], st));
+  rc = do_project<T>(c, Xt, ldt, Yt, c->ld, ns, c->Hs, c->Ms, st);
+  if (rc) return rc;
+  CK(c, cudaEventRecord(c->ev[4], st));
+  CK(c, gen_eig(c->eig, c->Hs, c->Ms, ns, c->lam, c->Z, st));
+  CK(c, cudaEventRecord(c->ev[5], st));
+  CK(c, rotate_simt<T>(Xt, ldt, c->nd, ns, c->Z, X, ldx, st));
+  CK(c, cudaEventRecord(c->ev[6], st));
+  c->timed = true;
+  rc = read_status(c, st);  // synchronises the stream
+  if (rc) return rc;
+  double lmax;
+  CK(c, cudaMemcpy(&lmax, c->lam + ns - 1, sizeof(double), cudaMemcpyDeviceToHost));
+  c->have_prev = true;
+  c->prev_max = lmax;
+  if (eig) {
+    if (eig_on_host)
+      CK(c, cudaMemcpy(eig, c->lam, ns * sizeof(double), cudaMemcpyDeviceToHost));
+    else
+      CK(c, cudaMemcpyAsync(eig, c->lam, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  return SPARC_OK;
+}
+
+// Stage a host block into the library's staging buffer (dtype elements).
+int stage_in(sparc_context* c, const void* X, int ns, int64_t ld, int dtype, void** dev,
+             int64_t* ldd, cudaStream_t st) {
+  size_t es = elem_size(dtype);
+  if (!c->Wstage) CK(c, cudaMalloc(&c->Wstage, (size_t)c->ld * c->ns_max * es));
+  CK(c, cudaMemcpy2DAsync(c->Wstage, c->ld * es, X, ld * es, c->nd * es, ns,
+                          cudaMemcpyHostToDevice, st));
+  *dev = c->Wstage;
+  *ldd = c->ld;
+  return SPARC_OK;
+}
+
+int stage_out(sparc_context* c, void* X, int ns, int64_t ld, int dtype, cudaStream_t st) {
+  size_t es = elem_size(dtype);
+  CK(c, cudaMemcpy2DAsync(X, ld * es, c->Wstage, c->ld * es, c->nd * es, ns,
+                          cudaMemcpyDeviceToHost, st));
+  CK(c, cudaStreamSynchronize(st));
+  return SPARC_OK;
+}
+
+void destroy_ctx(sparc_context* c) {
+  if (!c) return;
+  for (int i = 0; i < c->nl_nmem; ++i) cudaFree(c->nl_mem[i]);
+  cudaFree(c->veff64); cudaFree(c->veff32);
+  cudaFree(c->W1); cudaFree(c->W2); cudaFree(c->Wstage); cudaFree(c->D);
+  cudaFree(c->Hs); cudaFree(c->Ms); cudaFree(c->Z); cudaFree(c->lam); cudaFree(c->proj_work);
+  cudaFree(c->lz);
+  eig_free(c->eig);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* nl,
+                const sparc_options* opt, sparc_context* c) {
+  ARG(c, g != nullptr && veff != nullptr, "grid and veff are required");
+  ARG(c, g->nx >= 1 && g->ny >= 1 && g->nz >= 1, "grid sizes must be >= 1");
+  ARG(c, g->h > 0.0 && std::isfinite(g->h), "h must be positive");
+  for (int d = 0; d < 3; ++d)
+    ARG(c, g->bc[d] == SPARC_PERIODIC || g->bc[d] == SPARC_DIRICHLET, "bad boundary condition");
+  const int64_t nd = (int64_t)g->nx * g->ny * g->nz;
+  ARG(c, nd < (int64_t)1 << 31, "grid too large (Nd must fit in int32)");
+  sparc_options o = opt ? *opt : sparc_options{SPARC_PREC_FP64, 1, 0, {0, 0, 0, 0, 0}};
+  ARG(c, o.precision == SPARC_PREC_FP64 || o.precision == SPARC_PREC_MIXED, "bad precision");
+  ARG(c, o.ns_max >= 1 && o.ns_max <= 65535, "ns_max must be in [1, 65535]");
+  CK(c, cudaSetDevice(o.device));
+  c->device = o.device;
+  c->grid.nx = g->nx; c->grid.ny = g->ny; c->grid.nz = g->nz;
+  for (int d = 0; d < 3; ++d) c->grid.bc[d] = g->bc[d];
+  c->h = g->h;
+  c->nd = nd;
+  c->ld = (nd + 31) / 32 * 32;
+  c->precision = o.precision;
+  c->ns_max = o.ns_max;
+  const double h2 = g->h * g->h;
+  c->lap.diag = -0.5 * 3.0 * kW[0] / h2;
+  c->lap.off[0] = 0.0;
+  for (int p = 1; p <= kRadius; ++p) c->lap.off[p] = -0.5 * kW[p] / h2;
+  for (int64_t i = 0; i < nd; ++i) ARG(c, std::isfinite(veff[i]), "veff must be finite");
+
+  // --- nonlocal tables -----------------------------------------------------
+  int natoms = nl ? nl->natoms : 0;
+  ARG(c, natoms >= 0, "natoms must be >= 0");
+  std::vector<int> proj_ptr32(natoms + 1, 0);
+  int64_t nsupp_tot = 0, nchi_tot = 0;
+  int kp = 0;
+  if (natoms > 0) {
+    ARG(c, nl->supp_ptr && nl->supp_idx && nl->nproj && nl->chi_ptr && nl->chi && nl->proj_ptr &&
+               nl->gamma, "null nonlocal table");
+    ARG(c, nl->supp_ptr[0] == 0 && nl->chi_ptr[0] == 0 && nl->proj_ptr[0] == 0,
+        "nonlocal offsets must start at 0");
+    for (int J = 0; J < natoms; ++J) {
+      int64_t ns_ = nl->supp_ptr[J + 1] - nl->supp_ptr[J];
+      ARG(c, ns_ >= 0 && nl->nproj[J] >= 0 && nl->nproj[J] <= 64, "bad support/projector count");
+      ARG(c, nl->chi_ptr[J + 1] - nl->chi_ptr[J] == ns_ * nl->nproj[J], "chi_ptr inconsistent");
+      ARG(c, nl->proj_ptr[J + 1] - nl->proj_ptr[J] == nl->nproj[J], "proj_ptr inconsistent");
+      proj_ptr32[J + 1] = (int)nl->proj_ptr[J + 1];
+    }
+    nsupp_tot = nl->supp_ptr[natoms];
+    nchi_tot = nl->chi_ptr[natoms];
+    kp = (int)nl->proj_ptr[natoms];
+    for (int64_t t = 0; t < nsupp_tot; ++t)
+      ARG(c, nl->supp_idx[t] >= 0 && nl->supp_idx[t] < nd, "support index out of range");
+    for (int64_t t = 0; t < nchi_tot; ++t) ARG(c, std::isfinite(nl->chi[t]), "chi must be finite");
+    for (int k = 0; k < kp; ++k) ARG(c, std::isfinite(nl->gamma[k]), "gamma must be finite");
+  }
+  // pull form: per grid point, (projector, chi) entries ordered by atom then projector
+  std::vector<int> pull_ptr(nd + 1, 0);
+  int64_t nent = 0;
+  for (int J = 0; J < natoms; ++J) {
+    for (int64_t t = nl->supp_ptr[J]; t < nl->supp_ptr[J + 1]; ++t)
+      pull_ptr[nl->supp_idx[t] + 1] += nl->nproj[J];
+    nent += (nl->supp_ptr[J + 1] - nl->supp_ptr[J]) * nl->nproj[J];
+  }
+  ARG(c, nent < (int64_t)1 << 31, "too many projector entries");
+  for (int64_t i = 0; i < nd; ++i) pull_ptr[i + 1] += pull_ptr[i];
+  std::vector<int> pull_k(nent > 0 ? nent : 1);
+  std::vector<double> pull_chi(nent > 0 ? nent : 1);
+  {
+    std::vector<int> fill(pull_ptr.begin(), pull_ptr.end() - 1);
+    for (int J = 0; J < natoms; ++J) {
+      int64_t s0 = nl->supp_ptr[J], nsup = nl->supp_ptr[J + 1] - s0;
+      for (int64_t t = 0; t < nsup; ++t) {
+        int i = nl->supp_idx[s0 + t];
+        for (int q = 0; q < nl->nproj[J]; ++q) {
+          int slot = fill[i]++;
+          pull_k[slot] = proj_ptr32[J] + q;
+          pull_chi[slot] = nl->chi[nl->chi_ptr[J] + q * nsup + t];
+        }
+      }
+    }
+  }
+
+  // --- device copies --------------------------------------------------------
+  CK(c, cudaMalloc(&c->veff64, nd * sizeof(double)));
+  CK(c, cudaMemcpy(c->veff64, veff, nd * sizeof(double), cudaMemcpyHostToDevice));
+  std::vector<float> f32(std::max<int64_t>(std::max<int64_t>(nd, nent), nchi_tot) + 1);
+  if (c->precision == SPARC_PREC_MIXED) {
+    for (int64_t i = 0; i < nd; ++i) f32[i] = (float)veff[i];
+    CK(c, cudaMalloc(&c->veff32, nd * sizeof(float)));
+    CK(c, cudaMemcpy(c->veff32, f32.data(), nd * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  Nonlocal<double>& n64 = c->nl64;
+  n64.natoms = natoms;
+  n64.kp = kp;
+  if (natoms > 0) {
+    int64_t *sp, *cp;
+    int *si, *npj, *pp;
+    double *chi, *gam;
+    int rc;
+    if ((rc = upload<int64_t>(c, nl->supp_ptr, natoms + 1, &sp))) return rc;
+    if ((rc = upload<int>(c, nl->supp_idx, nsupp_tot, &si))) return rc;
+    if ((rc = upload<int>(c, nl->nproj, natoms, &npj))) return rc;
+    if ((rc = upload<int64_t>(c, nl->chi_ptr, natoms + 1, &cp))) return rc;
+    if ((rc = upload<double>(c, nl->chi, nchi_tot, &chi))) return rc;
+    if ((rc = upload<int>(c, proj_ptr32.data(), natoms + 1, &pp))) return rc;
+    if ((rc = upload<double>(c, nl->gamma, kp, &gam))) return rc;
+    int *pptr, *pk;
+    double* pchi;
+    if ((rc = upload<int>(c, pull_ptr.data(), nd + 1, &pptr))) return rc;
+    if ((rc = upload<int>(c, pull_k.data(), nent, &pk))) return rc;
+    if ((rc = upload<double>(c, pull_chi.data(), nent, &pchi))) return rc;
+    n64.supp_ptr = sp; n64.supp_idx = si; n64.nproj = npj; n64.chi_ptr = cp; n64.chi = chi;
+    n64.proj_ptr = pp; n64.gamma = gam; n64.pull_ptr = pptr; n64.pull_k = pk;
+    n64.pull_chi = pchi;
+    Nonlocal<float>& n32 = c->nl32;
+    n32.natoms = natoms; n32.kp = kp; n32.supp_ptr = sp; n32.supp_idx = si; n32.nproj = npj;
+    n32.chi_ptr = cp; n32.proj_ptr = pp; n32.gamma = gam; n32.pull_ptr = pptr; n32.pull_k = pk;
+    if (c->precision == SPARC_PREC_MIXED) {
+      float *chi32, *pchi32;
+      for (int64_t t = 0; t < nchi_tot; ++t) f32[t] = (float)nl->chi[t];
+      if ((rc = upload<float>(c, f32.data(), nchi_tot, &chi32))) return rc;
+      for (int64_t t = 0; t < nent; ++t) f32[t] = (float)pull_chi[t];
+      if ((rc = upload<float>(c, f32.data(), nent, &pchi32))) return rc;
+      n32.chi = chi32;
+      n32.pull_chi = pchi32;
+    }
+  }
+
+  // --- workspace ----------------------------------------------------------
+  const size_t es = c->precision == SPARC_PREC_MIXED ? 4 : 8;
+  const size_t blk = (size_t)c->ld * c->ns_max * es;
+  CK(c, cudaMalloc(&c->W1, blk));
+  CK(c, cudaMalloc(&c->W2, blk));
+  CK(c, cudaMemset(c->W1, 0, blk));
+  CK(c, cudaMemset(c->W2, 0, blk));
+  CK(c, cudaMalloc(&c->D, (size_t)std::max(kp, 1) * c->ns_max * 8));
+  const size_t nn = (size_t)c->ns_max * c->ns_max;
+  CK(c, cudaMalloc(&c->Hs, nn * 8));
+  CK(c, cudaMalloc(&c->Ms, nn * 8));
+  CK(c, cudaMalloc(&c->Z, nn * 8));
+  CK(c, cudaMalloc(&c->lam, (size_t)c->ns_max * 8));
+  int64_t pw = 0;
+  for (int n = 1; n <= c->ns_max; ++n)
+    pw = std::max<int64_t>(pw, (int64_t)project_nsplit(nd, n) * 2 * n * n);
+  c->proj_work_elems = pw;
+  CK(c, cudaMalloc(&c->proj_work, pw * 8));
+  CK(c, cudaMalloc(&c->lz, ((size_t)3 * nd + 1024 + 384 + std::max(kp, 1)) * 8));
+  CK(c, eig_alloc(c->eig, c->ns_max));
+  for (auto& e : c->ev) CK(c, cudaEventCreate(&e));
+  return SPARC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sparc_create(const sparc_grid* g, const double* veff, const sparc_nonlocal* nl,
+                 const sparc_options* opt, sparc_handle* out) {
+  if (!out) {
+    g_create_err = "invalid argument: out is NULL";
+    return SPARC_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  sparc_context* c = new sparc_context();
+  int rc = create_impl(g, veff, nl, opt, c);
+  if (rc) {
+    g_create_err = c->err;
+    destroy_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return SPARC_OK;
+}
+
+int sparc_destroy(sparc_handle h) {
+  if (!h) return SPARC_OK;
+  cudaSetDevice(h->device);
+  destroy_ctx(h);
+  return SPARC_OK;
+}
+
+const char* sparc_last_error(sparc_handle h) {
+  return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+int sparc_hpsi(sparc_handle c, const void* X, void* Y, int ns, int64_t ld, int dtype,
+               void* stream) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  int rc = check_block(c, X, ns, ld, dtype);
+  if (rc) return rc;
+  ARG(c, Y != nullptr && X != Y, "Y must be non-null and distinct from X");
+  ARG(c, is_device_ptr(X) && is_device_ptr(Y), "hpsi takes device blocks");
+  CK(c, cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == SPARC_F64)
+    return hstep<double>(c, (const double*)X, ld, (double*)Y, ld, nullptr, 0, ns, 0.0, 1.0, 0.0, st);
+  return hstep<float>(c, (const float*)X, ld, (float*)Y, ld, nullptr, 0, ns, 0.0, 1.0, 0.0, st);
+}
+
+int sparc_spectrum_bounds(sparc_handle c, int iters, uint64_t seed, double* a0, double* b,
+                          void* stream) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  ARG(c, iters >= 2 && iters <= 512, "iters must be in [2, 512]");
+  ARG(c, a0 && b, "null output");
+  CK(c, cudaSetDevice(c->device));
+  return lanczos(c, iters, seed, a0, b, (cudaStream_t)stream);
+}
+
+int sparc_cheb_filter(sparc_handle c, void* X, int ns, int64_t ld, int dtype, int degree, double a,
+                      double b, double a0, void* stream) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  int rc = check_block(c, X, ns, ld, dtype);
+  if (rc) return rc;
+  ARG(c, degree >= 1 && degree <= 1000, "degree must be in [1, 1000]");
+  ARG(c, std::isfinite(a) && std::isfinite(b) && std::isfinite(a0) && a0 < a && a < b,
+      "bounds must satisfy a0 < a < b");
+  CK(c, cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool host = !is_device_ptr(X);
+  void* Xd = X;
+  int64_t ldd = ld;
+  if (host && (rc = stage_in(c, X, ns, ld, dtype, &Xd, &ldd, st))) return rc;
+  void* res;
+  int64_t ldr;
+  if (dtype == SPARC_F64)
+    rc = run_filter<double>(c, (double*)Xd, ldd, ns, degree, a, b, a0, false, (double**)&res, &ldr,
+                            st);
+  else
+    rc = run_filter<float>(c, (float*)Xd, ldd, ns, degree, a, b, a0, false, (float**)&res, &ldr,
+                           st);
+  if (rc) return rc;
+  if (res != Xd) {
+    if (dtype == SPARC_F64)
+      CK(c, copy_block<double>((const double*)res, ldr, (double*)Xd, ldd, c->nd, ns, st));
+    else
+      CK(c, copy_block<float>((const float*)res, ldr, (float*)Xd, ldd, c->nd, ns, st));
+  }
+  if (host) return stage_out(c, X, ns, ld, dtype, st);
+  return SPARC_OK;
+}
+
+int sparc_project(sparc_handle c, const void* Xt, const void* Yt, int ns, int64_t ld, int dtype,
+                  double* Hs, double* Ms, void* stream) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  int rc = check_block(c, Xt, ns, ld, dtype);
+  if (rc) return rc;
+  ARG(c, Yt && Hs && Ms, "null argument");
+  CK(c, cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == SPARC_F64)
+    return do_project<double>(c, (const double*)Xt, ld, (const double*)Yt, ld, ns, Hs, Ms, st);
+  return do_project<float>(c, (const float*)Xt, ld, (const float*)Yt, ld, ns, Hs, Ms, st);
+}
+
+int sparc_subspace_eig(sparc_handle c, const double* Hs, const double* Ms, int ns, double* lam,
+                       double* Z, void* stream) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  ARG(c, Hs && Ms && lam && Z, "null argument");
+  ARG(c, ns >= 1 && ns <= c->ns_max, "ns must be in [1, ns_max]");
+  CK(c, cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(c, gen_eig(c->eig, Hs, Ms, ns, lam, Z, st));
+  return read_status(c, st);
+}
+
+int sparc_rotate(sparc_handle c, const void* Xt, void* Xout, const double* Z, int ns, int64_t ld,
+                 int dtype, void* stream) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  int rc = check_block(c, Xt, ns, ld, dtype);
+  if (rc) return rc;
+  ARG(c, Xout && Z && Xout != Xt, "Xout must be non-null and distinct from Xt");
+  CK(c, cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == SPARC_F64)
+    CK(c, rotate_simt<double>((const double*)Xt, ld, c->nd, ns, Z, (double*)Xout, ld, st));
+  else
+    CK(c, rotate_simt<float>((const float*)Xt, ld, c->nd, ns, Z, (float*)Xout, ld, st));
+  return SPARC_OK;
+}
+
+int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, int degree,
+                      const double* bounds, double* eig, int eig_on_host, void* stream) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  int rc = check_block(c, X, ns, ld, dtype);
+  if (rc) return rc;
+  ARG(c, degree >= 1 && degree <= 1000, "degree must be in [1, 1000]");
+  CK(c, cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(c, cudaEventRecord(c->ev[0], st));
+  double a, b, a0;
+  if (bounds) {
+    a = bounds[0];
+    b = bounds[1];
+    a0 = bounds[2];
+  } else {
+    if (!c->have_bounds) {
+      if ((rc = lanczos(c, 32, 0, &c->a0, &c->b, st))) return rc;
+      c->have_bounds = true;
+    }
+    b = c->b;
+    a0 = c->a0;
+    a = c->have_prev ? c->prev_max : a0 + 0.1 * (b - a0);
+    double lo = a0 + 1e-3 * (b - a0), hi = b - 1e-3 * (b - a0);
+    a = std::min(std::max(a, lo), hi);
+  }
+  ARG(c, std::isfinite(a) && std::isfinite(b) && std::isfinite(a0) && a0 < a && a < b,
+      "bounds must satisfy a0 < a < b");
+  const bool host = !is_device_ptr(X);
+  void* Xd = X;
+  int64_t ldd = ld;
+  if (host && (rc = stage_in(c, X, ns, ld, dtype, &Xd, &ldd, st))) return rc;
+  if (dtype == SPARC_F64)
+    rc = do_step<double>(c, (double*)Xd, ldd, ns, degree, a, b, a0, eig, eig_on_host, st);
+  else
+    rc = do_step<float>(c, (float*)Xd, ldd, ns, degree, a, b, a0, eig, eig_on_host, st);
+  if (rc) return rc;
+  if (host) return stage_out(c, X, ns, ld, dtype, st);
+  return SPARC_OK;
+}
+
+int sparc_get_timings(sparc_handle c, sparc_timings* t) {
+  if (!c || !t) return SPARC_ERR_INVALID_ARG;
+  ARG(c, c->timed, "no step has run on this handle");
+  CK(c, cudaEventSynchronize(c->ev[6]));
+  float ms[6];
+  for (int i = 0; i < 6; ++i) CK(c, cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]));
+  t->bounds_ms = ms[0];
+  t->filter_ms = ms[1];
+  t->hx_ms = ms[2];
+  t->project_ms = ms[3];
+  t->eig_ms = ms[4];
+  t->rotate_ms = ms[5];
+  CK(c, cudaEventElapsedTime(&t->total_ms, c->ev[0], c->ev[6]));
+  return SPARC_OK;
+}
+
+}  // extern "C"

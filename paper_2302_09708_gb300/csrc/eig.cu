@@ -1,0 +1,702 @@
+// FP64 generalised symmetric eigensolver for the subspace problem
+// Hs Z = Ms Z D (Algorithm 1, "Diagonalization"; paper Sec. II C solves it
+// with a single-GPU sygvd).  Steps, all on the device:
+//   1. Cholesky Ms = L L^T (blocked, right-looking; status NOT_SPD on a
+//      non-positive pivot);
+//   2. A = L^-1 Hs L^-T by two triangular solves (warp per column), symmetrised;
+//   3. Householder reduction A = Q T Q^T (T tridiagonal);
+//   4. eigenvalues of T by Sturm-count bisection (thread per eigenvalue);
+//   5. eigenvectors of T by inverse iteration (thread per eigenvalue; clusters
+//      of nearly equal eigenvalues are iterated in sequence with Gram-Schmidt
+//      against the earlier members), then one Cholesky-QR pass that restores
+//      orthonormality to working precision;
+//   6. V = Q V_T by applying the reflectors (warp per column, all reflectors);
+//   7. Z = L^-T V, each column's largest-magnitude entry made positive.
+// Every reduction runs in a fixed order, so results are bit-reproducible.
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace sparc {
+
+namespace {
+
+constexpr int kNb = 32;  // Cholesky panel width
+
+enum { ST_OK = 0, ST_NOT_SPD = 4, ST_NUMERIC = 5 };
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky (lower, column-major, in place on A's lower triangle)
+// ---------------------------------------------------------------------------
+__global__ void k_potrf_diag(double* A, int n, int j0, int jb, int* status) {
+  __shared__ double s[kNb][kNb + 1];
+  if (*status) return;
+  const int t = threadIdx.x;  // 0..kNb-1: row within the block
+  for (int c = 0; c < jb; ++c)
+    if (t < jb) s[t][c] = A[(j0 + t) + (int64_t)(j0 + c) * n];
+  __syncthreads();
+  for (int c = 0; c < jb; ++c) {
+    if (t == 0) {
+      double d = s[c][c];
+      if (!(d > 0.0) || !isfinite(d)) {
+        *status = ST_NOT_SPD;
+        s[c][c] = 1.0;
+      } else {
+        s[c][c] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (t > c && t < jb) s[t][c] /= s[c][c];
+    __syncthreads();
+    if (t > c && t < jb)
+      for (int k = c + 1; k <= t; ++k) s[t][k] -= s[t][c] * s[k][c];
+    __syncthreads();
+  }
+  for (int c = 0; c < jb; ++c)
+    if (t < jb && t >= c) A[(j0 + t) + (int64_t)(j0 + c) * n] = s[t][c];
+}
+
+// rows i >= j0 + jb: L[i, j0:j0+jb] = A[i, j0:j0+jb] L11^-T
+__global__ void k_potrf_panel(double* A, int n, int j0, int jb, const int* status) {
+  __shared__ double L11[kNb][kNb + 1];
+  if (*status) return;
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+    int r = e % jb, c = e / jb;
+    L11[r][c] = A[(j0 + r) + (int64_t)(j0 + c) * n];
+  }
+  __syncthreads();
+  int i = j0 + jb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x[kNb];
+#pragma unroll
+  for (int c = 0; c < kNb; ++c)
+    if (c < jb) x[c] = A[i + (int64_t)(j0 + c) * n];
+#pragma unroll
+  for (int c = 0; c < kNb; ++c) {
+    if (c < jb) {
+      double v = x[c];
+#pragma unroll
+      for (int k = 0; k < kNb; ++k)
+        if (k < c) v -= x[k] * L11[c][k];
+      x[c] = v / L11[c][c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kNb; ++c)
+    if (c < jb) A[i + (int64_t)(j0 + c) * n] = x[c];
+}
+
+// trailing update A22 -= L21 L21^T on the lower triangle (32 x 32 tiles)
+__global__ void k_potrf_update(double* A, int n, int j0, int jb, const int* status) {
+  __shared__ double Li[32][kNb + 1];
+  __shared__ double Lj[32][kNb + 1];
+  if (*status) return;
+  const int base = j0 + jb;
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  const int i0 = base + bi * 32, jj0 = base + bj * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8 threads
+  for (int e = threadIdx.x; e < 32 * jb; e += blockDim.x) {
+    int r = e % 32, c = e / 32;
+    Li[r][c] = (i0 + r < n) ? A[(i0 + r) + (int64_t)(j0 + c) * n] : 0.0;
+    Lj[r][c] = (jj0 + r < n) ? A[(jj0 + r) + (int64_t)(j0 + c) * n] : 0.0;
+  }
+  __syncthreads();
+  for (int rr = ty; rr < 32; rr += 8) {
+    int i = i0 + tx, j = jj0 + rr;
+    if (i < n && j < n && j <= i) {
+      double s = 0.0;
+      for (int c = 0; c < jb; ++c) s += Li[tx][c] * Lj[rr][c];
+      A[i + (int64_t)j * n] -= s;
+    }
+  }
+}
+
+// lower-triangular copy with zeroed upper part: L = tril(A)
+__global__ void k_tril_copy(const double* A, double* L, int n) {
+  int64_t nn = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % n), j = (int)(t / n);
+    L[t] = i >= j ? A[t] : 0.0;
+  }
+}
+
+__global__ void k_transpose(const double* __restrict__ A, double* __restrict__ B, int n) {
+  __shared__ double tile[32][33];
+  int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int i = bx + threadIdx.x, j = by + r;
+    if (i < n && j < n) tile[r][threadIdx.x] = A[i + (int64_t)j * n];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int i = by + threadIdx.x, j = bx + r;
+    if (i < n && j < n) B[i + (int64_t)j * n] = tile[threadIdx.x][r];
+  }
+}
+
+// B = (A + A^T)/2
+__global__ void k_symmetrize(const double* __restrict__ A, double* __restrict__ B, int n) {
+  int64_t nn = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % n), j = (int)(t / n);
+    B[t] = 0.5 * (A[t] + A[j + (int64_t)i * n]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Triangular solves, one warp per right-hand-side column (column-major B, X).
+// forward:  X = L^-1 B   (Lrm = L stored row-major, i.e. L^T column-major)
+// backward: X = L^-T B   (Lcm = L column-major)
+// ---------------------------------------------------------------------------
+constexpr int kTrsmWarps = 4;
+
+template <bool FORWARD>
+__global__ void __launch_bounds__(kTrsmWarps * 32)
+    k_trsm(const double* __restrict__ Lt, const double* __restrict__ B, double* __restrict__ X,
+           int n, int ncols, const int* status) {
+  extern __shared__ double xs_all[];
+  if (*status) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= ncols) return;
+  double* xs = xs_all + (int64_t)warp * n;
+  const double* b = B + (int64_t)c * n;
+  for (int step = 0; step < n; ++step) {
+    const int i = FORWARD ? step : n - 1 - step;
+    // Lt row i holds L[i, k] (forward, k < i) or L[k, i] (backward, k > i)
+    const double* row = Lt + (int64_t)i * n;
+    double s = 0.0;
+    if (FORWARD) {
+      for (int k = lane; k < i; k += 32) s += row[k] * xs[k];
+    } else {
+      for (int k = i + 1 + lane; k < n; k += 32) s += row[k] * xs[k];
+    }
+    s = warp_sum_d(s);
+    double xi = (b[i] - s) / row[i];
+    if (lane == 0) xs[i] = xi;
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) X[(int64_t)c * n + i] = xs[i];
+}
+
+// ---------------------------------------------------------------------------
+// Householder tridiagonalisation of a symmetric A (column-major == row-major).
+// Step k: v from A[k+1:, k]; p = A v on the trailing block; A -= 2(v q^T + q v^T)
+// with q = p - (v.p) v.  Reflector k is stored in row k of Hv (entries k+1..n-1).
+// ---------------------------------------------------------------------------
+__device__ double block_sum_d(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;  // every thread gets the same value
+}
+
+__global__ void k_house_vec(const double* __restrict__ A, double* __restrict__ Hv, double* d,
+                            double* e, int n, int k) {
+  __shared__ double sh[32];
+  const double* col = A + (int64_t)k * n;  // column k == row k
+  double acc = 0.0;
+  for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += col[i] * col[i];
+  double xn = sqrt(block_sum_d(acc, sh));
+  double x0 = col[k + 1];
+  double alpha = x0 >= 0.0 ? -xn : xn;
+  // v = x - alpha e1, |v|^2 = xn^2 - 2 alpha x0 + alpha^2 = 2 xn^2 + 2 xn |x0|
+  double vn2 = 0.0;
+  for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+    double v = col[i] - (i == k + 1 ? alpha : 0.0);
+    vn2 += v * v;
+  }
+  double vn = sqrt(block_sum_d(vn2, sh));
+  double* hv = Hv + (int64_t)k * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = 0.0;
+    if (i > k && xn > 0.0 && vn > 0.0) v = (col[i] - (i == k + 1 ? alpha : 0.0)) / vn;
+    hv[i] = v;
+  }
+  if (threadIdx.x == 0) {
+    d[k] = col[k];
+    e[k] = xn > 0.0 ? alpha : 0.0;
+  }
+}
+
+// p_i = sum_{j>k} A[i][j] v_j for i > k (warp per row)
+__global__ void k_house_matvec(const double* __restrict__ A, const double* __restrict__ Hv,
+                               double* __restrict__ p, int n, int k) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int i = k + 1 + warp;
+  if (i >= n) return;
+  const double* row = A + (int64_t)i * n;
+  const double* v = Hv + (int64_t)k * n;
+  double s = 0.0;
+  for (int j = k + 1 + lane; j < n; j += 32) s += row[j] * v[j];
+  s = warp_sum_d(s);
+  if (lane == 0) p[i] = s;
+}
+
+// A[i][j] -= 2 (v_i q_j + q_i v_j), q = p - (v.p) v, on the trailing block
+__global__ void k_house_update(double* __restrict__ A, const double* __restrict__ Hv,
+                               const double* __restrict__ p, int n, int k) {
+  __shared__ double sh[32];
+  const double* v = Hv + (int64_t)k * n;
+  double acc = 0.0;
+  for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += v[i] * p[i];
+  const double K = block_sum_d(acc, sh);
+  const int m = n - k - 1;
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < mm;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = k + 1 + (int)(t % m), j = k + 1 + (int)(t / m);
+    double qi = p[i] - K * v[i], qj = p[j] - K * v[j];
+    A[i + (int64_t)j * n] -= 2.0 * (v[i] * qj + qi * v[j]);
+  }
+}
+
+__global__ void k_house_tail(const double* A, double* Hv, double* d, double* e, int n) {
+  if (threadIdx.x != 0) return;
+  int k0 = n >= 2 ? n - 2 : 0;
+  for (int k = k0; k < n; ++k) {
+    d[k] = A[k + (int64_t)k * n];
+    for (int i = 0; i < n; ++i) Hv[(int64_t)k * n + i] = 0.0;
+  }
+  if (n >= 2) e[n - 2] = A[(n - 1) + (int64_t)(n - 2) * n];
+}
+
+// ---------------------------------------------------------------------------
+// Tridiagonal eigenvalues by bisection.  scal[0..1] = Gershgorin interval,
+// scal[2] = pivmin.
+// ---------------------------------------------------------------------------
+__global__ void k_gersh(const double* d, const double* e, int n, double* e2, double* scal) {
+  __shared__ double sh[32];
+  double lo = 1e300, hi = -1e300, emax = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i + 1 < n) {
+      e2[i] = e[i] * e[i];
+      emax = fmax(emax, e2[i]);
+    }
+  }
+  // block min / max via shared memory
+  __shared__ double slo[1024], shi[1024], sem[1024];
+  slo[threadIdx.x] = lo;
+  shi[threadIdx.x] = hi;
+  sem[threadIdx.x] = emax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 1; t < (int)blockDim.x; ++t) {
+      lo = fmin(lo, slo[t]);
+      hi = fmax(hi, shi[t]);
+      emax = fmax(emax, sem[t]);
+    }
+    double tnorm = fmax(fabs(lo), fabs(hi));
+    double pad = 2.2e-16 * tnorm * n + 1e-300;
+    scal[0] = lo - pad;
+    scal[1] = hi + pad;
+    scal[2] = fmax(2.2250738585072014e-308 * fmax(1.0, emax), 1e-300);
+    scal[3] = tnorm;
+  }
+  (void)sh;
+}
+
+__device__ int sturm(const double* __restrict__ d, const double* __restrict__ e2, int n,
+                     double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0.0) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e2, int n,
+                         const double* __restrict__ scal, double* __restrict__ lam) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double lo = scal[0], hi = scal[1], pivmin = scal[2];
+  for (int it = 0; it < 256; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (hi - lo <= 2.0 * 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
+    if (sturm(d, e2, n, mid, pivmin) > j) hi = mid; else lo = mid;
+  }
+  lam[j] = 0.5 * (lo + hi);
+}
+
+// Cluster bookkeeping: clus[j] = first index of j's cluster, clus[n + j] = its size.
+__global__ void k_clusters(const double* lam, int n, const double* scal, int* clus) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double tol = 1e-9 * fmax(scal[3], 1e-300);
+  int start = 0;
+  for (int j = 1; j <= n; ++j) {
+    if (j == n || lam[j] - lam[j - 1] > tol) {
+      for (int t = start; t < j; ++t) {
+        clus[t] = start;
+        clus[n + t] = j - start;
+      }
+      start = j;
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double start_value(uint64_t seed, int i) {
+  uint64_t z = mix64(seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ULL);
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+}
+
+// LU with partial pivoting of T - sigma I.  Factors at lu[(f * n + i) * stride + j]
+// for f = 0 (u0), 1 (u1), 2 (u2), 3 (l); pivot flags in piv[i * stride + j].
+struct TriLU {
+  double* lu;
+  int* piv;
+  int n;
+  int64_t stride;
+  int j;
+  __device__ double& at(int f, int i) const { return lu[((int64_t)f * n + i) * stride + j]; }
+  __device__ int& pv(int i) const { return piv[(int64_t)i * stride + j]; }
+};
+
+__device__ void tri_factor(const TriLU& F, const double* d, const double* e, double sigma,
+                           double pivmin) {
+  const int n = F.n;
+  double p0 = d[0] - sigma, p1 = n > 1 ? e[0] : 0.0, p2 = 0.0;
+  for (int k = 0; k + 1 < n; ++k) {
+    double ek = e[k];
+    double a1 = d[k + 1] - sigma;
+    double e1 = k + 2 < n ? e[k + 1] : 0.0;
+    if (fabs(p0) >= fabs(ek)) {
+      if (fabs(p0) < pivmin) p0 = p0 >= 0.0 ? pivmin : -pivmin;
+      double l = ek / p0;
+      F.at(0, k) = p0; F.at(1, k) = p1; F.at(2, k) = p2; F.at(3, k) = l; F.pv(k) = 0;
+      double np0 = a1 - l * p1, np1 = e1 - l * p2;
+      p0 = np0; p1 = np1; p2 = 0.0;
+    } else {
+      double l = p0 / ek;
+      F.at(0, k) = ek; F.at(1, k) = a1; F.at(2, k) = e1; F.at(3, k) = l; F.pv(k) = 1;
+      double np0 = p1 - l * a1, np1 = p2 - l * e1;
+      p0 = np0; p1 = np1; p2 = 0.0;
+    }
+  }
+  if (fabs(p0) < pivmin) p0 = p0 >= 0.0 ? pivmin : -pivmin;
+  F.at(0, n - 1) = p0;
+  F.at(1, n - 1) = 0.0;
+  F.at(2, n - 1) = 0.0;
+  F.at(3, n - 1) = 0.0;
+  F.pv(n - 1) = 0;
+}
+
+// Solve (T - sigma) x = b in place in column x (stride 1).
+__device__ void tri_solve(const TriLU& F, double* x) {
+  const int n = F.n;
+  for (int k = 0; k + 1 < n; ++k) {
+    if (F.pv(k)) {
+      double t = x[k];
+      x[k] = x[k + 1];
+      x[k + 1] = t;
+    }
+    x[k + 1] -= F.at(3, k) * x[k];
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    double s = x[k];
+    if (k + 1 < n) s -= F.at(1, k) * x[k + 1];
+    if (k + 2 < n) s -= F.at(2, k) * x[k + 2];
+    x[k] = s / F.at(0, k);
+  }
+}
+
+__device__ void scale_maxabs(double* x, int n) {
+  double m = 0.0;
+  for (int i = 0; i < n; ++i) m = fmax(m, fabs(x[i]));
+  if (m > 0.0) {
+    double inv = 1.0 / m;
+    for (int i = 0; i < n; ++i) x[i] *= inv;
+  }
+}
+
+constexpr int kInvIters = 3;
+
+// Thread per eigenvalue, singletons only: column j of V (column-major).
+__global__ void k_inviter_single(const double* __restrict__ d, const double* __restrict__ e,
+                                 const double* __restrict__ lam, const double* __restrict__ scal,
+                                 const int* __restrict__ clus, int n, double* lu, int* piv,
+                                 double* V) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || clus[n + j] != 1) return;
+  TriLU F{lu, piv, n, n, j};
+  const double pivmin = fmax(2.2e-16 * scal[3], 1e-300);
+  tri_factor(F, d, e, lam[j], pivmin);
+  double* x = V + (int64_t)j * n;
+  for (int i = 0; i < n; ++i) x[i] = start_value(0x5EEDull + j, i);
+  for (int it = 0; it < kInvIters; ++it) {
+    scale_maxabs(x, n);
+    tri_solve(F, x);
+  }
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += x[i] * x[i];
+  double inv = 1.0 / sqrt(s);
+  for (int i = 0; i < n; ++i) x[i] *= inv;
+}
+
+// One CTA per cluster (launched for every j; only cluster starts of size > 1 work).
+// Members are iterated in order; each iterate is orthogonalised against the
+// earlier members (classical Gram-Schmidt, applied twice).
+__global__ void k_inviter_cluster(const double* __restrict__ d, const double* __restrict__ e,
+                                  const double* __restrict__ lam, const double* __restrict__ scal,
+                                  const int* __restrict__ clus, int n, double* lu, int* piv,
+                                  double* V) {
+  __shared__ double sh[32];
+  __shared__ double coef[1];
+  const int j0 = blockIdx.x;
+  if (clus[j0] != j0 || clus[n + j0] < 2) return;
+  const int size = clus[n + j0];
+  const double pivmin = fmax(2.2e-16 * scal[3], 1e-300);
+  const double sep = 10.0 * 2.2e-16 * fmax(scal[3], 1e-300);
+  double shift_prev = 0.0;
+  for (int m = 0; m < size; ++m) {
+    const int j = j0 + m;
+    double sigma = lam[j];
+    if (m > 0 && sigma - shift_prev < sep) sigma = shift_prev + sep;
+    shift_prev = sigma;
+    TriLU F{lu, piv, n, n, j};
+    if (threadIdx.x == 0) tri_factor(F, d, e, sigma, pivmin);
+    double* x = V + (int64_t)j * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = start_value(0x5EEDull + j, i);
+    __syncthreads();
+    for (int it = 0; it < kInvIters; ++it) {
+      if (threadIdx.x == 0) {
+        scale_maxabs(x, n);
+        tri_solve(F, x);
+      }
+      __syncthreads();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int q = 0; q < m; ++q) {
+          const double* y = V + (int64_t)(j0 + q) * n;
+          double acc = 0.0;
+          for (int i = threadIdx.x; i < n; i += blockDim.x) acc += y[i] * x[i];
+          double c = block_sum_d(acc, sh);
+          for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] -= c * y[i];
+          __syncthreads();
+        }
+      }
+      double acc = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) acc += x[i] * x[i];
+      double nrm = sqrt(block_sum_d(acc, sh));
+      if (threadIdx.x == 0) coef[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] *= coef[0];
+      __syncthreads();
+    }
+  }
+}
+
+// Apply all reflectors: V <- H_0 H_1 ... H_{n-3} V, warp per column of V.
+constexpr int kBtWarps = 4;
+__global__ void __launch_bounds__(kBtWarps * 32)
+    k_backtransform(const double* __restrict__ Hv, double* __restrict__ V, int n) {
+  extern __shared__ double cols[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= n) return;
+  double* x = cols + (int64_t)warp * n;
+  for (int i = lane; i < n; i += 32) x[i] = V[(int64_t)c * n + i];
+  __syncwarp();
+  for (int k = n - 3; k >= 0; --k) {
+    const double* v = Hv + (int64_t)k * n;
+    double s = 0.0;
+    for (int i = k + 1 + lane; i < n; i += 32) s += v[i] * x[i];
+    s = 2.0 * warp_sum_d(s);
+    for (int i = k + 1 + lane; i < n; i += 32) x[i] -= s * v[i];
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) V[(int64_t)c * n + i] = x[i];
+}
+
+// Largest-magnitude entry of each column made positive (first index on ties);
+// eigenvalue NaN/Inf check.
+__global__ void k_fix_signs(double* Z, int n, const double* lam, int* status) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  double* z = Z + (int64_t)warp * n;
+  double best = -1.0;
+  int bi = 0;
+  for (int i = lane; i < n; i += 32) {
+    double a = fabs(z[i]);
+    if (a > best) { best = a; bi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  bool neg = z[bi] < 0.0;
+  if (neg)
+    for (int i = lane; i < n; i += 32) z[i] = -z[i];
+  if (lane == 0 && !isfinite(lam[warp])) atomicCAS(status, 0, ST_NUMERIC);
+}
+
+cudaError_t cholesky(double* A, int n, int* status, cudaStream_t st) {
+  for (int j0 = 0; j0 < n; j0 += kNb) {
+    int jb = min(kNb, n - j0);
+    k_potrf_diag<<<1, kNb, 0, st>>>(A, n, j0, jb, status);
+    int rem = n - j0 - jb;
+    if (rem > 0) {
+      k_potrf_panel<<<(rem + 127) / 128, 128, 0, st>>>(A, n, j0, jb, status);
+      int nt = (rem + 31) / 32;
+      k_potrf_update<<<dim3(nt, nt), 256, 0, st>>>(A, n, j0, jb, status);
+    }
+  }
+  return cudaGetLastError();
+}
+
+// warps per block for the column-per-warp kernels: each warp keeps one n-vector
+// in shared memory
+int col_warps(int n) {
+  int w = (int)((200 * 1024) / ((size_t)n * sizeof(double)));
+  return w < 1 ? 1 : (w > 4 ? 4 : w);
+}
+
+template <bool FWD>
+cudaError_t trsm(const double* Lt, const double* B, double* X, int n, const int* status,
+                 cudaStream_t st) {
+  int wpb = col_warps(n);
+  size_t smem = (size_t)wpb * n * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_trsm<FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_trsm<FWD><<<(n + wpb - 1) / wpb, wpb * 32, smem, st>>>(Lt, B, X, n, n, status);
+  return cudaGetLastError();
+}
+
+int blocks_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
+
+}  // namespace
+
+cudaError_t eig_alloc(EigWork& w, int nmax) {
+  eig_free(w);
+  w.nmax = nmax;
+  size_t nn = (size_t)nmax * nmax;
+  cudaError_t err = cudaSuccess;
+  auto take = [&](auto** p, size_t bytes) {
+    if (err == cudaSuccess) err = cudaMalloc((void**)p, bytes > 0 ? bytes : 8);
+  };
+  take(&w.L, nn * 8);
+  take(&w.A, nn * 8);
+  take(&w.W, nn * 8);
+  take(&w.V, nn * 8);
+  take(&w.d, (size_t)nmax * 8);
+  take(&w.e, (size_t)nmax * 8 + 8);
+  take(&w.tau, (size_t)nmax * 8 * 2 + 8);
+  take(&w.lu, 4 * nn * 8);
+  take(&w.scal, 64 * 8);
+  take(&w.status, 64);
+  take(&w.clus, (size_t)2 * nmax * 4 + 8);
+  take(&w.piv, nn * 4);
+  if (err != cudaSuccess) eig_free(w);
+  return err;
+}
+
+void eig_free(EigWork& w) {
+  cudaFree(w.L); cudaFree(w.A); cudaFree(w.W); cudaFree(w.V); cudaFree(w.d); cudaFree(w.e);
+  cudaFree(w.tau); cudaFree(w.lu); cudaFree(w.scal); cudaFree(w.status); cudaFree(w.clus);
+  cudaFree(w.piv);
+  w = EigWork{};
+}
+
+cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, double* lam, double* Z,
+                    cudaStream_t st) {
+  // Buffers (n x n unless noted): L (Cholesky factor of Ms, kept to the end),
+  // A, W, V, lu (4 n x n), piv (n x n ints).  status[0]: NOT_SPD/NUMERIC of the
+  // problem; status[1]: failure of the internal re-orthonormalisation.
+  const int64_t nn = (int64_t)n * n;
+  const int nb = blocks_for(nn);
+  const dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
+  int* st0 = w.status;
+  int* st1 = w.status + 1;
+  cudaMemsetAsync(w.status, 0, 2 * sizeof(int), st);
+  // 1. Ms = L L^T
+  cudaMemcpyAsync(w.W, Ms, nn * 8, cudaMemcpyDeviceToDevice, st);
+  cholesky(w.W, n, st0, st);
+  k_tril_copy<<<nb, 256, 0, st>>>(w.W, w.L, n);
+  k_transpose<<<tg, tb, 0, st>>>(w.L, w.V, n);  // V = L row-major (forward solves)
+  // 2. A = sym(L^-1 (L^-1 Hs)^T)
+  trsm<true>(w.V, Hs, w.W, n, st0, st);          // W = L^-1 Hs
+  k_transpose<<<tg, tb, 0, st>>>(w.W, w.A, n);  // A = W^T
+  trsm<true>(w.V, w.A, w.W, n, st0, st);         // W = L^-1 W^T
+  k_symmetrize<<<nb, 256, 0, st>>>(w.W, w.A, n);
+  // 3. Householder tridiagonalisation; reflectors in the rows of Hv = lu[0, nn)
+  double* Hv = w.lu;
+  double* p = w.tau;
+  for (int k = 0; k + 2 < n; ++k) {
+    k_house_vec<<<1, 256, 0, st>>>(w.A, Hv, w.d, w.e, n, k);
+    int m = n - k - 1;
+    k_house_matvec<<<(m + 7) / 8, 256, 0, st>>>(w.A, Hv, p, n, k);
+    int ub = (int)std::min<int64_t>(((int64_t)m * m + 255) / 256, 1024);
+    k_house_update<<<ub, 256, 0, st>>>(w.A, Hv, p, n, k);
+  }
+  k_house_tail<<<1, 32, 0, st>>>(w.A, Hv, w.d, w.e, n);
+  cudaMemcpyAsync(w.A, Hv, nn * 8, cudaMemcpyDeviceToDevice, st);  // reflectors -> A
+  // 4. eigenvalues of T (ascending)
+  double* e2 = w.tau + n;
+  k_gersh<<<1, 1024, 0, st>>>(w.d, w.e, n, e2, w.scal);
+  k_bisect<<<(n + 31) / 32, 32, 0, st>>>(w.d, e2, n, w.scal, lam);
+  // 5. eigenvectors of T into W (column-major); factors in lu (4 n x n)
+  k_clusters<<<1, 32, 0, st>>>(lam, n, w.scal, w.clus);
+  double* VT = w.W;
+  k_inviter_single<<<(n + 31) / 32, 32, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv,
+                                                 VT);
+  k_inviter_cluster<<<n, 256, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv, VT);
+  //    Cholesky-QR pass: G = VT^T VT = R R^T, Q = VT R^-T  (Q^T = R^-1 VT^T)
+  {
+    double* G1 = w.lu;           // unused copy (projection writes two outputs)
+    double* G = w.lu + nn;
+    double* work = w.lu + 2 * nn;  // 2 nn doubles for one split
+    project_simt<double>(VT, VT, n, n, n, G1, G, work, 1, st);
+    cholesky(G, n, st1, st);
+    k_tril_copy<<<nb, 256, 0, st>>>(G, w.V, n);            // V = R (column-major)
+    k_transpose<<<tg, tb, 0, st>>>(w.V, w.lu, n);          // lu0 = R row-major
+    k_transpose<<<tg, tb, 0, st>>>(VT, w.lu + 2 * nn, n);  // lu2 = VT^T column-major
+    trsm<true>(w.lu, w.lu + 2 * nn, w.lu + nn, n, st1, st);  // lu1 = Q^T
+    k_transpose<<<tg, tb, 0, st>>>(w.lu + nn, VT, n);      // VT = Q
+  }
+  // 6. V = Q_house VT (all reflectors, warp per column)
+  {
+    int wpb = col_warps(n);
+    size_t smem = (size_t)wpb * n * sizeof(double);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+    k_backtransform<<<(n + wpb - 1) / wpb, wpb * 32, smem, st>>>(w.A, VT, n);
+  }
+  // 7. Z = L^-T V; sign convention; NaN check
+  trsm<false>(w.L, VT, Z, n, st0, st);
+  k_fix_signs<<<(n * 32 + 255) / 256, 256, 0, st>>>(Z, n, lam, st0);
+  return cudaGetLastError();
+}
+
+}  // namespace sparc

@@ -1,0 +1,151 @@
+// Internal declarations shared by the CUDA translation units of libsparc.so.
+// Nothing here is part of the public C ABI (see include/sparc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sparc.h"
+
+namespace sparc {
+
+constexpr int kRadius = 6;  // 12th-order central FD Laplacian (radius 6)
+
+struct Grid {
+  int nx, ny, nz;
+  int bc[3];  // SPARC_PERIODIC / SPARC_DIRICHLET
+};
+
+// -1/2 Laplacian coefficients: diag = -1/2 * 3 w0 / h^2, off[p] = -1/2 w_p / h^2.
+struct LapCoef {
+  double diag;
+  double off[kRadius + 1];  // off[0] unused
+};
+
+// Nonlocal tables on the device.
+//  Gather form (per atom): support indices and the n_supp x nproj chi block,
+//  used to form D[n][k] = gamma_k h^3 sum_s chi[s][k] x[idx_s] for all
+//  projectors k (global numbering proj_ptr[J] + q).
+//  Pull form (per grid point i): entries pull_ptr[i]..pull_ptr[i+1]-1 hold
+//  (k, chi_k(i)) so that (V_nl x)_i = sum_e chi_e D[k_e].
+template <typename T>
+struct Nonlocal {
+  int natoms = 0;
+  int kp = 0;  // total projector count
+  const int64_t* supp_ptr = nullptr;
+  const int* supp_idx = nullptr;
+  const int* nproj = nullptr;
+  const int64_t* chi_ptr = nullptr;
+  const T* chi = nullptr;
+  const int* proj_ptr = nullptr;  // int32 copy of proj_ptr
+  const double* gamma = nullptr;
+  const int* pull_ptr = nullptr;
+  const int* pull_k = nullptr;
+  const T* pull_chi = nullptr;
+};
+
+// Launchers (stencil.cu) -------------------------------------------------
+// y = s_h * ((H - shift) x) + s_p * prev   (prev may be null: s_p ignored)
+// with D the nonlocal coefficients of x (computed by nl_coefficients).
+template <typename T>
+cudaError_t apply_h(const Grid& g, const LapCoef& lc, const T* veff, const Nonlocal<T>& nl,
+                    const T* D, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
+                    int64_t ldp, int ns, double shift, double s_h, double s_p,
+                    cudaStream_t st);
+
+// D[n * kp + k] = gamma_k h^3 sum_s chi[s][k] x[idx_s + n ldx]
+template <typename T>
+cudaError_t nl_coefficients(const Nonlocal<T>& nl, double h3, const T* x, int64_t ldx, int ns,
+                            T* D, cudaStream_t st);
+
+// Small vector kernels (stencil.cu): deterministic two-pass reductions.
+cudaError_t dot_f64(const double* u, const double* v, int64_t n, double* partial, double* out,
+                    cudaStream_t st);
+cudaError_t fill_uniform_f64(double* v, int64_t n, uint64_t seed, cudaStream_t st);
+cudaError_t lanczos_update(double* w, const double* v, double* vp, const double* alpha_beta,
+                           int j, int64_t n, cudaStream_t st);
+cudaError_t lanczos_normalize(double* v, double* w, double* vp, double* alpha_beta, int j,
+                              int64_t n, double* partial, cudaStream_t st);
+cudaError_t lanczos_bounds(const double* alpha_beta, int k, double* out2, cudaStream_t st);
+template <typename T>
+cudaError_t copy_block(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t nd, int ns,
+                       cudaStream_t st);
+
+// Dense FP64 kernels (dense.cu) -------------------------------------------
+// Hs = Xt^T Yt, Ms = Xt^T Xt (upper tiles + mirror), split-K with a
+// deterministic reduction.  `work` holds nsplit * ns * ns * 2 doubles.
+template <typename T>
+cudaError_t project_simt(const T* Xt, const T* Yt, int64_t ld, int64_t nd, int ns, double* Hs,
+                         double* Ms, double* work, int nsplit, cudaStream_t st);
+int project_nsplit(int64_t nd, int ns);
+// Xout = Xt Z (Z column-major ns x ns)
+template <typename T>
+cudaError_t rotate_simt(const T* Xt, int64_t ld, int64_t nd, int ns, const double* Z, T* Xout,
+                        int64_t ldo, cudaStream_t st);
+
+// Generalised symmetric eigensolver workspace and driver (eig.cu).
+struct EigWork {
+  int nmax = 0;
+  double* L = nullptr;     // Cholesky factor (col-major)
+  double* A = nullptr;     // reduced matrix / Householder vectors (row-major)
+  double* W = nullptr;     // scratch n x n
+  double* V = nullptr;     // eigenvectors of T then of A (row-major)
+  double* d = nullptr;     // tridiagonal diagonal
+  double* e = nullptr;     // tridiagonal off-diagonal
+  double* tau = nullptr;   // Householder scalars
+  double* lu = nullptr;    // inverse-iteration factors (4 n x n)
+  double* scal = nullptr;  // small scalars
+  int* status = nullptr;   // device status word
+  int* clus = nullptr;     // cluster bookkeeping (2 n ints)
+  int* piv = nullptr;      // inverse-iteration pivot flags (n x n ints)
+};
+cudaError_t eig_alloc(EigWork& w, int nmax);
+void eig_free(EigWork& w);
+// lam ascending, Z column-major with Z^T M Z = I. Writes *dev_status (device).
+cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, double* lam, double* Z,
+                    cudaStream_t st);
+
+}  // namespace sparc
+
+// Handle ------------------------------------------------------------------
+struct sparc_context {
+  int device = 0;
+  sparc::Grid grid{};
+  double h = 0.0;
+  int64_t nd = 0, ld = 0;  // internal leading dimension (padded)
+  int precision = SPARC_PREC_FP64;
+  int ns_max = 1;
+  sparc::LapCoef lap{};
+  // potentials
+  double* veff64 = nullptr;
+  float* veff32 = nullptr;
+  // nonlocal tables
+  sparc::Nonlocal<double> nl64;
+  sparc::Nonlocal<float> nl32;
+  void* nl_mem[16] = {};
+  int nl_nmem = 0;
+  // workspaces
+  void* W1 = nullptr;
+  void* W2 = nullptr;
+  void* Wstage = nullptr;  // host-pointer staging (lazy)
+  void* D = nullptr;       // nonlocal coefficients kp x ns_max
+  double* Hs = nullptr;
+  double* Ms = nullptr;
+  double* Z = nullptr;
+  double* lam = nullptr;
+  double* proj_work = nullptr;
+  int64_t proj_work_elems = 0;
+  sparc::EigWork eig;
+  // Lanczos
+  double* lz = nullptr;  // 3 vectors + coefficients + partials
+  bool have_bounds = false;
+  double a0 = 0.0, b = 0.0;
+  bool have_prev = false;
+  double prev_max = 0.0;
+  // timings
+  cudaEvent_t ev[7] = {};
+  bool timed = false;
+  std::string err;
+};
