@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Benchmark of one CheFSI step (Algorithm 1 of arXiv 2302.09708) on GB300.
+
+Workload (default): the 96^3 periodic bulk system, h = 0.4 bohr, 216 atoms on a
+jittered simple-cubic lattice, Ns = 1300 orbitals, Chebyshev degree 20, FP64,
+seeded synthetic inputs (Gaussian Veff, Gaussian x real-Y_lm KB projectors,
+orthonormal random X0).  A "step" is one full CheFSI pass: filter, Yt = H Xt,
+projection, subspace eigensolve, rotation, with library-chosen bounds (cached
+Lanczos, cut-off = previous largest Ritz value).  The orbital block (9.2 GB)
+is far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CheFSI step time & Hpsi GB/s; mixed-FP32/batched vs FP64 speedup at <=1e-6 Ha"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 pipe of GB300: 2 FP64 FMA per SM per clock (4 FLOP), 152 SMs, 2070 MHz max.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", type=int, default=2)
+    p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=20.0)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, dev):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU oracle sample (baseline and reference arm)
+# --------------------------------------------------------------------------
+def oracle_sample(system, ns, degree, budget_s):
+    """Time the CPU oracle on a bounded sample of one CheFSI step and
+    extrapolate to the full step by each stage's scaling in Ns (filter and
+    H Xt ~ Ns, projection and rotation ~ Ns^2, eigensolve ~ Ns^3)."""
+    import numpy as np
+
+    import oracle
+    from paper_2302_09708_gb300 import synth
+
+    cores = len(os.sched_getaffinity(0))
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    o = oracle.Oracle(system)
+    nd = system.nd
+    t0 = time.perf_counter()
+    a0, b, *_ = o.lanczos(8, 0)
+    a = a0 + 0.1 * (b - a0)
+    # filter + one H application on `cores` columns (one per thread), scaled by
+    # the number of such column batches in Ns
+    deg_s = max(1, min(degree, int(budget_s)))  # keep the sample bounded
+    nc = cores
+    Xs = synth.random_orbitals(nd, nc, seed=1)
+    t = time.perf_counter()
+    o.cheb_filter(Xs, deg_s, a, b, a0)
+    t_deg = (time.perf_counter() - t) / deg_s
+    batches = math.ceil(ns / nc)
+    t_filter = t_deg * (degree + 1) * batches
+    # projection and rotation on a 64-column panel
+    p = min(64, ns)
+    Xp = np.random.default_rng(2).standard_normal((p, nd))
+    t = time.perf_counter()
+    oracle.project(Xp, Xp, nd)
+    t_proj = (time.perf_counter() - t) * (ns / p) ** 2
+    Zp = np.random.default_rng(3).standard_normal((p, p))
+    t = time.perf_counter()
+    oracle.rotate(Xp, Zp, nd)
+    t_rot = (time.perf_counter() - t) * (ns / p) ** 2
+    q = min(ns, 200)
+    A = np.random.default_rng(4).standard_normal((q, q))
+    M = A @ A.T + q * np.eye(q)
+    t = time.perf_counter()
+    oracle.gen_eig(0.5 * (A + A.T), M)
+    t_eig = (time.perf_counter() - t) * (ns / q) ** 3
+    total = t_filter + t_proj + t_rot + t_eig
+    sample = (f"oracle on {cores} host cores: {deg_s} filter degrees on {nc} of {ns} columns "
+              f"(scaled x{degree + 1}/{deg_s} x{batches}), projection and rotation on a {p}-column "
+              f"panel (scaled x(Ns/{p})^2), eigensolve at Ns={q} (scaled x(Ns/{q})^3)")
+    return {"step_s": total, "cores": cores, "sample": sample,
+            "parts_s": {"filter_hx": t_filter, "project": t_proj, "rotate": t_rot,
+                        "eig": t_eig}, "wall_s": time.perf_counter() - t0}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    from paper_2302_09708_gb300 import synth
+
+    cfg = synth.CONFIGS[2 if args.config == 3 else args.config]
+    system = synth.make_config_system(args.config)
+    ns, m = cfg["ns"], cfg["degree"]
+    budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    times = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(system, ns, m, budget)
+        if i >= args.warmup:
+            times.append(r["step_s"])
+        last = r
+    step_s = statistics.mean(times) if times else last["step_s"]
+    value = 1.0 / step_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "precision": "fp64", "l2": "inputs > L2"},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": last["cores"],
+                         "kind": "oracle", "sample": last["sample"]},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_2302_09708_gb300 import sparc, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sparc.load()
+    cfg = synth.CONFIGS[2 if args.config == 3 else args.config]
+    system = synth.make_config_system(args.config)
+    ns, m = cfg["ns"], cfg["degree"]
+    nd = system.nd
+    seed = synth.config_seed(args.config) + rank
+    t_setup = time.perf_counter()
+    X0 = synth.random_orbitals(nd, ns, seed=seed)
+    setup_s = time.perf_counter() - t_setup
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- FP64 (headline) ------------------------------------------------
+    h = sparc.Handle(system, "fp64", ns_max=ns, device=local)
+    Xd = torch.from_numpy(X0).to(dev)
+    lam_hist = []
+    for _ in range(args.warmup):
+        lam_hist.append(h.chefsi_step(Xd, m))
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    stage = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            lam_hist.append(h.chefsi_step(Xd, m))
+            stage.append(h.timings())
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    t_loc = e0.elapsed_time(e1) / 1e3
+    t_max = max_over_ranks(t_loc, world, dev)
+    value = world * args.steps / t_max
+    launches = int(sum(s["launches"] for s in stage))
+
+    def med(key):
+        return statistics.median(s[key] for s in stage)
+
+    st_ms = {k: med(k) for k in ("bounds_ms", "filter_ms", "hx_ms", "project_ms", "eig_ms",
+                                 "rotate_ms", "total_ms")}
+    # filtering throughput: per degree reads Y_i, Y_{i-1}, writes Y_{i+1}
+    # (first degree: read X, write Y_1) -> (2 + 3 (m - 1)) Nd Ns s bytes
+    s_bytes = 8
+    filt_bytes = (2 + 3 * (m - 1)) * nd * ns * s_bytes
+    hx_bytes = 2 * nd * ns * s_bytes
+    filt_gbs = filt_bytes / (st_ms["filter_ms"] / 1e3) / 1e9
+    hx_gbs = hx_bytes / (st_ms["hx_ms"] / 1e3) / 1e9
+    proj_flops = 2.0 * nd * ns * ns  # Hs and Ms as symmetric halves
+    rot_flops = 2.0 * nd * ns * ns
+    stage_rate = {
+        "filter": {"ms": st_ms["filter_ms"], "GB/s": filt_gbs},
+        "hx": {"ms": st_ms["hx_ms"], "GB/s": hx_gbs},
+        "project": {"ms": st_ms["project_ms"],
+                    "TFLOP/s": proj_flops / (st_ms["project_ms"] / 1e3) / 1e12},
+        "eig": {"ms": st_ms["eig_ms"]},
+        "rotate": {"ms": st_ms["rotate_ms"],
+                   "TFLOP/s": rot_flops / (st_ms["rotate_ms"] / 1e3) / 1e12},
+    }
+    # dominant kernel roofline (FP64 path: the FP64 pipe is the binding roof)
+    dom = max(("filter", "project", "rotate"), key=lambda k: stage_rate[k]["ms"])
+    pk = peaks()
+    if dom == "filter":
+        # K1 per degree: 48 FP64 flops per point per orbital (symmetric pair sums)
+        flops = 48.0 * nd * ns * m
+        ach = flops / (st_ms["filter_ms"] / 1e3) / 1e12
+        roof = {"kernel": "k_apply_h<double> (fused stencil+Veff+nonlocal+recurrence)",
+                "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    else:
+        ms_ = st_ms[dom + "_ms"]
+        ach = (proj_flops if dom == "project" else rot_flops) / (ms_ / 1e3) / 1e12
+        roof = {"kernel": "k_project_partial<double>" if dom == "project" else "k_rotate<double>",
+                "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["peak_source"] = "derived: 152 SMs x 4 FP64 FLOP/clk x 2.07 GHz (FP64 pipe)"
+    roof["traffic"] = None
+    roof["hbm_frac_filter"] = filt_gbs / pk.get("hbm_gbs", 6674.5)
+
+    clocks = clk.summary()
+
+    # ---- e2e through host buffers ----------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty((ns, nd), dtype=torch.float64, pin_memory=True)
+        Xh.copy_(torch.from_numpy(X0))
+        Xn = Xh.numpy()
+        he = sparc.Handle(system, "fp64", ns_max=ns, device=local)
+        he.chefsi_step(Xn, m)  # warm (Lanczos, staging buffer)
+        Xh.copy_(torch.from_numpy(X0))
+        ke = max(1, min(args.steps, 2))
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        for _ in range(ke):
+            he.chefsi_step(Xn, m)
+        te = time.perf_counter() - t
+        te = max_over_ranks(te, world, dev)
+        e2e = {"value": world * ke / te, "unit": "steps/s",
+               "h2d_bytes_per_step": nd * ns * 8, "d2h_bytes_per_step": nd * ns * 8 + ns * 8}
+        he.close()
+        del Xh, Xn
+
+    # ---- mixed precision on the same system ---------------------------------
+    mixed = None
+    if not args.no_mixed:
+        try:
+            mixed = run_mixed(system, X0, ns, m, args, dev, stream, h)
+        except Exception as exc:  # report, do not hide
+            mixed = {"error": repr(exc)}
+    h.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        r = oracle_sample(system, ns, m, args.cpu_seconds)
+        cpu = {"value": 1.0 / r["step_s"], "unit": "steps/s", "cores": r["cores"],
+               "kind": "oracle", "sample": r["sample"], "extrapolated_step_s": r["step_s"],
+               "parts_s": r["parts_s"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "precision": "fp64", "grid": list(system.shape),
+                   "h": system.h, "natoms": system.natoms, "ns": ns, "degree": m,
+                   "l2": "inputs larger than L2 (9.2 GB block)", "bounds": "library (Lanczos 32, "
+                   "cut-off = previous max Ritz value)", "parallelism": f"replicas x{world}"},
+        "stages": stage_rate,
+        "hpsi_gbs": hx_gbs,
+        "roofline": roof,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "mixed": mixed,
+        "cpu_baseline": cpu,
+        "setup_s": setup_s,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_mixed(system, X0, ns, m, args, dev, stream, h64):
+    """Mixed precision (FP32 orbitals and filtering) on the same system: time
+    per step and Ritz-value error against the FP64 GPU path (itself checked
+    against the oracle by the test suite) from the same start and bounds."""
+    import numpy as np
+    import torch
+
+    from paper_2302_09708_gb300 import sparc
+
+    a0, b = h64.spectrum_bounds(32, 0)
+    hm = sparc.Handle(system, "mixed", ns_max=ns, device=dev.index)
+    X32 = torch.from_numpy(X0).to(dev, torch.float32)
+    X64 = torch.from_numpy(X0).to(dev)
+    nsteps = 3
+    a = a0 + 0.1 * (b - a0)
+    errs = []
+    lam64 = lam32 = None
+    for s in range(nsteps):
+        lam64 = h64.chefsi_step(X64, m, bounds=(a, b, a0))
+        lam32 = hm.chefsi_step(X32, m, bounds=(a, b, a0))
+        errs.append(float(np.max(np.abs(lam64 - lam32))))
+        a = float(lam64[-1])
+    # occupied-state error (Ne = 2 round((Ns - 5)/1.2), Fermi-Dirac kT = 0.01 Ha)
+    from paper_2302_09708_gb300 import synth
+    ne = synth.electrons_for(ns)
+    occ = np.arange(ns) < ne // 2 + 8
+    err_occ = float(np.max(np.abs(lam64 - lam32)[occ]))
+    # timing
+    for _ in range(max(0, args.warmup - nsteps)):
+        hm.chefsi_step(X32, m)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stage = []
+    for _ in range(args.steps):
+        hm.chefsi_step(X32, m)
+        stage.append(hm.timings())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    st = {k: statistics.median(x[k] for x in stage) for k in stage[0] if k != "launches"}
+    filt_bytes = (2 + 3 * (m - 1)) * system.nd * ns * 4
+    hm.close()
+    return {"ms_per_step": t * 1e3, "stage_ms": st,
+            "filter_GBps": filt_bytes / (st["filter_ms"] / 1e3) / 1e9,
+            "ritz_err_vs_fp64_gpu_per_step": errs, "ritz_err_occupied": err_occ,
+            "note": "errors vs the FP64 GPU path from the same start and bounds"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -95,9 +95,11 @@ typedef struct {
   int reserved[5];
 } sparc_options;
 
-/* Stage times (ms) of the last sparc_chefsi_step on the handle (CUDA events). */
+/* Stage times (ms) of the last sparc_chefsi_step on the handle (CUDA events)
+ * and the number of library kernels it launched. */
 typedef struct {
   float bounds_ms, filter_ms, hx_ms, project_ms, eig_ms, rotate_ms, total_ms;
+  int64_t launches;
 } sparc_timings;
 
 /*

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -16,6 +17,13 @@
 #include "internal.cuh"
 
 using namespace sparc;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void sparc::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long sparc::launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -556,6 +564,7 @@ int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   ARG(c, degree >= 1 && degree <= 1000, "degree must be in [1, 1000]");
   CK(c, cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
+  const long long launches0 = launch_count();
   CK(c, cudaEventRecord(c->ev[0], st));
   double a, b, a0;
   if (bounds) {
@@ -584,6 +593,7 @@ int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   else
     rc = do_step<float>(c, (float*)Xd, ldd, ns, degree, a, b, a0, eig, eig_on_host, st);
   if (rc) return rc;
+  c->step_launches = launch_count() - launches0;
   if (host) return stage_out(c, X, ns, ld, dtype, st);
   return SPARC_OK;
 }
@@ -601,6 +611,7 @@ int sparc_get_timings(sparc_handle c, sparc_timings* t) {
   t->eig_ms = ms[4];
   t->rotate_ms = ms[5];
   CK(c, cudaEventElapsedTime(&t->total_ms, c->ev[0], c->ev[6]));
+  t->launches = c->step_launches;
   return SPARC_OK;
 }
 

@@ -184,10 +184,10 @@ cudaError_t project_simt(const T* Xt, const T* Yt, int64_t ld, int64_t nd, int n
   int tiles = nb * (nb + 1) / 2;
   int64_t kchunk = (nd + nsplit - 1) / nsplit;
   kchunk = (kchunk + kK - 1) / kK * kK;
-  k_project_partial<T><<<dim3(tiles, nsplit), kThreads, 0, st>>>(Xt, Yt, ld, nd, ns, kchunk, work);
+  note_launch(), k_project_partial<T><<<dim3(tiles, nsplit), kThreads, 0, st>>>(Xt, Yt, ld, nd, ns, kchunk, work);
   int64_t nn = (int64_t)ns * ns;
   int blocks = (int)std::min<int64_t>((nn + 255) / 256, 4096);
-  k_project_reduce<<<blocks, 256, 0, st>>>(work, nsplit, ns, Hs, Ms);
+  note_launch(), k_project_reduce<<<blocks, 256, 0, st>>>(work, nsplit, ns, Hs, Ms);
   return cudaGetLastError();
 }
 
@@ -195,7 +195,7 @@ template <typename T>
 cudaError_t rotate_simt(const T* Xt, int64_t ld, int64_t nd, int ns, const double* Z, T* Xout,
                         int64_t ldo, cudaStream_t st) {
   dim3 grid((unsigned)((nd + kT - 1) / kT), (ns + kT - 1) / kT);
-  k_rotate<T><<<grid, kThreads, 0, st>>>(Xt, ld, nd, ns, Z, Xout, ldo);
+  note_launch(), k_rotate<T><<<grid, kThreads, 0, st>>>(Xt, ld, nd, ns, Z, Xout, ldo);
   return cudaGetLastError();
 }
 

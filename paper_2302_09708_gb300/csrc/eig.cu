@@ -564,12 +564,12 @@ __global__ void k_fix_signs(double* Z, int n, const double* lam, int* status) {
 cudaError_t cholesky(double* A, int n, int* status, cudaStream_t st) {
   for (int j0 = 0; j0 < n; j0 += kNb) {
     int jb = min(kNb, n - j0);
-    k_potrf_diag<<<1, kNb, 0, st>>>(A, n, j0, jb, status);
+    note_launch(), k_potrf_diag<<<1, kNb, 0, st>>>(A, n, j0, jb, status);
     int rem = n - j0 - jb;
     if (rem > 0) {
-      k_potrf_panel<<<(rem + 127) / 128, 128, 0, st>>>(A, n, j0, jb, status);
+      note_launch(), k_potrf_panel<<<(rem + 127) / 128, 128, 0, st>>>(A, n, j0, jb, status);
       int nt = (rem + 31) / 32;
-      k_potrf_update<<<dim3(nt, nt), 256, 0, st>>>(A, n, j0, jb, status);
+      note_launch(), k_potrf_update<<<dim3(nt, nt), 256, 0, st>>>(A, n, j0, jb, status);
     }
   }
   return cudaGetLastError();
@@ -589,7 +589,7 @@ cudaError_t trsm(const double* Lt, const double* B, double* X, int n, const int*
   size_t smem = (size_t)wpb * n * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_trsm<FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_trsm<FWD><<<(n + wpb - 1) / wpb, wpb * 32, smem, st>>>(Lt, B, X, n, n, status);
+  note_launch(), k_trsm<FWD><<<(n + wpb - 1) / wpb, wpb * 32, smem, st>>>(Lt, B, X, n, n, status);
   return cudaGetLastError();
 }
 
@@ -642,35 +642,35 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
   // 1. Ms = L L^T
   cudaMemcpyAsync(w.W, Ms, nn * 8, cudaMemcpyDeviceToDevice, st);
   cholesky(w.W, n, st0, st);
-  k_tril_copy<<<nb, 256, 0, st>>>(w.W, w.L, n);
-  k_transpose<<<tg, tb, 0, st>>>(w.L, w.V, n);  // V = L row-major (forward solves)
+  note_launch(), k_tril_copy<<<nb, 256, 0, st>>>(w.W, w.L, n);
+  note_launch(), k_transpose<<<tg, tb, 0, st>>>(w.L, w.V, n);  // V = L row-major (forward solves)
   // 2. A = sym(L^-1 (L^-1 Hs)^T)
   trsm<true>(w.V, Hs, w.W, n, st0, st);          // W = L^-1 Hs
-  k_transpose<<<tg, tb, 0, st>>>(w.W, w.A, n);  // A = W^T
+  note_launch(), k_transpose<<<tg, tb, 0, st>>>(w.W, w.A, n);  // A = W^T
   trsm<true>(w.V, w.A, w.W, n, st0, st);         // W = L^-1 W^T
-  k_symmetrize<<<nb, 256, 0, st>>>(w.W, w.A, n);
+  note_launch(), k_symmetrize<<<nb, 256, 0, st>>>(w.W, w.A, n);
   // 3. Householder tridiagonalisation; reflectors in the rows of Hv = lu[0, nn)
   double* Hv = w.lu;
   double* p = w.tau;
   for (int k = 0; k + 2 < n; ++k) {
-    k_house_vec<<<1, 256, 0, st>>>(w.A, Hv, w.d, w.e, n, k);
+    note_launch(), k_house_vec<<<1, 256, 0, st>>>(w.A, Hv, w.d, w.e, n, k);
     int m = n - k - 1;
-    k_house_matvec<<<(m + 7) / 8, 256, 0, st>>>(w.A, Hv, p, n, k);
+    note_launch(), k_house_matvec<<<(m + 7) / 8, 256, 0, st>>>(w.A, Hv, p, n, k);
     int ub = (int)std::min<int64_t>(((int64_t)m * m + 255) / 256, 1024);
-    k_house_update<<<ub, 256, 0, st>>>(w.A, Hv, p, n, k);
+    note_launch(), k_house_update<<<ub, 256, 0, st>>>(w.A, Hv, p, n, k);
   }
-  k_house_tail<<<1, 32, 0, st>>>(w.A, Hv, w.d, w.e, n);
+  note_launch(), k_house_tail<<<1, 32, 0, st>>>(w.A, Hv, w.d, w.e, n);
   cudaMemcpyAsync(w.A, Hv, nn * 8, cudaMemcpyDeviceToDevice, st);  // reflectors -> A
   // 4. eigenvalues of T (ascending)
   double* e2 = w.tau + n;
-  k_gersh<<<1, 1024, 0, st>>>(w.d, w.e, n, e2, w.scal);
-  k_bisect<<<(n + 31) / 32, 32, 0, st>>>(w.d, e2, n, w.scal, lam);
+  note_launch(), k_gersh<<<1, 1024, 0, st>>>(w.d, w.e, n, e2, w.scal);
+  note_launch(), k_bisect<<<(n + 31) / 32, 32, 0, st>>>(w.d, e2, n, w.scal, lam);
   // 5. eigenvectors of T into W (column-major); factors in lu (4 n x n)
-  k_clusters<<<1, 32, 0, st>>>(lam, n, w.scal, w.clus);
+  note_launch(), k_clusters<<<1, 32, 0, st>>>(lam, n, w.scal, w.clus);
   double* VT = w.W;
-  k_inviter_single<<<(n + 31) / 32, 32, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv,
+  note_launch(), k_inviter_single<<<(n + 31) / 32, 32, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv,
                                                  VT);
-  k_inviter_cluster<<<n, 256, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv, VT);
+  note_launch(), k_inviter_cluster<<<n, 256, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv, VT);
   //    Cholesky-QR pass: G = VT^T VT = R R^T, Q = VT R^-T  (Q^T = R^-1 VT^T)
   {
     double* G1 = w.lu;           // unused copy (projection writes two outputs)
@@ -678,11 +678,11 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
     double* work = w.lu + 2 * nn;  // 2 nn doubles for one split
     project_simt<double>(VT, VT, n, n, n, G1, G, work, 1, st);
     cholesky(G, n, st1, st);
-    k_tril_copy<<<nb, 256, 0, st>>>(G, w.V, n);            // V = R (column-major)
-    k_transpose<<<tg, tb, 0, st>>>(w.V, w.lu, n);          // lu0 = R row-major
-    k_transpose<<<tg, tb, 0, st>>>(VT, w.lu + 2 * nn, n);  // lu2 = VT^T column-major
+    note_launch(), k_tril_copy<<<nb, 256, 0, st>>>(G, w.V, n);            // V = R (column-major)
+    note_launch(), k_transpose<<<tg, tb, 0, st>>>(w.V, w.lu, n);          // lu0 = R row-major
+    note_launch(), k_transpose<<<tg, tb, 0, st>>>(VT, w.lu + 2 * nn, n);  // lu2 = VT^T column-major
     trsm<true>(w.lu, w.lu + 2 * nn, w.lu + nn, n, st1, st);  // lu1 = Q^T
-    k_transpose<<<tg, tb, 0, st>>>(w.lu + nn, VT, n);      // VT = Q
+    note_launch(), k_transpose<<<tg, tb, 0, st>>>(w.lu + nn, VT, n);      // VT = Q
   }
   // 6. V = Q_house VT (all reflectors, warp per column)
   {
@@ -691,11 +691,11 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-    k_backtransform<<<(n + wpb - 1) / wpb, wpb * 32, smem, st>>>(w.A, VT, n);
+    note_launch(), k_backtransform<<<(n + wpb - 1) / wpb, wpb * 32, smem, st>>>(w.A, VT, n);
   }
   // 7. Z = L^-T V; sign convention; NaN check
   trsm<false>(w.L, VT, Z, n, st0, st);
-  k_fix_signs<<<(n * 32 + 255) / 256, 256, 0, st>>>(Z, n, lam, st0);
+  note_launch(), k_fix_signs<<<(n * 32 + 255) / 256, 256, 0, st>>>(Z, n, lam, st0);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,10 @@
 
 namespace sparc {
 
+// Counts kernel launches made by the library (host side, every launch site).
+void note_launch();
+long long launch_count();
+
 constexpr int kRadius = 6;  // 12th-order central FD Laplacian (radius 6)
 
 struct Grid {
@@ -147,5 +151,6 @@ struct sparc_context {
   // timings
   cudaEvent_t ev[7] = {};
   bool timed = false;
+  long long step_launches = 0;
   std::string err;
 };

@@ -290,9 +290,9 @@ cudaError_t apply_h(const Grid& g, const LapCoef& lc, const T* veff, const Nonlo
                    (!prev || (uintptr_t)prev % (C::VX * sizeof(T)) == 0) &&
                    ((uintptr_t)veff % (C::VX * sizeof(T)) == 0);
   if (vec)
-    k_apply_h<T, C::VX, C::BX, C::BY, true><<<grid, block, 0, st>>>(a);
+    note_launch(), k_apply_h<T, C::VX, C::BX, C::BY, true><<<grid, block, 0, st>>>(a);
   else
-    k_apply_h<T, C::VX, C::BX, C::BY, false><<<grid, block, 0, st>>>(a);
+    note_launch(), k_apply_h<T, C::VX, C::BX, C::BY, false><<<grid, block, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -370,7 +370,7 @@ cudaError_t nl_coefficients(const Nonlocal<T>& nl, double h3, const T* x, int64_
                             T* D, cudaStream_t st) {
   if (nl.natoms == 0 || nl.kp == 0) return cudaSuccess;
   dim3 grid(nl.natoms, (ns + kNlOrb - 1) / kNlOrb);
-  k_nl_coef<T><<<grid, kNlThreads, 0, st>>>(nl, h3, x, ldx, ns, D);
+  note_launch(), k_nl_coef<T><<<grid, kNlThreads, 0, st>>>(nl, h3, x, ldx, ns, D);
   return cudaGetLastError();
 }
 
@@ -397,7 +397,7 @@ template <typename T>
 cudaError_t copy_block(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t nd, int ns,
                        cudaStream_t st) {
   int bx = (int)std::min<int64_t>((nd + 255) / 256, 1024);
-  k_copy_block<T><<<dim3(bx, ns), 256, 0, st>>>(src, lds, dst, ldd, nd);
+  note_launch(), k_copy_block<T><<<dim3(bx, ns), 256, 0, st>>>(src, lds, dst, ldd, nd);
   return cudaGetLastError();
 }
 template cudaError_t copy_block<double>(const double*, int64_t, double*, int64_t, int64_t, int,
@@ -536,20 +536,20 @@ int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 2048); 
 
 cudaError_t dot_f64(const double* u, const double* v, int64_t n, double* partial, double* out,
                     cudaStream_t st) {
-  k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(u, v, n, partial);
-  k_sum_partials<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, out, 0);
+  note_launch(), k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(u, v, n, partial);
+  note_launch(), k_sum_partials<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, out, 0);
   return cudaGetLastError();
 }
 
 cudaError_t fill_uniform_f64(double* v, int64_t n, uint64_t seed, cudaStream_t st) {
-  k_fill_uniform<<<grid_for(n), 256, 0, st>>>(v, n, seed);
+  note_launch(), k_fill_uniform<<<grid_for(n), 256, 0, st>>>(v, n, seed);
   return cudaGetLastError();
 }
 
 // w -= beta_{j-1} vp; alpha_j = w.v; w -= alpha_j v
 cudaError_t lanczos_update(double* w, const double* v, double* vp, const double* ab, int j,
                            int64_t n, cudaStream_t st) {
-  k_lz_sub_prev<<<grid_for(n), 256, 0, st>>>(w, vp, ab, j, n);
+  note_launch(), k_lz_sub_prev<<<grid_for(n), 256, 0, st>>>(w, vp, ab, j, n);
   return cudaGetLastError();
 }
 
@@ -558,22 +558,22 @@ cudaError_t lanczos_update(double* w, const double* v, double* vp, const double*
 cudaError_t lanczos_normalize(double* v, double* w, double* vp, double* ab, int j, int64_t n,
                               double* partial, cudaStream_t st) {
   if (j < 0) {
-    k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(v, v, n, partial);
-    k_sum_partials<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, partial + kRedBlocks, 1);
-    k_scale_inv<<<grid_for(n), 256, 0, st>>>(v, partial + kRedBlocks, n);
+    note_launch(), k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(v, v, n, partial);
+    note_launch(), k_sum_partials<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, partial + kRedBlocks, 1);
+    note_launch(), k_scale_inv<<<grid_for(n), 256, 0, st>>>(v, partial + kRedBlocks, n);
     return cudaGetLastError();
   }
-  k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(w, v, n, partial);
-  k_sum_partials<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, ab + 2 * j, 0);
-  k_lz_sub_alpha<<<grid_for(n), 256, 0, st>>>(w, v, ab, j, n);
-  k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(w, w, n, partial);
-  k_sum_partials<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, ab + 2 * j + 1, 1);
-  k_lz_shift<<<grid_for(n), 256, 0, st>>>(v, w, vp, ab, j, n);
+  note_launch(), k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(w, v, n, partial);
+  note_launch(), k_sum_partials<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, ab + 2 * j, 0);
+  note_launch(), k_lz_sub_alpha<<<grid_for(n), 256, 0, st>>>(w, v, ab, j, n);
+  note_launch(), k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(w, w, n, partial);
+  note_launch(), k_sum_partials<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, ab + 2 * j + 1, 1);
+  note_launch(), k_lz_shift<<<grid_for(n), 256, 0, st>>>(v, w, vp, ab, j, n);
   return cudaGetLastError();
 }
 
 cudaError_t lanczos_bounds(const double* ab, int k, double* out2, cudaStream_t st) {
-  k_lz_bounds<<<1, 32, 0, st>>>(ab, k, out2);
+  note_launch(), k_lz_bounds<<<1, 32, 0, st>>>(ab, k, out2);
   return cudaGetLastError();
 }
 

@@ -61,7 +61,7 @@ class sparc_options(ctypes.Structure):
 class sparc_timings(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in
                 ("bounds_ms", "filter_ms", "hx_ms", "project_ms", "eig_ms", "rotate_ms",
-                 "total_ms")]
+                 "total_ms")] + [("launches", ctypes.c_int64)]
 
 
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_hpsi",
