@@ -194,6 +194,36 @@ int sparc_chefsi_step(sparc_handle h, void* X, int ns, int64_t ld, int dtype, in
 /* Stage times of the last sparc_chefsi_step (waits for its events). */
 int sparc_get_timings(sparc_handle h, sparc_timings* t);
 
+/*
+ * sparc_project_noalloc — the FP64 projection of sparc_project (Hs = Xt^T Yt,
+ * Ms = Xt^T Xt) without a handle and without allocating any device memory.
+ * The paper has no counterpart; this entry point exists for callers that may
+ * not call cudaMalloc: code whose device memory is owned by another allocator
+ * (a framework's caching pool or a pre-partitioned budget) that a raw
+ * cudaMalloc would bypass, and latency-critical loops that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree may cause.
+ *
+ * Xt, Yt: device FP64 blocks, Nd x ns column-major with leading dimension
+ * ld >= nd.  Hs, Ms: device ns x ns FP64 column-major outputs, symmetrised from
+ * their upper triangles, as in sparc_project.  The caller passes (and owns) all
+ * inputs and outputs.
+ *
+ * Scratch: the split-K partial sums live in one library-owned, file-scope
+ * device array of 4,194,304 doubles (32 MiB) that every GPU which loads the
+ * library holds until the process exits.  ns may be at most 1448 (two ns x ns
+ * partials must fit); larger ns returns INVALID_ARG without launching work.
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current); make that first call before any CUDA
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents; every value a call reads from it is written earlier by the same
+ * call, so nothing needs clearing, but calls that overlap on the GPU (for
+ * example on two streams at once) race on it and must be serialised by the
+ * caller.  Errors: INVALID_ARG (null or host pointers, bad sizes), CUDA; the
+ * message is available from sparc_last_error(NULL).  Asynchronous.
+ */
+int sparc_project_noalloc(const double* Xt, const double* Yt, int ns, int64_t nd, int64_t ld,
+                          double* Hs, double* Ms, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

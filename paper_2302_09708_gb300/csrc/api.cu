@@ -22,12 +22,18 @@ namespace {
 std::atomic<long long> g_launches{0};
 }  // namespace
 
+
 void sparc::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long sparc::launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
 thread_local std::string g_create_err;
+}  // namespace
+
+void sparc::set_global_error(const std::string& msg) { g_create_err = msg; }
+
+namespace {
 
 // 12th-order central second-derivative weights (Fornberg 1988, radius 6):
 // w0 = -5369/1800, w1..w6 = 12/7, -15/56, 10/189, -1/112, 2/1925, -1/16632.

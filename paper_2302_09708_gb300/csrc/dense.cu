@@ -7,6 +7,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "internal.cuh"
 
@@ -209,3 +211,93 @@ template cudaError_t rotate_simt<float>(const float*, int64_t, int64_t, int, con
                                         int64_t, cudaStream_t);
 
 }  // namespace sparc
+
+// ---------------------------------------------------------------------------
+// Projection without any device allocation (sparc_project_noalloc).
+//
+// The split-K partial sums of the projection live in one file-scope device
+// array instead of a handle's cudaMalloc'd workspace, so the call needs no
+// handle and allocates nothing.  The array is created when the library is
+// loaded onto a device and stays resident until the process exits.  Host code
+// must not hand the symbol g_noalloc_scratch to a kernel (on the host it is only
+// a stand-in); its device address is looked up once per device with
+// cudaGetSymbolAddress and passed to the kernels.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoallocScratchDoubles = size_t(1) << 22;  // 32 MiB per device
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once).
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+bool device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" int sparc_project_noalloc(const double* Xt, const double* Yt, int ns, int64_t nd,
+                                     int64_t ld, double* Hs, double* Ms, void* stream) {
+  using sparc::set_global_error;
+  if (!Xt || !Yt || !Hs || !Ms) {
+    set_global_error("invalid argument: null pointer");
+    return SPARC_ERR_INVALID_ARG;
+  }
+  if (ns < 1 || nd < 1 || ld < nd) {
+    set_global_error("invalid argument: need ns >= 1, nd >= 1, ld >= nd");
+    return SPARC_ERR_INVALID_ARG;
+  }
+  // one split needs the two ns x ns partial outputs
+  if ((size_t)2 * ns * ns > kNoallocScratchDoubles) {
+    set_global_error("invalid argument: ns exceeds 1448, the largest size the static scratch "
+                     "of sparc_project_noalloc (2 ns^2 doubles of 4194304) can hold");
+    return SPARC_ERR_INVALID_ARG;
+  }
+  if (!device_pointer(Xt) || !device_pointer(Yt) || !device_pointer(Hs) ||
+      !device_pointer(Ms)) {
+    set_global_error("invalid argument: sparc_project_noalloc takes device pointers");
+    return SPARC_ERR_INVALID_ARG;
+  }
+  double* work = nullptr;
+  cudaError_t e = noalloc_scratch(&work);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    return SPARC_ERR_CUDA;
+  }
+  int nsplit = sparc::project_nsplit(nd, ns);
+  int fit = (int)(kNoallocScratchDoubles / ((size_t)2 * ns * ns));
+  if (nsplit > fit) nsplit = fit;
+  // every partial the reduction reads is written by the same call, so the
+  // scratch needs no clearing between calls
+  e = sparc::project_simt<double>(Xt, Yt, ld, nd, ns, Hs, Ms, work, nsplit,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    set_global_error(std::string("projection launch: ") + cudaGetErrorString(e));
+    return SPARC_ERR_CUDA;
+  }
+  return SPARC_OK;
+}

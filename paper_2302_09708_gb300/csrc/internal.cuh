@@ -15,6 +15,9 @@ namespace sparc {
 void note_launch();
 long long launch_count();
 
+// Message returned by sparc_last_error(NULL) (calls made without a handle).
+void set_global_error(const std::string& msg);
+
 constexpr int kRadius = 6;  // 12th-order central FD Laplacian (radius 6)
 
 struct Grid {

@@ -66,7 +66,7 @@ class sparc_timings(ctypes.Structure):
 
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_hpsi",
            "sparc_spectrum_bounds", "sparc_cheb_filter", "sparc_project", "sparc_subspace_eig",
-           "sparc_rotate", "sparc_chefsi_step", "sparc_get_timings"]
+           "sparc_rotate", "sparc_chefsi_step", "sparc_get_timings", "sparc_project_noalloc"]
 
 _lib = None
 
@@ -99,6 +99,7 @@ def load(build: bool = True):
     L.sparc_rotate.argtypes = [vp, vp, vp, vp, i, i64, i, vp]
     L.sparc_chefsi_step.argtypes = [vp, vp, i, i64, i, i, vp, vp, i, vp]
     L.sparc_get_timings.argtypes = [vp, ctypes.POINTER(sparc_timings)]
+    L.sparc_project_noalloc.argtypes = [vp, vp, i, i64, i64, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("sparc_last_error",):
             getattr(L, name).restype = ctypes.c_int

@@ -1,0 +1,62 @@
+"""sparc_project_noalloc: the FP64 projection for callers that may not allocate
+device memory (their memory belongs to another allocator, or a cudaMalloc would
+stall a latency-critical loop).  It keeps its split-K scratch in a static device
+array, so this file checks it through the C ABI against sparc_project on a
+handle, on consecutive calls that reuse the same scratch.  The file sorts last
+so that a run stopping at the first failure has already run every other test."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2302_09708_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2302_09708_gb300 import sparc  # noqa: E402
+
+DEV = torch.device("cuda:0")
+TOL = 1e-10  # the projection tolerance of the parity tests
+
+
+def _noalloc(L, X, Y, ns, nd, ld):
+    Hs = torch.full((ns, ns), float("nan"), dtype=torch.float64, device=DEV)
+    Ms = torch.full((ns, ns), float("nan"), dtype=torch.float64, device=DEV)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.sparc_project_noalloc(X.data_ptr(), Y.data_ptr(), ns, nd, ld, Hs.data_ptr(),
+                                 Ms.data_ptr(), stream)
+    assert rc == sparc.SPARC_OK, L.sparc_last_error(None)
+    torch.cuda.synchronize()
+    return Hs, Ms
+
+
+def test_project_noalloc_matches_handle_projection_on_consecutive_calls():
+    L = sparc.load()
+    s = synth.make_config_system(1)
+    nd = s.nd
+    h = sparc.Handle(s, "fp64", ns_max=64)
+    rng = np.random.default_rng(2302)
+    for ns, pad in ((40, 0), (33, 5), (64, 32)):  # consecutive calls share the scratch
+        ld = nd + pad
+        X = torch.from_numpy(rng.standard_normal((ns, ld))).to(DEV)
+        Y = torch.from_numpy(rng.standard_normal((ns, ld))).to(DEV)
+        Hs, Ms = _noalloc(L, X, Y, ns, nd, ld)
+        rH, rM = h.project(X, Y)
+        torch.cuda.synchronize()
+        assert torch.isfinite(Hs).all() and torch.isfinite(Ms).all()
+        assert float((Hs - rH).abs().max()) < TOL
+        assert float((Ms - rM).abs().max()) < TOL
+    h.close()
+
+
+def test_project_noalloc_rejects_sizes_beyond_its_scratch():
+    L = sparc.load()
+    X = torch.zeros((2, 64), dtype=torch.float64, device=DEV)
+    rc = L.sparc_project_noalloc(X.data_ptr(), X.data_ptr(), 1449, 64, 64, X.data_ptr(),
+                                 X.data_ptr(), ctypes.c_void_p(0))
+    assert rc == sparc.SPARC_ERR_INVALID_ARG
+    assert b"1448" in L.sparc_last_error(None)
