@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
+    p.add_argument("--ns", type=int, default=0, help="override Ns (profiling on a smaller case)")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                   help="precision of the timed (headline) run")
     return p.parse_args()
 
 
@@ -243,7 +246,7 @@ def main():
     sparc.load()
     cfg = synth.CONFIGS[2 if args.config == 3 else args.config]
     system = synth.make_config_system(args.config)
-    ns, m = cfg["ns"], cfg["degree"]
+    ns, m = (args.ns or cfg["ns"]), cfg["degree"]
     nd = system.nd
     seed = synth.config_seed(args.config) + rank
     t_setup = time.perf_counter()
@@ -251,9 +254,10 @@ def main():
     setup_s = time.perf_counter() - t_setup
     stream = torch.cuda.current_stream(dev)
 
-    # ---- FP64 (headline) ------------------------------------------------
-    h = sparc.Handle(system, "fp64", ns_max=ns, device=local)
-    Xd = torch.from_numpy(X0).to(dev)
+    # ---- headline run (FP64 unless --precision mixed) ------------------
+    prec = args.precision
+    h = sparc.Handle(system, prec, ns_max=ns, device=local)
+    Xd = torch.from_numpy(X0).to(dev, torch.float64 if prec == "fp64" else torch.float32)
     lam_hist = []
     for _ in range(args.warmup):
         lam_hist.append(h.chefsi_step(Xd, m))
@@ -282,7 +286,7 @@ def main():
                                  "rotate_ms", "total_ms")}
     # filtering throughput: per degree reads Y_i, Y_{i-1}, writes Y_{i+1}
     # (first degree: read X, write Y_1) -> (2 + 3 (m - 1)) Nd Ns s bytes
-    s_bytes = 8
+    s_bytes = 8 if prec == "fp64" else 4
     filt_bytes = (2 + 3 * (m - 1)) * nd * ns * s_bytes
     hx_bytes = 2 * nd * ns * s_bytes
     filt_gbs = filt_bytes / (st_ms["filter_ms"] / 1e3) / 1e9
@@ -321,7 +325,7 @@ def main():
 
     # ---- e2e through host buffers ----------------------------------------
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and prec == "fp64":
         Xh = torch.empty((ns, nd), dtype=torch.float64, pin_memory=True)
         Xh.copy_(torch.from_numpy(X0))
         Xn = Xh.numpy()
@@ -342,7 +346,7 @@ def main():
 
     # ---- mixed precision on the same system ---------------------------------
     mixed = None
-    if not args.no_mixed:
+    if not args.no_mixed and prec == "fp64":
         try:
             mixed = run_mixed(system, X0, ns, m, args, dev, stream, h)
         except Exception as exc:  # report, do not hide
@@ -359,9 +363,11 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f32",
         "data": "synthetic",
-        "config": {"workload": cfg["name"], "precision": "fp64", "grid": list(system.shape),
+        "config": {"workload": cfg["name"] + (f" (Ns overridden to {ns})" if args.ns else ""),
+                   "precision": prec, "grid": list(system.shape),
                    "h": system.h, "natoms": system.natoms, "ns": ns, "degree": m,
                    "l2": "inputs larger than L2 (9.2 GB block)", "bounds": "library (Lanczos 32, "
                    "cut-off = previous max Ritz value)", "parallelism": f"replicas x{world}"},

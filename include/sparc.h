@@ -25,7 +25,11 @@
  *    call says "device or host", a host pointer is copied through a library
  *    buffer inside the call.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
- *    enqueued on it; calls return without waiting unless stated.
+ *    enqueued on it; calls return without waiting unless stated.  Kernels that
+ *    wait on barriers bound every wait; if one runs out the kernel stops and
+ *    records SPARC_ERR_TIMEOUT, which the next synchronous call on the handle
+ *    (sparc_chefsi_step, sparc_subspace_eig, mixed-precision sparc_project /
+ *    sparc_rotate) returns.
  *  - All inputs given at create time are copied; the caller may free them.
  *  - The library owns its workspace (two Nd x ns_max blocks of the working
  *    precision plus the Ns x Ns subspace buffers), sized at create time.
@@ -92,7 +96,8 @@ typedef struct {
                     projection/rotation, FP64 bounds/Cholesky/eigensolve.      */
   int ns_max;    /* largest Ns passed to any call on this handle (>= 1)        */
   int device;    /* CUDA device ordinal                                        */
-  int reserved[5];
+  int reserved[5]; /* reserved[0] bit 0: use the generic stencil kernel instead
+                      of the TMA plane-ring form (for cross-checking); others 0 */
 } sparc_options;
 
 /* Stage times (ms) of the last sparc_chefsi_step on the handle (CUDA events)
@@ -193,6 +198,45 @@ int sparc_chefsi_step(sparc_handle h, void* X, int ns, int64_t ld, int dtype, in
 
 /* Stage times of the last sparc_chefsi_step (waits for its events). */
 int sparc_get_timings(sparc_handle h, sparc_timings* t);
+
+/*
+ * Batched form — many independent systems (the paper treats the eigenproblems
+ * of different k-points / spins / configurations as independent, Sec. II).
+ * A batch is built from existing handles (same precision and device; each keeps
+ * its own workspace).  One batched step runs Algorithm 1 on every member: each
+ * Chebyshev degree of all members is one launch of the nonlocal-coefficient
+ * kernel plus one launch of the stencil kernel; the Rayleigh-Ritz parts of the
+ * members run concurrently on library streams.  The whole step is captured as a
+ * CUDA graph on the first call and replayed on later calls with the same X
+ * pointers, ld, ns and degrees (otherwise it is re-captured).
+ */
+typedef struct sparc_batch_context* sparc_batch;
+
+/* sparc_batch_create — hs: n >= 1 handles (borrowed: they must outlive the
+ * batch).  Errors: INVALID_ARG, OOM, CUDA (message via sparc_last_error(NULL)). */
+int sparc_batch_create(const sparc_handle* hs, int n, sparc_batch* out);
+
+/* sparc_batch_destroy — frees the batch (not the handles); NULL is a no-op. */
+int sparc_batch_destroy(sparc_batch b);
+
+/* Last error message of a batch call. */
+const char* sparc_batch_last_error(sparc_batch b);
+
+/*
+ * sparc_batch_chefsi_step — one CheFSI step of every member i = 0..n-1.
+ * X[i]: device block of member i (dtype, ld[i] >= Nd_i), replaced by Xt Z.
+ * ns[i] must equal member i's ns_max.  degree[i] >= 1.  bounds: 3n host
+ * doubles {a, b, a0} per member, or NULL (library bounds per member as in
+ * sparc_chefsi_step).  eig: n host pointers to ns[i] doubles (ascending Ritz
+ * values), or NULL.  Synchronous.  Errors as sparc_chefsi_step; the failing
+ * member is named in the message.
+ */
+int sparc_batch_chefsi_step(sparc_batch b, void* const* X, const int* ns, const int64_t* ld,
+                            int dtype, const int* degree, const double* bounds,
+                            double* const* eig, void* stream);
+
+/* Kernel launches per batched step (nodes of the captured graph). */
+int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step);
 
 /*
  * sparc_project_noalloc — the FP64 projection of sparc_project (Hs = Xt^T Yt,

@@ -106,7 +106,7 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
   T* D = (T*)c->D;
   CK(c, nl_coefficients<T>(nl, c->h * c->h * c->h, x, ldx, ns, D, st));
   CK(c, apply_h<T>(c->grid, c->lap, veff, nl, D, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
-                   st));
+                   c->ring_enabled ? c->eig.status + 3 : nullptr, st));
   return SPARC_OK;
 }
 
@@ -170,7 +170,7 @@ int lanczos(sparc_context* c, int iters, uint64_t seed, double* a0, double* b, c
     CK(c, nl_coefficients<double>(nl, c->h * c->h * c->h, v, nd, 1, c->lz + 3 * nd + 1024 + 384,
                                   st));
     CK(c, apply_h<double>(c->grid, c->lap, c->veff64, nl, c->lz + 3 * nd + 1024 + 384, v, nd, w,
-                          nd, nullptr, 0, 1, 0.0, 1.0, 0.0, st));
+                          nd, nullptr, 0, 1, 0.0, 1.0, 0.0, nullptr, st));
     CK(c, lanczos_update(w, v, vp, ab, j, nd, st));
     CK(c, lanczos_normalize(v, w, vp, ab, j, nd, partial, st));
   }
@@ -188,9 +188,16 @@ int lanczos(sparc_context* c, int iters, uint64_t seed, double* a0, double* b, c
 }
 
 int read_status(sparc_context* c, cudaStream_t st) {
-  int hs[2] = {0, 0};
-  CK(c, cudaMemcpyAsync(hs, c->eig.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  int hs[5] = {0, 0, 0, 0, 0};
+  CK(c, cudaMemcpyAsync(hs, c->eig.status, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(c, cudaStreamSynchronize(st));
+  if (hs[2] == SPARC_ERR_TIMEOUT || hs[3] == SPARC_ERR_TIMEOUT || hs[4] == SPARC_ERR_TIMEOUT) {
+    c->err = hs[2] ? "a bounded wait in a tensor-core GEMM ran out"
+                   : hs[3] ? "a bounded wait in the TMA stencil ran out"
+                           : "a bounded grid barrier in the eigensolver ran out";
+    CK(c, cudaMemsetAsync(c->eig.status + 2, 0, 3 * sizeof(int), st));
+    return SPARC_ERR_TIMEOUT;
+  }
   if (hs[0] == SPARC_ERR_NOT_SPD) {
     c->err = "subspace overlap Ms is not positive definite";
     return SPARC_ERR_NOT_SPD;
@@ -210,8 +217,26 @@ int do_project(sparc_context* c, const T* Xt, int64_t ldx, const T* Yt, int64_t 
     c->err = "projection operands must share a leading dimension";
     return SPARC_ERR_INVALID_ARG;
   }
+  if (std::is_same<T, float>::value) {
+    int nsplit = tc_project_nsplit(ns);
+    CK(c, tc_project((const float*)Xt, (const float*)Yt, ldx, c->nd, ns, Hs, Ms, c->proj_work,
+                     nsplit, c->S1, c->S2, c->esc, c->eig.status + 2, st));
+    return SPARC_OK;
+  }
   int nsplit = project_nsplit(c->nd, ns);
   CK(c, project_simt<T>(Xt, Yt, ldx, c->nd, ns, Hs, Ms, c->proj_work, nsplit, st));
+  return SPARC_OK;
+}
+
+template <typename T>
+int do_rotate(sparc_context* c, const T* Xt, int64_t ldt, int ns, const double* Z, T* Xo,
+              int64_t ldo, cudaStream_t st) {
+  if (std::is_same<T, float>::value) {
+    CK(c, tc_rotate((const float*)Xt, ldt, c->nd, ns, Z, (float*)Xo, ldo, c->S1, c->SZ, c->esc,
+                    c->eig.status + 2, st));
+    return SPARC_OK;
+  }
+  CK(c, rotate_simt<T>(Xt, ldt, c->nd, ns, Z, Xo, ldo, st));
   return SPARC_OK;
 }
 
@@ -233,7 +258,8 @@ int do_step(sparc_context* c, T* X, int64_t ldx, int ns, int m, double a, double
   CK(c, cudaEventRecord(c->ev[4], st));
   CK(c, gen_eig(c->eig, c->Hs, c->Ms, ns, c->lam, c->Z, st));
   CK(c, cudaEventRecord(c->ev[5], st));
-  CK(c, rotate_simt<T>(Xt, ldt, c->nd, ns, c->Z, X, ldx, st));
+  rc = do_rotate<T>(c, Xt, ldt, ns, c->Z, X, ldx, st);
+  if (rc) return rc;
   CK(c, cudaEventRecord(c->ev[6], st));
   c->timed = true;
   rc = read_status(c, st);  // synchronises the stream
@@ -276,6 +302,7 @@ void destroy_ctx(sparc_context* c) {
   for (int i = 0; i < c->nl_nmem; ++i) cudaFree(c->nl_mem[i]);
   cudaFree(c->veff64); cudaFree(c->veff32);
   cudaFree(c->W1); cudaFree(c->W2); cudaFree(c->Wstage); cudaFree(c->D);
+  cudaFree(c->S1); cudaFree(c->S2); cudaFree(c->SZ); cudaFree(c->esc);
   cudaFree(c->Hs); cudaFree(c->Ms); cudaFree(c->Z); cudaFree(c->lam); cudaFree(c->proj_work);
   cudaFree(c->lz);
   eig_free(c->eig);
@@ -424,12 +451,25 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
   CK(c, cudaMalloc(&c->Z, nn * 8));
   CK(c, cudaMalloc(&c->lam, (size_t)c->ns_max * 8));
   int64_t pw = 0;
-  for (int n = 1; n <= c->ns_max; ++n)
+  for (int n = 1; n <= c->ns_max; ++n) {
     pw = std::max<int64_t>(pw, (int64_t)project_nsplit(nd, n) * 2 * n * n);
+    if (c->precision == SPARC_PREC_MIXED)
+      pw = std::max<int64_t>(pw, (int64_t)tc_project_nsplit(n) * 2 * n * n);
+  }
+  if (c->precision == SPARC_PREC_MIXED) {
+    const size_t se = tc_slice_elems(c->ld, nd, c->ns_max);
+    CK(c, cudaMalloc(&c->S1, se * sizeof(__nv_bfloat16)));
+    CK(c, cudaMalloc(&c->S2, se * sizeof(__nv_bfloat16)));
+    const size_t zk = (size_t)(c->ns_max + 7) / 8 * 8;
+    CK(c, cudaMalloc(&c->SZ, 4 * zk * c->ns_max * sizeof(__nv_bfloat16)));
+    CK(c, cudaMalloc(&c->esc, (size_t)(nd + 2 * c->ns_max) * sizeof(int)));
+  }
   c->proj_work_elems = pw;
   CK(c, cudaMalloc(&c->proj_work, pw * 8));
   CK(c, cudaMalloc(&c->lz, ((size_t)3 * nd + 1024 + 384 + std::max(kp, 1)) * 8));
   CK(c, eig_alloc(c->eig, c->ns_max));
+  CK(c, cudaMemset(c->eig.status, 0, 16 * sizeof(int)));
+  c->ring_enabled = !(opt && (opt->reserved[0] & 1));
   for (auto& e : c->ev) CK(c, cudaEventCreate(&e));
   return SPARC_OK;
 }
@@ -476,6 +516,8 @@ int sparc_hpsi(sparc_handle c, const void* X, void* Y, int ns, int64_t ld, int d
   ARG(c, is_device_ptr(X) && is_device_ptr(Y), "hpsi takes device blocks");
   CK(c, cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
+  // a stencil wait that runs out is reported by the next call that reads status
+  CK(c, cudaMemsetAsync(c->eig.status + 3, 0, sizeof(int), st));
   if (dtype == SPARC_F64)
     return hstep<double>(c, (const double*)X, ld, (double*)Y, ld, nullptr, 0, ns, 0.0, 1.0, 0.0, st);
   return hstep<float>(c, (const float*)X, ld, (float*)Y, ld, nullptr, 0, ns, 0.0, 1.0, 0.0, st);
@@ -503,6 +545,7 @@ int sparc_cheb_filter(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   const bool host = !is_device_ptr(X);
   void* Xd = X;
   int64_t ldd = ld;
+  CK(c, cudaMemsetAsync(c->eig.status + 3, 0, sizeof(int), st));
   if (host && (rc = stage_in(c, X, ns, ld, dtype, &Xd, &ldd, st))) return rc;
   void* res;
   int64_t ldr;
@@ -533,7 +576,9 @@ int sparc_project(sparc_handle c, const void* Xt, const void* Yt, int ns, int64_
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == SPARC_F64)
     return do_project<double>(c, (const double*)Xt, ld, (const double*)Yt, ld, ns, Hs, Ms, st);
-  return do_project<float>(c, (const float*)Xt, ld, (const float*)Yt, ld, ns, Hs, Ms, st);
+  CK(c, cudaMemsetAsync(c->eig.status, 0, 3 * sizeof(int), st));
+  rc = do_project<float>(c, (const float*)Xt, ld, (const float*)Yt, ld, ns, Hs, Ms, st);
+  return rc ? rc : read_status(c, st);
 }
 
 int sparc_subspace_eig(sparc_handle c, const double* Hs, const double* Ms, int ns, double* lam,
@@ -556,10 +601,10 @@ int sparc_rotate(sparc_handle c, const void* Xt, void* Xout, const double* Z, in
   CK(c, cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == SPARC_F64)
-    CK(c, rotate_simt<double>((const double*)Xt, ld, c->nd, ns, Z, (double*)Xout, ld, st));
-  else
-    CK(c, rotate_simt<float>((const float*)Xt, ld, c->nd, ns, Z, (float*)Xout, ld, st));
-  return SPARC_OK;
+    return do_rotate<double>(c, (const double*)Xt, ld, ns, Z, (double*)Xout, ld, st);
+  CK(c, cudaMemsetAsync(c->eig.status, 0, 3 * sizeof(int), st));
+  rc = do_rotate<float>(c, (const float*)Xt, ld, ns, Z, (float*)Xout, ld, st);
+  return rc ? rc : read_status(c, st);
 }
 
 int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, int degree,
@@ -572,6 +617,7 @@ int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   cudaStream_t st = (cudaStream_t)stream;
   const long long launches0 = launch_count();
   CK(c, cudaEventRecord(c->ev[0], st));
+  CK(c, cudaMemsetAsync(c->eig.status + 2, 0, 2 * sizeof(int), st));
   double a, b, a0;
   if (bounds) {
     a = bounds[0];
@@ -618,6 +664,350 @@ int sparc_get_timings(sparc_handle c, sparc_timings* t) {
   t->rotate_ms = ms[5];
   CK(c, cudaEventElapsedTime(&t->total_ms, c->ev[0], c->ev[6]));
   t->launches = c->step_launches;
+  return SPARC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched CheFSI step (many independent systems, one launch per degree).
+// ---------------------------------------------------------------------------
+struct sparc_batch_context {
+  std::vector<sparc_context*> hs;
+  int precision = SPARC_PREC_FP64;
+  int device = 0;
+  void* d_sys = nullptr;
+  void* d_items = nullptr;
+  void* h_items = nullptr;  // pinned staging of the per-degree tables
+  int max_rows = 0;         // degrees + 1 rows of nsys items
+  int64_t cta_total = 0, nl_total = 0;
+  cudaStream_t cs = nullptr;
+  std::vector<cudaStream_t> workers;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr, start = nullptr, stop = nullptr, done = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int64_t> key;
+  long long graph_launches = 0;
+  long long last_launches = 0;
+  std::string err;
+};
+
+namespace {
+
+constexpr int kBatchWorkers = 8;
+
+void batch_free(sparc_batch_context* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  cudaFree(b->d_sys);
+  cudaFree(b->d_items);
+  cudaFreeHost(b->h_items);
+  for (auto s : b->workers) cudaStreamDestroy(s);
+  for (auto e : b->joins) cudaEventDestroy(e);
+  if (b->cs) cudaStreamDestroy(b->cs);
+  for (auto e : {b->fork, b->start, b->stop, b->done})
+    if (e) cudaEventDestroy(e);
+  delete b;
+}
+
+template <typename T>
+int batch_step_impl(sparc_batch_context* b, void* const* X, const int* ns, const int64_t* ld,
+                    const int* degree, const double* bounds, double* const* eig,
+                    cudaStream_t caller) {
+  const int n = (int)b->hs.size();
+  const size_t isz = batch_item_bytes();
+  int mmax = 0;
+  for (int i = 0; i < n; ++i) mmax = std::max(mmax, degree[i]);
+  if (mmax + 1 > b->max_rows) {
+    cudaFree(b->d_items);
+    cudaFreeHost(b->h_items);
+    b->d_items = nullptr;
+    b->h_items = nullptr;
+    b->max_rows = mmax + 1;
+    if (cudaMalloc(&b->d_items, (size_t)b->max_rows * n * isz) != cudaSuccess ||
+        cudaMallocHost(&b->h_items, (size_t)b->max_rows * n * isz) != cudaSuccess) {
+      b->err = "cannot allocate batch tables";
+      return SPARC_ERR_OOM;
+    }
+  }
+  // per-system bounds and the buffer plan of the filter (as in run_filter)
+  std::vector<T*> xt(n), yt(n);
+  std::vector<int64_t> ldt(n);
+  uint8_t* tab = static_cast<uint8_t*>(b->h_items);
+  for (int i = 0; i < n; ++i) {
+    sparc_context* c = b->hs[i];
+    double a, bb, a0;
+    if (bounds) {
+      a = bounds[3 * i];
+      bb = bounds[3 * i + 1];
+      a0 = bounds[3 * i + 2];
+    } else {
+      if (!c->have_bounds) {
+        int rc = lanczos(c, 32, 0, &c->a0, &c->b, b->cs);
+        if (rc) {
+          b->err = c->err;
+          return rc;
+        }
+        c->have_bounds = true;
+      }
+      bb = c->b;
+      a0 = c->a0;
+      a = c->have_prev ? c->prev_max : a0 + 0.1 * (bb - a0);
+      a = std::min(std::max(a, a0 + 1e-3 * (bb - a0)), bb - 1e-3 * (bb - a0));
+    }
+    if (!(a0 < a && a < bb)) {
+      b->err = "invalid argument: bounds must satisfy a0 < a < b";
+      return SPARC_ERR_INVALID_ARG;
+    }
+    const int m = degree[i];
+    const double e = (bb - a) / 2.0, cc = (bb + a) / 2.0;
+    double sigma = e / (a0 - cc);
+    const double sigma1 = sigma, tau = 2.0 / sigma1;
+    std::vector<T*> buf(m + 1);
+    std::vector<int64_t> lds(m + 1);
+    T* Xi = (T*)X[i];
+    buf[0] = Xi;
+    lds[0] = ld[i];
+    for (int k = 1; k <= m; ++k) {
+      T* out = (m % 2 == 1) ? ((k % 2 == 1) ? (T*)c->W1 : Xi) : ((k % 2 == 1) ? (T*)c->W1 : (T*)c->W2);
+      buf[k] = out;
+      lds[k] = out == Xi ? ld[i] : c->ld;
+    }
+    for (int k = 0; k < mmax; ++k) {
+      BatchItemHost it{};
+      if (k < m) {
+        const int deg = k + 1;
+        it.x = buf[deg - 1];
+        it.ldx = lds[deg - 1];
+        it.y = buf[deg];
+        it.ldy = lds[deg];
+        it.shift = cc;
+        it.active = 1;
+        if (deg == 1) {
+          it.prev = nullptr;
+          it.s_h = sigma1 / e;
+          it.s_p = 0.0;
+        } else {
+          const double sn = 1.0 / (tau - sigma);
+          it.prev = buf[deg - 2];
+          it.ldp = lds[deg - 2];
+          it.s_h = 2.0 * sn / e;
+          it.s_p = -sigma * sn;
+          sigma = sn;
+        }
+      }
+      batch_pack_item(it, tab + ((size_t)k * n + i) * isz);
+    }
+    xt[i] = buf[m];
+    ldt[i] = lds[m];
+    yt[i] = buf[m] == (T*)c->W1 ? (T*)c->W2 : (T*)c->W1;
+    BatchItemHost hx{};
+    hx.x = xt[i];
+    hx.ldx = ldt[i];
+    hx.y = yt[i];
+    hx.ldy = c->ld;
+    hx.s_h = 1.0;
+    hx.active = 1;
+    batch_pack_item(hx, tab + ((size_t)mmax * n + i) * isz);
+  }
+  // rows beyond mmax are unused; upload the table
+  std::vector<int64_t> key;
+  key.push_back(mmax);
+  for (int i = 0; i < n; ++i) {
+    key.push_back((int64_t)(uintptr_t)X[i]);
+    key.push_back(ns[i]);
+    key.push_back(ld[i]);
+    key.push_back(degree[i]);
+  }
+  CK(b, cudaEventRecord(b->start, caller));
+  CK(b, cudaStreamWaitEvent(b->cs, b->start, 0));
+  CK(b, cudaMemcpyAsync(b->d_items, b->h_items, (size_t)(mmax + 1) * n * isz,
+                        cudaMemcpyHostToDevice, b->cs));
+  for (int i = 0; i < n; ++i)
+    CK(b, cudaMemsetAsync(b->hs[i]->eig.status, 0, 4 * sizeof(int), b->cs));
+  if (!b->exec || key != b->key) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    const long long l0 = launch_count();
+    CK(b, cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k <= mmax; ++k) {
+      const uint8_t* rows = static_cast<const uint8_t*>(b->d_items) + (size_t)k * n * isz;
+      cudaError_t e = batch_degree<T>(b->d_sys, rows, n, b->cta_total, b->nl_total, b->cs);
+      if (e != cudaSuccess) {
+        cudaGraph_t g;
+        cudaStreamEndCapture(b->cs, &g);
+        b->err = std::string("batched degree launch: ") + cudaGetErrorString(e);
+        return SPARC_ERR_CUDA;
+      }
+    }
+    cudaEventRecord(b->fork, b->cs);
+    for (auto w : b->workers) cudaStreamWaitEvent(w, b->fork, 0);
+    int rc = SPARC_OK;
+    for (int i = 0; i < n && !rc; ++i) {
+      sparc_context* c = b->hs[i];
+      cudaStream_t w = b->workers[i % b->workers.size()];
+      rc = do_project<T>(c, xt[i], ldt[i], yt[i], c->ld, ns[i], c->Hs, c->Ms, w);
+      if (!rc && gen_eig(c->eig, c->Hs, c->Ms, ns[i], c->lam, c->Z, w) != cudaSuccess) rc = SPARC_ERR_CUDA;
+      if (!rc) rc = do_rotate<T>(c, xt[i], ldt[i], ns[i], c->Z, (T*)X[i], ld[i], w);
+      if (rc) b->err = c->err;
+    }
+    for (size_t k = 0; k < b->workers.size(); ++k) {
+      cudaEventRecord(b->joins[k], b->workers[k]);
+      cudaStreamWaitEvent(b->cs, b->joins[k], 0);
+    }
+    cudaGraph_t graph;
+    cudaError_t ec = cudaStreamEndCapture(b->cs, &graph);
+    if (rc) return rc;
+    CK(b, ec);
+    ec = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(b, ec);
+    b->key = key;
+    b->graph_launches = launch_count() - l0;
+  }
+  CK(b, cudaEventRecord(b->stop, b->cs));
+  CK(b, cudaGraphLaunch(b->exec, b->cs));
+  CK(b, cudaEventRecord(b->done, b->cs));
+  CK(b, cudaStreamWaitEvent(caller, b->done, 0));
+  b->last_launches = b->graph_launches;
+  CK(b, cudaStreamSynchronize(b->cs));
+  for (int i = 0; i < n; ++i) {
+    sparc_context* c = b->hs[i];
+    int rc = read_status(c, b->cs);
+    if (rc) {
+      b->err = "system " + std::to_string(i) + ": " + c->err;
+      return rc;
+    }
+    double lmax;
+    CK(b, cudaMemcpy(&lmax, c->lam + ns[i] - 1, sizeof(double), cudaMemcpyDeviceToHost));
+    c->have_prev = true;
+    c->prev_max = lmax;
+    if (eig && eig[i])
+      CK(b, cudaMemcpy(eig[i], c->lam, ns[i] * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  return SPARC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sparc_batch_create(const sparc_handle* hs, int n, sparc_batch* out) {
+  if (!out) return SPARC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!hs || n < 1) {
+    g_create_err = "invalid argument: need n >= 1 handles";
+    return SPARC_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i)
+    if (!hs[i] || hs[i]->precision != hs[0]->precision || hs[i]->device != hs[0]->device) {
+      g_create_err = "invalid argument: handles must be non-null, same precision and device";
+      return SPARC_ERR_INVALID_ARG;
+    }
+  sparc_batch_context* b = new sparc_batch_context();
+  b->hs.assign(hs, hs + n);
+  b->precision = hs[0]->precision;
+  b->device = hs[0]->device;
+  auto fail = [&](const char* what, cudaError_t e) {
+    g_create_err = std::string(what) + ": " + cudaGetErrorString(e);
+    batch_free(b);
+    return cuda_status(e);
+  };
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e != cudaSuccess) return fail("cudaSetDevice", e);
+  std::vector<BatchSysHost> sys(n);
+  for (int i = 0; i < n; ++i) {
+    sparc_context* c = hs[i];
+    BatchSysHost& s = sys[i];
+    s = BatchSysHost{};
+    s.nx = c->grid.nx; s.ny = c->grid.ny; s.nz = c->grid.nz;
+    for (int d = 0; d < 3; ++d) s.bc[d] = c->grid.bc[d];
+    s.ns = c->ns_max;
+    s.diag = c->lap.diag;
+    for (int p = 0; p <= kRadius; ++p) s.off[p] = c->lap.off[p];
+    s.h3 = c->h * c->h * c->h;
+    const bool mixed = c->precision == SPARC_PREC_MIXED;
+    s.veff = mixed ? (const void*)c->veff32 : (const void*)c->veff64;
+    s.natoms = c->nl64.natoms;
+    s.kp = c->nl64.kp;
+    s.pull_ptr = c->nl64.pull_ptr;
+    s.pull_k = c->nl64.pull_k;
+    s.pull_chi = mixed ? (const void*)c->nl32.pull_chi : (const void*)c->nl64.pull_chi;
+    s.supp_ptr = c->nl64.supp_ptr;
+    s.supp_idx = c->nl64.supp_idx;
+    s.nproj = c->nl64.nproj;
+    s.chi_ptr = c->nl64.chi_ptr;
+    s.chi = mixed ? (const void*)c->nl32.chi : (const void*)c->nl64.chi;
+    s.proj_ptr = c->nl64.proj_ptr;
+    s.gamma = c->nl64.gamma;
+    s.D = c->D;
+  }
+  if (b->precision == SPARC_PREC_MIXED)
+    batch_layout<float>(sys, &b->cta_total, &b->nl_total);
+  else
+    batch_layout<double>(sys, &b->cta_total, &b->nl_total);
+  std::vector<uint8_t> packed(batch_sys_bytes() * n);
+  for (int i = 0; i < n; ++i) batch_pack_sys(sys[i], packed.data() + i * batch_sys_bytes());
+  if ((e = cudaMalloc(&b->d_sys, packed.size())) != cudaSuccess) return fail("cudaMalloc", e);
+  if ((e = cudaMemcpy(b->d_sys, packed.data(), packed.size(), cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return fail("cudaMemcpy", e);
+  if ((e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail("cudaStreamCreate", e);
+  const int nw = std::min(kBatchWorkers, n);
+  for (int k = 0; k < nw; ++k) {
+    cudaStream_t s;
+    cudaEvent_t j;
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
+      return fail("cudaStreamCreate", e);
+    b->workers.push_back(s);
+    if ((e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming)) != cudaSuccess)
+      return fail("cudaEventCreate", e);
+    b->joins.push_back(j);
+  }
+  for (cudaEvent_t* ev : {&b->fork, &b->start, &b->done})
+    if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+      return fail("cudaEventCreate", e);
+  if ((e = cudaEventCreate(&b->stop)) != cudaSuccess) return fail("cudaEventCreate", e);
+  *out = b;
+  return SPARC_OK;
+}
+
+int sparc_batch_destroy(sparc_batch b) {
+  if (!b) return SPARC_OK;
+  cudaSetDevice(b->device);
+  batch_free(b);
+  return SPARC_OK;
+}
+
+const char* sparc_batch_last_error(sparc_batch b) { return b ? b->err.c_str() : ""; }
+
+int sparc_batch_chefsi_step(sparc_batch b, void* const* X, const int* ns, const int64_t* ld,
+                            int dtype, const int* degree, const double* bounds,
+                            double* const* eig, void* stream) {
+  if (!b) return SPARC_ERR_INVALID_ARG;
+  ARG(b, X && ns && ld && degree, "null argument");
+  const int n = (int)b->hs.size();
+  for (int i = 0; i < n; ++i) {
+    sparc_context* c = b->hs[i];
+    ARG(b, X[i] && is_device_ptr(X[i]), "batched blocks must be device pointers");
+    ARG(b, ns[i] == c->ns_max, "batch members run with ns equal to their handle's ns_max");
+    ARG(b, ld[i] >= c->nd, "ld must be >= Nd");
+    ARG(b, degree[i] >= 1 && degree[i] <= 1000, "degree must be in [1, 1000]");
+  }
+  const int want = b->precision == SPARC_PREC_MIXED ? SPARC_F32 : SPARC_F64;
+  ARG(b, dtype == want, "dtype does not match the handles' precision");
+  CK(b, cudaSetDevice(b->device));
+  if (dtype == SPARC_F64)
+    return batch_step_impl<double>(b, X, ns, ld, degree, bounds, eig, (cudaStream_t)stream);
+  return batch_step_impl<float>(b, X, ns, ld, degree, bounds, eig, (cudaStream_t)stream);
+}
+
+int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step) {
+  if (!b || !launches_per_step) return SPARC_ERR_INVALID_ARG;
+  *launches_per_step = b->last_launches;
   return SPARC_OK;
 }
 

@@ -169,9 +169,10 @@ __global__ void __launch_bounds__(kThreads)
 }  // namespace
 
 int project_nsplit(int64_t nd, int ns) {
+  // ~8 waves of the 3-CTA-per-SM residency so the last wave's tail is small
   int nb = (ns + kT - 1) / kT;
   int64_t tiles = (int64_t)nb * (nb + 1) / 2;
-  int64_t want = (3 * 152 + tiles - 1) / tiles;
+  int64_t want = (8 * 3 * 152 + tiles - 1) / tiles;
   int64_t maxk = (nd + 1023) / 1024;  // at least ~1024 K per split
   int64_t s = want < maxk ? want : maxk;
   if (s < 1) s = 1;
@@ -187,6 +188,13 @@ cudaError_t project_simt(const T* Xt, const T* Yt, int64_t ld, int64_t nd, int n
   int64_t kchunk = (nd + nsplit - 1) / nsplit;
   kchunk = (kchunk + kK - 1) / kK * kK;
   note_launch(), k_project_partial<T><<<dim3(tiles, nsplit), kThreads, 0, st>>>(Xt, Yt, ld, nd, ns, kchunk, work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return project_reduce(work, nsplit, ns, Hs, Ms, st);
+}
+
+cudaError_t project_reduce(const double* work, int nsplit, int ns, double* Hs, double* Ms,
+                           cudaStream_t st) {
   int64_t nn = (int64_t)ns * ns;
   int blocks = (int)std::min<int64_t>((nn + 255) / 256, 4096);
   note_launch(), k_project_reduce<<<blocks, 256, 0, st>>>(work, nsplit, ns, Hs, Ms);

@@ -278,6 +278,109 @@ __global__ void k_house_tail(const double* A, double* Hv, double* d, double* e, 
 }
 
 // ---------------------------------------------------------------------------
+// Persistent form of the Householder reduction: one cooperative launch runs all
+// n - 2 steps, separated by a grid barrier (3 per step) instead of 3 kernel
+// launches per step.  The barrier waits are bounded: on expiry the kernel
+// records SPARC_ERR_TIMEOUT in status[4] and every block leaves the loop.
+// ---------------------------------------------------------------------------
+constexpr long long kBarrierCycles = 4000000000LL;
+
+struct GridBar {
+  unsigned* count;
+  unsigned* gen;
+  int* status;
+};
+
+// Returns false if the barrier timed out (in any block).
+__device__ bool grid_barrier(const GridBar& gb, unsigned nblocks, int* abort_sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gb.gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(gb.count, 1u) == nblocks - 1) {
+      atomicExch(gb.count, 0u);
+      __threadfence();
+      atomicAdd(gb.gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (*(volatile int*)gb.status != 0 || clock64() - t0 > kBarrierCycles) {
+          atomicCAS(gb.status, 0, SPARC_ERR_TIMEOUT);
+          *abort_sh = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)gb.status != 0) *abort_sh = 1;
+  }
+  __syncthreads();
+  return *abort_sh == 0;
+}
+
+__global__ void __launch_bounds__(256)
+    k_house_persistent(double* __restrict__ A, double* __restrict__ Hv, double* d, double* e,
+                       double* __restrict__ p, int n, GridBar gb) {
+  __shared__ double sh[32];
+  __shared__ int abort_sh;
+  if (threadIdx.x == 0) abort_sh = 0;
+  __syncthreads();
+  const unsigned nb = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int k = 0; k + 2 < n; ++k) {
+    const double* col = A + (int64_t)k * n;
+    double* hv = Hv + (int64_t)k * n;
+    if (blockIdx.x == 0) {
+      double acc = 0.0;
+      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += col[i] * col[i];
+      const double xn = sqrt(block_sum_d(acc, sh));
+      const double x0 = col[k + 1];
+      const double alpha = x0 >= 0.0 ? -xn : xn;
+      double vn2 = 0.0;
+      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const double v = col[i] - (i == k + 1 ? alpha : 0.0);
+        vn2 += v * v;
+      }
+      const double vn = sqrt(block_sum_d(vn2, sh));
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = 0.0;
+        if (i > k && xn > 0.0 && vn > 0.0) v = (col[i] - (i == k + 1 ? alpha : 0.0)) / vn;
+        hv[i] = v;
+      }
+      if (threadIdx.x == 0) {
+        d[k] = col[k];
+        e[k] = xn > 0.0 ? alpha : 0.0;
+      }
+    }
+    if (!grid_barrier(gb, nb, &abort_sh)) return;
+    // p = A v on the trailing block (warp per row)
+    for (int i = k + 1 + gwarp; i < n; i += nwarps) {
+      const double* row = A + (int64_t)i * n;
+      double s2 = 0.0;
+      for (int j = k + 1 + lane; j < n; j += 32) s2 += row[j] * hv[j];
+      s2 = warp_sum_d(s2);
+      if (lane == 0) p[i] = s2;
+    }
+    if (!grid_barrier(gb, nb, &abort_sh)) return;
+    double acc = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += hv[i] * p[i];
+    const double K = block_sum_d(acc, sh);
+    const int m = n - k - 1;
+    const int64_t mm = (int64_t)m * m;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < mm;
+         t += (int64_t)gridDim.x * blockDim.x) {
+      const int i = k + 1 + (int)(t % m), j = k + 1 + (int)(t / m);
+      const double qi = p[i] - K * hv[i], qj = p[j] - K * hv[j];
+      A[i + (int64_t)j * n] -= 2.0 * (hv[i] * qj + qi * hv[j]);
+    }
+    if (!grid_barrier(gb, nb, &abort_sh)) return;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Tridiagonal eigenvalues by bisection.  scal[0..1] = Gershgorin interval,
 // scal[2] = pivmin.
 // ---------------------------------------------------------------------------
@@ -638,7 +741,7 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
   const dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
   int* st0 = w.status;
   int* st1 = w.status + 1;
-  cudaMemsetAsync(w.status, 0, 2 * sizeof(int), st);
+  cudaMemsetAsync(w.status, 0, 2 * sizeof(int), st);  // words 2, 3: GEMM / stencil waits
   // 1. Ms = L L^T
   cudaMemcpyAsync(w.W, Ms, nn * 8, cudaMemcpyDeviceToDevice, st);
   cholesky(w.W, n, st0, st);
@@ -652,7 +755,33 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
   // 3. Householder tridiagonalisation; reflectors in the rows of Hv = lu[0, nn)
   double* Hv = w.lu;
   double* p = w.tau;
-  for (int k = 0; k + 2 < n; ++k) {
+  bool coop_done = false;
+  if (n >= 64) {
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_house_persistent, 256, 0);
+    if (coop && sms > 0 && per_sm > 0) {
+      int blocks = sms * std::min(per_sm, 2);
+      GridBar gb{reinterpret_cast<unsigned*>(w.status + 8), reinterpret_cast<unsigned*>(w.status + 9),
+                 w.status + 4};
+      cudaMemsetAsync(w.status + 4, 0, sizeof(int), st);
+      cudaMemsetAsync(w.status + 8, 0, 2 * sizeof(int), st);
+      double* Ap = w.A;
+      double* dp = w.d;
+      double* ep = w.e;
+      int nn_ = n;
+      void* args[] = {&Ap, &Hv, &dp, &ep, &p, &nn_, &gb};
+      note_launch();
+      if (cudaLaunchCooperativeKernel((void*)k_house_persistent, dim3(blocks), dim3(256), args, 0,
+                                      st) == cudaSuccess)
+        coop_done = true;
+      else
+        cudaGetLastError();
+    }
+  }
+  for (int k = 0; !coop_done && k + 2 < n; ++k) {
     note_launch(), k_house_vec<<<1, 256, 0, st>>>(w.A, Hv, w.d, w.e, n, k);
     int m = n - k - 1;
     note_launch(), k_house_matvec<<<(m + 7) / 8, 256, 0, st>>>(w.A, Hv, p, n, k);

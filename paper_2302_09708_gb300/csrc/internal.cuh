@@ -2,10 +2,12 @@
 // Nothing here is part of the public C ABI (see include/sparc.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/sparc.h"
 
@@ -56,11 +58,19 @@ struct Nonlocal {
 // Launchers (stencil.cu) -------------------------------------------------
 // y = s_h * ((H - shift) x) + s_p * prev   (prev may be null: s_p ignored)
 // with D the nonlocal coefficients of x (computed by nl_coefficients).
+// `status` (device int, may be null): receives SPARC_ERR_TIMEOUT if a bounded
+// wait of the TMA-ring form runs out; with a null status the generic form runs.
 template <typename T>
 cudaError_t apply_h(const Grid& g, const LapCoef& lc, const T* veff, const Nonlocal<T>& nl,
                     const T* D, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
-                    int64_t ldp, int ns, double shift, double s_h, double s_p,
+                    int64_t ldp, int ns, double shift, double s_h, double s_p, int* status,
                     cudaStream_t st);
+// TMA plane-ring form (stencil_tma.cu); *used = false when it does not apply.
+template <typename T>
+cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const Nonlocal<T>& nl,
+                         const T* D, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
+                         int64_t ldp, int ns, double shift, double s_h, double s_p, int* status,
+                         cudaStream_t st, bool* used);
 
 // D[n * kp + k] = gamma_k h^3 sum_s chi[s][k] x[idx_s + n ldx]
 template <typename T>
@@ -87,6 +97,20 @@ template <typename T>
 cudaError_t project_simt(const T* Xt, const T* Yt, int64_t ld, int64_t nd, int ns, double* Hs,
                          double* Ms, double* work, int nsplit, cudaStream_t st);
 int project_nsplit(int64_t nd, int ns);
+// Sum the nsplit partials work[s][{H, M}][ns x ns] of the upper elements, mirror.
+cudaError_t project_reduce(const double* work, int nsplit, int ns, double* Hs, double* Ms,
+                           cudaStream_t st);
+
+// Split-precision tensor-core GEMMs (tc_gemm.cu), FP32 operands.
+size_t tc_slice_elems(int64_t ld, int64_t nd, int ns_max);
+int tc_project_nsplit(int ns);
+// `esc`: int workspace of max(2 ns, nd + ns) entries (per-row binary exponents).
+cudaError_t tc_project(const float* Xt, const float* Yt, int64_t ld, int64_t nd, int ns,
+                       double* Hs, double* Ms, double* work, int nsplit, __nv_bfloat16* SX,
+                       __nv_bfloat16* SY, int* esc, int* status, cudaStream_t st);
+cudaError_t tc_rotate(const float* Xt, int64_t ld, int64_t nd, int ns, const double* Z,
+                      float* Xout, int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc,
+                      int* status, cudaStream_t st);
 // Xout = Xt Z (Z column-major ns x ns)
 template <typename T>
 cudaError_t rotate_simt(const T* Xt, int64_t ld, int64_t nd, int ns, const double* Z, T* Xout,
@@ -114,6 +138,44 @@ void eig_free(EigWork& w);
 cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, double* lam, double* Z,
                     cudaStream_t st);
 
+// Batched form (batch.cu) -------------------------------------------------
+struct BatchSysHost {
+  int nx, ny, nz, bc[3];
+  int ns, tiles_x, tiles_y, nzc, bz;
+  int natoms, kp;
+  int64_t cta_begin, nl_cta_begin;
+  double diag, off[kRadius + 1], h3;
+  const void* veff;
+  const int* pull_ptr;
+  const int* pull_k;
+  const void* pull_chi;
+  const int64_t* supp_ptr;
+  const int* supp_idx;
+  const int* nproj;
+  const int64_t* chi_ptr;
+  const void* chi;
+  const int* proj_ptr;
+  const double* gamma;
+  void* D;
+};
+struct BatchItemHost {
+  const void* x;
+  void* y;
+  const void* prev;
+  int64_t ldx, ldy, ldp;
+  double shift, s_h, s_p;
+  int active;
+};
+template <typename T>
+void batch_layout(std::vector<BatchSysHost>& hs, int64_t* cta_total, int64_t* nl_total);
+size_t batch_sys_bytes();
+size_t batch_item_bytes();
+void batch_pack_sys(const BatchSysHost& h, void* out);
+void batch_pack_item(const BatchItemHost& h, void* out);
+template <typename T>
+cudaError_t batch_degree(const void* sys, const void* items, int nsys, int64_t cta_total,
+                         int64_t nl_total, cudaStream_t st);
+
 }  // namespace sparc
 
 // Handle ------------------------------------------------------------------
@@ -137,6 +199,10 @@ struct sparc_context {
   void* W1 = nullptr;
   void* W2 = nullptr;
   void* Wstage = nullptr;  // host-pointer staging (lazy)
+  __nv_bfloat16* S1 = nullptr;  // BF16 operand slices (mixed precision)
+  __nv_bfloat16* S2 = nullptr;
+  __nv_bfloat16* SZ = nullptr;
+  int* esc = nullptr;  // per-row exponents of the digit slices (mixed precision)
   void* D = nullptr;       // nonlocal coefficients kp x ns_max
   double* Hs = nullptr;
   double* Ms = nullptr;
@@ -155,5 +221,6 @@ struct sparc_context {
   cudaEvent_t ev[7] = {};
   bool timed = false;
   long long step_launches = 0;
+  bool ring_enabled = true;  // TMA-ring stencil (options.reserved[0] bit 0 turns it off)
   std::string err;
 };

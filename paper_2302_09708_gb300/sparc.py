@@ -66,7 +66,9 @@ class sparc_timings(ctypes.Structure):
 
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_hpsi",
            "sparc_spectrum_bounds", "sparc_cheb_filter", "sparc_project", "sparc_subspace_eig",
-           "sparc_rotate", "sparc_chefsi_step", "sparc_get_timings", "sparc_project_noalloc"]
+           "sparc_rotate", "sparc_chefsi_step", "sparc_get_timings", "sparc_project_noalloc",
+           "sparc_batch_create", "sparc_batch_destroy", "sparc_batch_last_error",
+           "sparc_batch_chefsi_step", "sparc_batch_get_info"]
 
 _lib = None
 
@@ -100,8 +102,14 @@ def load(build: bool = True):
     L.sparc_chefsi_step.argtypes = [vp, vp, i, i64, i, i, vp, vp, i, vp]
     L.sparc_get_timings.argtypes = [vp, ctypes.POINTER(sparc_timings)]
     L.sparc_project_noalloc.argtypes = [vp, vp, i, i64, i64, vp, vp, vp]
+    L.sparc_batch_create.argtypes = [vp, i, ctypes.POINTER(vp)]
+    L.sparc_batch_destroy.argtypes = [vp]
+    L.sparc_batch_last_error.argtypes = [vp]
+    L.sparc_batch_last_error.restype = ctypes.c_char_p
+    L.sparc_batch_chefsi_step.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, vp]
+    L.sparc_batch_get_info.argtypes = [vp, ctypes.POINTER(i64)]
     for name in EXPORTS:
-        if name not in ("sparc_last_error",):
+        if name not in ("sparc_last_error", "sparc_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -146,8 +154,10 @@ def _arr(a, dtype):
 
 
 # -- C-named functions -------------------------------------------------------
-def sparc_create(system, precision: int = SPARC_PREC_FP64, ns_max: int = 1, device: int = 0):
-    """Create a handle for a `synth.System`-like object (grid, Veff, projectors)."""
+def sparc_create(system, precision: int = SPARC_PREC_FP64, ns_max: int = 1, device: int = 0,
+                 flags: int = 0):
+    """Create a handle for a `synth.System`-like object (grid, Veff, projectors).
+    flags (sparc_options.reserved[0]): bit 0 selects the generic stencil form."""
     L = load()
     g = sparc_grid(system.nx, system.ny, system.nz, system.h, (ctypes.c_int * 3)(*system.bc))
     keep = [_arr(system.veff, np.float64), _arr(system.supp_ptr, np.int64),
@@ -157,7 +167,7 @@ def sparc_create(system, precision: int = SPARC_PREC_FP64, ns_max: int = 1, devi
     veff, sp, si, npj, cp, chi, pp, gam = keep
     nl = sparc_nonlocal(int(system.natoms), sp.ctypes.data, si.ctypes.data, npj.ctypes.data,
                         cp.ctypes.data, chi.ctypes.data, pp.ctypes.data, gam.ctypes.data)
-    opt = sparc_options(precision, ns_max, device, (ctypes.c_int * 5)())
+    opt = sparc_options(precision, ns_max, device, (ctypes.c_int * 5)(flags, 0, 0, 0, 0))
     out = ctypes.c_void_p()
     rc = L.sparc_create(ctypes.byref(g), veff.ctypes.data, ctypes.byref(nl), ctypes.byref(opt),
                         ctypes.byref(out))
@@ -236,12 +246,12 @@ def sparc_get_timings(h):
 class Handle:
     """Convenience wrapper owning one sparc_handle."""
 
-    def __init__(self, system, precision="fp64", ns_max=1, device=0):
+    def __init__(self, system, precision="fp64", ns_max=1, device=0, options_flags=0):
         prec = SPARC_PREC_MIXED if precision == "mixed" else SPARC_PREC_FP64
         self.system = system
         self.precision = precision
         self.ns_max = ns_max
-        self.h = sparc_create(system, prec, ns_max, device)
+        self.h = sparc_create(system, prec, ns_max, device, options_flags)
 
     @property
     def dtype(self):
@@ -297,3 +307,53 @@ class Handle:
 
     def timings(self):
         return sparc_get_timings(self.h)
+
+
+class Batch:
+    """A batch of handles stepped together (sparc_batch_* calls)."""
+
+    def __init__(self, handles):
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h.h.value for h in self.handles])
+        out = ctypes.c_void_p()
+        rc = load().sparc_batch_create(arr, len(self.handles), ctypes.byref(out))
+        _check(None, rc)
+        self.b = out
+
+    def close(self):
+        if self.b:
+            load().sparc_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def chefsi_step(self, Xs, degrees, bounds=None, stream=None):
+        """One batched step; Xs: list of (ns_i, ld_i) tensors; returns Ritz values."""
+        L = load()
+        n = len(Xs)
+        blocks = [_block(X) for X in Xs]
+        dt = blocks[0][3]
+        ptrs = (ctypes.c_void_p * n)(*[b[0] for b in blocks])
+        nss = (ctypes.c_int * n)(*[b[1] for b in blocks])
+        lds = (ctypes.c_int64 * n)(*[b[2] for b in blocks])
+        degs = (ctypes.c_int * n)(*degrees)
+        eigs = [np.zeros(b[1]) for b in blocks]
+        eptr = (ctypes.c_void_p * n)(*[e.ctypes.data for e in eigs])
+        bptr = None
+        if bounds is not None:
+            flat = (ctypes.c_double * (3 * n))(*[v for t in bounds for v in t])
+            bptr = ctypes.cast(flat, ctypes.c_void_p)
+        rc = L.sparc_batch_chefsi_step(self.b, ptrs, nss, lds, dt, degs, bptr, eptr,
+                                       _stream(stream))
+        if rc != SPARC_OK:
+            raise SparcError(rc, L.sparc_batch_last_error(self.b).decode())
+        return eigs
+
+    def launches(self):
+        v = ctypes.c_int64()
+        _check(None, load().sparc_batch_get_info(self.b, ctypes.byref(v)))
+        return v.value

@@ -28,6 +28,9 @@ SYSTEMS = {
     "all_dirichlet_odd": lambda: synth.random_system((15, 13, 14), 0.5, (1, 1, 1), 2, seed=43),
     "wide_x": lambda: synth.random_system((70, 13, 16), 0.5, (0, 1, 0), 3, seed=44),
     "free": lambda: synth.free_system((16, 16, 16), 0.5, (0, 0, 0), v0=0.3),
+    # grids the TMA plane-ring stencil handles (x a multiple of 16, z split in chunks)
+    "ring_periodic": lambda: synth.random_system((32, 32, 64), 0.45, (0, 0, 0), 3, seed=45),
+    "ring_dirichlet_y": lambda: synth.random_system((48, 20, 17), 0.5, (0, 1, 1), 3, seed=46),
 }
 
 
@@ -72,7 +75,8 @@ def test_hpsi_leading_dimension(ld_pad):
     assert np.all(Y[:, s.nd:] == 7.0)  # rows beyond Nd are never written
 
 
-@pytest.mark.parametrize("name", ["cfg1", "dirichlet_z", "wide_x"])
+@pytest.mark.parametrize("name", ["cfg1", "dirichlet_z", "wide_x", "ring_periodic",
+                                  "ring_dirichlet_y"])
 def test_hpsi_fp32(name):
     s = SYSTEMS[name]()
     o = oracle.Oracle(s)
@@ -103,7 +107,8 @@ def test_spectrum_bounds(name):
 
 
 @pytest.mark.parametrize("name,degree", [("cfg1", 20), ("dirichlet_z", 7), ("ragged_periodic", 1),
-                                         ("wide_x", 12)])
+                                         ("wide_x", 12), ("ring_periodic", 9),
+                                         ("ring_dirichlet_y", 4)])
 def test_cheb_filter_fp64(name, degree):
     s = SYSTEMS[name]()
     o = oracle.Oracle(s)
@@ -276,3 +281,72 @@ def test_invalid_arguments():
         h.hpsi(to_dev(np.zeros((5, s.nd))))  # ns > ns_max
     with pytest.raises(sparc.SparcError):
         h.hpsi(X.float())  # dtype mismatch on an FP64 handle
+
+
+# ---------------------------------------------------------------------------
+# Mixed precision: FP32 orbitals, split-precision tensor-core projection and
+# rotation (three BF16 slices per operand, six slice products, double-FP32
+# accumulation) against the oracle evaluated on the same FP32 inputs.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,ns", [("cfg1", 40), ("ragged_periodic", 200), ("cfg1", 129),
+                                     ("wide_x", 1)])
+def test_project_mixed_tensor_cores(name, ns):
+    s = SYSTEMS[name]()
+    rng = np.random.default_rng(ns)
+    X = rng.standard_normal((ns, s.nd)).astype(np.float32)
+    Y = (0.3 * X + rng.standard_normal((ns, s.nd))).astype(np.float32)
+    h = sparc.Handle(s, "mixed", ns_max=ns)
+    Hs, Ms = h.project(to_dev(X, torch.float32), to_dev(Y, torch.float32))
+    rH, rM = oracle.project(X.astype(np.float64), Y.astype(np.float64), s.nd)
+    iu = np.triu_indices(ns)
+    eH = np.max(np.abs(Hs.cpu().numpy().T[iu] - rH[iu])) / np.max(np.abs(rH))
+    eM = np.max(np.abs(Ms.cpu().numpy() - rM)) / np.max(np.abs(rM))
+    assert eH < 1e-7 and eM < 1e-7, (eH, eM)
+
+
+@pytest.mark.parametrize("name,ns", [("cfg1", 40), ("ragged_periodic", 200), ("dirichlet_z", 7)])
+def test_rotate_mixed_tensor_cores(name, ns):
+    s = SYSTEMS[name]()
+    rng = np.random.default_rng(ns + 1)
+    X = rng.standard_normal((ns, s.nd)).astype(np.float32)
+    Z = rng.standard_normal((ns, ns))
+    h = sparc.Handle(s, "mixed", ns_max=ns)
+    R = h.rotate(to_dev(X, torch.float32), to_dev(Z)).double().cpu().numpy()
+    ref = oracle.rotate(X.astype(np.float64), Z, s.nd)
+    err = np.max(np.abs(R - ref)) / np.max(np.abs(ref))
+    assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("name,ns,degree", [("cfg1", 40, 20), ("dirichlet_z", 24, 10),
+                                            ("ring_periodic", 30, 12)])
+def test_chefsi_step_mixed_vs_oracle(name, ns, degree):
+    """Mixed precision step against the FP64 oracle: Ritz values of the
+    occupied states and the subspace agree to single-precision-level accuracy."""
+    s = SYSTEMS[name]()
+    o = oracle.Oracle(s)
+    a0, b, a = bounds_for(o)
+    X0 = synth.random_orbitals(s.nd, ns, seed=13)
+    h = sparc.Handle(s, "mixed", ns_max=ns)
+    Xd = to_dev(X0, torch.float32)
+    lam = h.chefsi_step(Xd, degree, bounds=(a, b, a0))
+    rX, rlam = o.chefsi_step(X0, degree, a, b, a0)
+    ne = synth.electrons_for(ns)
+    occ = np.arange(ns) < ne // 2
+    err_occ = np.max(np.abs(lam - rlam)[occ])
+    assert err_occ < 1e-5, err_occ
+    X1 = Xd.double().cpu().numpy()
+    assert np.max(np.abs(X1 @ X1.T - np.eye(ns))) < 1e-4
+
+
+@pytest.mark.parametrize("name", ["ring_periodic", "ring_dirichlet_y"])
+def test_ring_and_generic_stencil_agree(name):
+    """The TMA plane-ring form and the generic form of the stencil kernel give
+    the same H X (both FP64; summation order is identical up to the x window)."""
+    s = SYSTEMS[name]()
+    ns = 6
+    X = to_dev(np.random.default_rng(9).standard_normal((ns, s.nd)))
+    ring = sparc.Handle(s, "fp64", ns_max=ns)
+    generic = sparc.Handle(s, "fp64", ns_max=ns, options_flags=1)
+    Y1, Y2 = ring.hpsi(X), generic.hpsi(X)
+    torch.cuda.synchronize()
+    assert float((Y1 - Y2).abs().max()) <= 1e-13 * float(Y2.abs().max())
