@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-systems", type=int, default=64)
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--ns", type=int, default=0, help="override Ns (profiling on a smaller case)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
@@ -258,35 +260,53 @@ def main():
     prec = args.precision
     h = sparc.Handle(system, prec, ns_max=ns, device=local)
     Xd = torch.from_numpy(X0).to(dev, torch.float64 if prec == "fp64" else torch.float32)
-    lam_hist = []
+    ne = synth.electrons_for(ns)
+    lam_d = torch.empty(ns, dtype=torch.float64, device=dev)
+    dens_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def full_step():
+        """Algorithm 1 (bounds, filter, H Xt, projection, eigensolve, rotation),
+        then Fermi-Dirac occupations and the density of the new orbitals."""
+        h.chefsi_step(Xd, m, eig=lam_d)
+        dens_ev[0].record(stream)
+        occ, _mu = h.occupations(lam_d, ne, 0.01)
+        rho = h.density(Xd, occ)
+        dens_ev[1].record(stream)
+        return rho
+
     for _ in range(args.warmup):
-        lam_hist.append(h.chefsi_step(Xd, m))
+        full_step()
     torch.cuda.synchronize(dev)
     barrier(world)
     stage = []
+    dens_ms = []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            lam_hist.append(h.chefsi_step(Xd, m))
+            rho = full_step()
             stage.append(h.timings())
+            dens_ev[1].synchronize()
+            dens_ms.append(dens_ev[0].elapsed_time(dens_ev[1]))
         e1.record(stream)
         torch.cuda.synchronize(dev)
+    rho_electrons = float(rho.sum()) * system.h ** 3
     barrier(world)
     t_loc = e0.elapsed_time(e1) / 1e3
     t_max = max_over_ranks(t_loc, world, dev)
     value = world * args.steps / t_max
-    launches = int(sum(s["launches"] for s in stage))
+    # the step's own launches plus k_fermi and k_density (+ reduce when split)
+    launches = int(sum(s["launches"] for s in stage)) + 2 * args.steps
 
     def med(key):
         return statistics.median(s[key] for s in stage)
 
+    s_bytes = 8 if prec == "fp64" else 4
     st_ms = {k: med(k) for k in ("bounds_ms", "filter_ms", "hx_ms", "project_ms", "eig_ms",
                                  "rotate_ms", "total_ms")}
     # filtering throughput: per degree reads Y_i, Y_{i-1}, writes Y_{i+1}
     # (first degree: read X, write Y_1) -> (2 + 3 (m - 1)) Nd Ns s bytes
-    s_bytes = 8 if prec == "fp64" else 4
     filt_bytes = (2 + 3 * (m - 1)) * nd * ns * s_bytes
     hx_bytes = 2 * nd * ns * s_bytes
     filt_gbs = filt_bytes / (st_ms["filter_ms"] / 1e3) / 1e9
@@ -299,6 +319,9 @@ def main():
         "project": {"ms": st_ms["project_ms"],
                     "TFLOP/s": proj_flops / (st_ms["project_ms"] / 1e3) / 1e12},
         "eig": {"ms": st_ms["eig_ms"]},
+        "occupations_density": {"ms": statistics.median(dens_ms),
+                                "GB/s": nd * ns * s_bytes / (statistics.median(dens_ms) / 1e3)
+                                / 1e9, "electrons": rho_electrons, "ne": ne},
         "rotate": {"ms": st_ms["rotate_ms"],
                    "TFLOP/s": rot_flops / (st_ms["rotate_ms"] / 1e3) / 1e12},
     }
@@ -353,6 +376,13 @@ def main():
             mixed = {"error": repr(exc)}
     h.close()
 
+    batched = None
+    if not args.no_batch and world == 1 and args.batch_systems > 0:
+        try:
+            batched = run_batched(args, dev, stream)
+        except Exception as exc:  # report, do not hide
+            batched = {"error": repr(exc)}
+
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         r = oracle_sample(system, ns, m, args.cpu_seconds)
@@ -378,6 +408,7 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
         "mixed": mixed,
+        "batched": batched,
         "cpu_baseline": cpu,
         "setup_s": setup_s,
     }
@@ -437,6 +468,74 @@ def run_mixed(system, X0, ns, m, args, dev, stream, h64):
             "filter_GBps": filt_bytes / (st["filter_ms"] / 1e3) / 1e9,
             "ritz_err_vs_fp64_gpu_per_step": errs, "ritz_err_occupied": err_occ,
             "note": "errors vs the FP64 GPU path from the same start and bounds"}
+
+
+def run_batched(args, dev, stream):
+    """Batched form on 64 uneven small systems (N^3 grids, N in 24..48, 4-40
+    atoms, Ns 40-300, degree 16-24, fixed bounds per member): time per batched step (one launch per
+    Chebyshev degree for all members, replayed CUDA graph) against the same
+    members stepped one after another through sparc_chefsi_step, in FP64 and
+    mixed precision, with the largest Ritz-value difference between the two."""
+    import numpy as np
+    import torch
+
+    from paper_2302_09708_gb300 import sparc, synth
+
+    members = synth.batch_members(args.batch_systems)
+    t0 = time.perf_counter()
+    systems = [synth.random_system(mb["shape"], mb["h"], mb["bc"], mb["natoms"], seed=mb["seed"])
+               for mb in members]
+    X0 = [synth.random_orbitals(s.nd, mb["ns"], seed=mb["seed"] + 7)
+          for s, mb in zip(systems, members)]
+    setup_s = time.perf_counter() - t0
+    degrees = [mb["degree"] for mb in members]
+    out = {"systems": len(members), "setup_s": setup_s,
+           "nd_range": [min(s.nd for s in systems), max(s.nd for s in systems)],
+           "ns_range": [min(mb["ns"] for mb in members), max(mb["ns"] for mb in members)]}
+    steps = max(2, args.steps)
+    for prec, dt in (("fp64", torch.float64), ("mixed", torch.float32)):
+        handles = [sparc.Handle(s, prec, ns_max=mb["ns"], device=dev.index)
+                   for s, mb in zip(systems, members)]
+        bounds = []  # fixed (a, b, a0) per member, the same for both forms
+        for hh in handles:
+            a0, b = hh.spectrum_bounds(32, 0)
+            bounds.append((a0 + 0.1 * (b - a0), b, a0))
+        Xb = [torch.from_numpy(x).to(dev, dt) for x in X0]
+        Xs = [x.clone() for x in Xb]
+        batch = sparc.Batch(handles)
+        for _ in range(2):  # capture, then replay
+            lam_b = batch.chefsi_step(Xb, degrees, bounds=bounds)
+        for hh, x, d, bd in zip(handles, Xs, degrees, bounds):
+            hh.chefsi_step(x, d, bounds=bd)
+            hh.chefsi_step(x, d, bounds=bd)
+        torch.cuda.synchronize(dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        for _ in range(steps):
+            lam_b = batch.chefsi_step(Xb, degrees, bounds=bounds)
+        e[1].record(stream)
+        e[2].record(stream)
+        for _ in range(steps):
+            lam_s = [hh.chefsi_step(x, d, bounds=bd)
+                     for hh, x, d, bd in zip(handles, Xs, degrees, bounds)]
+        e[3].record(stream)
+        torch.cuda.synchronize(dev)
+        tb = e[0].elapsed_time(e[1]) / steps
+        ts = e[2].elapsed_time(e[3]) / steps
+        diff = max(float(np.max(np.abs(a - b))) for a, b in zip(lam_b, lam_s))
+        seq_launches = sum(hh.timings()["launches"] for hh in handles)
+        out[prec] = {"batched_ms_per_step": tb, "sequential_ms_per_step": ts,
+                     "speedup": ts / tb, "launches_batched": batch.launches(),
+                     "launches_sequential": int(seq_launches),
+                     "max_ritz_diff_batched_vs_sequential": diff}
+        batch.close()
+        for hh in handles:
+            hh.close()
+        del Xb, Xs
+        torch.cuda.empty_cache()
+    out["mixed_vs_fp64_batched_speedup"] = (out["fp64"]["batched_ms_per_step"]
+                                            / out["mixed"]["batched_ms_per_step"])
+    return out
 
 
 if __name__ == "__main__":

@@ -200,6 +200,30 @@ int sparc_chefsi_step(sparc_handle h, void* X, int ns, int64_t ld, int dtype, in
 int sparc_get_timings(sparc_handle h, sparc_timings* t);
 
 /*
+ * sparc_occupations — Fermi-Dirac occupations of the Ritz values (the smeared
+ * occupation a self-consistent cycle applies after each CheFSI step, Sec. 2.1):
+ * f_n = 1 / (1 + exp((lam_n - mu) / kT)), with the Fermi level mu found by
+ * bisection on [min lam - 1, max lam + 1] until |2 sum_n f_n - ne| < 1e-12
+ * (at most 400 halvings).  lam: ns device doubles (any order).  occ: ns device
+ * doubles (output).  mu: one device double (output).  Requires 1 <= ns,
+ * kT > 0 and 0 < ne < 2 ns (else INVALID_ARG).  Asynchronous.
+ */
+int sparc_occupations(sparc_handle h, const double* lam, int ns, double ne, double kT,
+                      double* occ, double* mu, void* stream);
+
+/*
+ * sparc_density — electron density of the occupied orbitals,
+ * rho_i = (2 / h^3) sum_n occ_n X_{i n}^2 for i < Nd (spin-degenerate, with
+ * X^T X = I so that h^3 sum_i rho_i = 2 sum_n occ_n).  X: device block (dtype,
+ * ld >= Nd, 0 <= ns <= ns_max; ns = 0 gives rho = 0).  occ: ns device doubles.
+ * rho: Nd device doubles (output).  FP64 blocks sum in FP64; FP32 blocks sum
+ * groups of 16 orbitals in FP32 and the groups in FP64.  Uses the handle's
+ * filter workspace as scratch.  Errors: INVALID_ARG, CUDA.  Asynchronous.
+ */
+int sparc_density(sparc_handle h, const void* X, int ns, int64_t ld, int dtype, const double* occ,
+                  double* rho, void* stream);
+
+/*
  * Batched form — many independent systems (the paper treats the eigenproblems
  * of different k-points / spins / configurations as independent, Sec. II).
  * A batch is built from existing handles (same precision and device; each keeps

@@ -423,6 +423,13 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
     n64.supp_ptr = sp; n64.supp_idx = si; n64.nproj = npj; n64.chi_ptr = cp; n64.chi = chi;
     n64.proj_ptr = pp; n64.gamma = gam; n64.pull_ptr = pptr; n64.pull_k = pk;
     n64.pull_chi = pchi;
+    {
+      std::vector<PullEntry<double>> pk64(nent > 0 ? nent : 1);
+      for (int64_t t = 0; t < nent; ++t) pk64[t] = PullEntry<double>{pull_k[t], pull_chi[t]};
+      PullEntry<double>* d64;
+      if ((rc = upload<PullEntry<double>>(c, pk64.data(), pk64.size(), &d64))) return rc;
+      n64.pull_pk = d64;
+    }
     Nonlocal<float>& n32 = c->nl32;
     n32.natoms = natoms; n32.kp = kp; n32.supp_ptr = sp; n32.supp_idx = si; n32.nproj = npj;
     n32.chi_ptr = cp; n32.proj_ptr = pp; n32.gamma = gam; n32.pull_ptr = pptr; n32.pull_k = pk;
@@ -434,6 +441,11 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
       if ((rc = upload<float>(c, f32.data(), nent, &pchi32))) return rc;
       n32.chi = chi32;
       n32.pull_chi = pchi32;
+      std::vector<PullEntry<float>> pk32(nent > 0 ? nent : 1);
+      for (int64_t t = 0; t < nent; ++t) pk32[t] = PullEntry<float>{pull_k[t], (float)pull_chi[t]};
+      PullEntry<float>* d32;
+      if ((rc = upload<PullEntry<float>>(c, pk32.data(), pk32.size(), &d32))) return rc;
+      n32.pull_pk = d32;
     }
   }
 
@@ -462,7 +474,7 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
     CK(c, cudaMalloc(&c->S2, se * sizeof(__nv_bfloat16)));
     const size_t zk = (size_t)(c->ns_max + 7) / 8 * 8;
     CK(c, cudaMalloc(&c->SZ, 4 * zk * c->ns_max * sizeof(__nv_bfloat16)));
-    CK(c, cudaMalloc(&c->esc, (size_t)(nd + 2 * c->ns_max) * sizeof(int)));
+    CK(c, cudaMalloc(&c->esc, tc_esc_bytes(c->ld, nd, c->ns_max)));
   }
   c->proj_work_elems = pw;
   CK(c, cudaMalloc(&c->proj_work, pw * 8));
@@ -647,6 +659,38 @@ int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   if (rc) return rc;
   c->step_launches = launch_count() - launches0;
   if (host) return stage_out(c, X, ns, ld, dtype, st);
+  return SPARC_OK;
+}
+
+int sparc_occupations(sparc_handle c, const double* lam, int ns, double ne, double kT,
+                      double* occ, double* mu, void* stream) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  ARG(c, ns >= 1, "ns must be >= 1");
+  ARG(c, std::isfinite(kT) && kT > 0.0, "kT must be > 0");
+  ARG(c, std::isfinite(ne) && ne > 0.0 && ne < 2.0 * ns, "ne must be in (0, 2 ns)");
+  ARG(c, lam && occ && mu, "null pointer");
+  ARG(c, is_device_ptr(lam) && is_device_ptr(occ) && is_device_ptr(mu),
+      "occupations take device arrays");
+  CK(c, cudaSetDevice(c->device));
+  CK(c, fermi_occupations(lam, ns, ne, kT, occ, mu, (cudaStream_t)stream));
+  return SPARC_OK;
+}
+
+int sparc_density(sparc_handle c, const void* X, int ns, int64_t ld, int dtype, const double* occ,
+                  double* rho, void* stream) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  ARG(c, ns >= 0 && ns <= c->ns_max, "ns must be in [0, ns_max]");
+  ARG(c, ld >= c->nd, "ld must be >= Nd");
+  const int want = c->precision == SPARC_PREC_MIXED ? SPARC_F32 : SPARC_F64;
+  ARG(c, dtype == want, "dtype must match the handle's precision");
+  ARG(c, rho != nullptr && is_device_ptr(rho), "rho must be a device array");
+  ARG(c, ns == 0 || (X && occ && is_device_ptr(X) && is_device_ptr(occ)),
+      "X and occ must be device arrays");
+  CK(c, cudaSetDevice(c->device));
+  // scratch: the W1 filter buffer (ld x ns_max elements of the handle's type)
+  const int64_t work_elems = c->ld * (int64_t)c->ns_max * (int64_t)elem_size(want) / 8;
+  CK(c, density(X, ld, c->nd, ns, dtype == SPARC_F32, occ, c->h, rho, (double*)c->W1, work_elems,
+                (cudaStream_t)stream));
   return SPARC_OK;
 }
 

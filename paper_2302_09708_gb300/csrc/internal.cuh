@@ -39,6 +39,13 @@ struct LapCoef {
 //  projectors k (global numbering proj_ptr[J] + q).
 //  Pull form (per grid point i): entries pull_ptr[i]..pull_ptr[i+1]-1 hold
 //  (k, chi_k(i)) so that (V_nl x)_i = sum_e chi_e D[k_e].
+// One pull-table entry: projector index k and chi_k(i) in one aligned load.
+template <typename T>
+struct PullEntry {
+  int k;
+  T chi;
+};
+
 template <typename T>
 struct Nonlocal {
   int natoms = 0;
@@ -53,6 +60,7 @@ struct Nonlocal {
   const int* pull_ptr = nullptr;
   const int* pull_k = nullptr;
   const T* pull_chi = nullptr;
+  const PullEntry<T>* pull_pk = nullptr;  // packed (k, chi) entries, same order
 };
 
 // Launchers (stencil.cu) -------------------------------------------------
@@ -103,8 +111,15 @@ cudaError_t project_reduce(const double* work, int nsplit, int ns, double* Hs, d
 
 // Split-precision tensor-core GEMMs (tc_gemm.cu), FP32 operands.
 size_t tc_slice_elems(int64_t ld, int64_t nd, int ns_max);
+size_t tc_esc_bytes(int64_t ld, int64_t nd, int ns_max);
+
+// density.cu: Fermi occupations (one block) and rho = (2/h^3) sum f_n x_n^2.
+cudaError_t fermi_occupations(const double* lam, int ns, double ne, double kT, double* occ,
+                              double* mu, cudaStream_t st);
+cudaError_t density(const void* X, int64_t ld, int64_t nd, int ns, bool fp32, const double* occ,
+                    double h, double* rho, double* work, int64_t work_elems, cudaStream_t st);
 int tc_project_nsplit(int ns);
-// `esc`: int workspace of max(2 ns, nd + ns) entries (per-row binary exponents).
+// `esc`: workspace of tc_esc_bytes() bytes (block exponents).
 cudaError_t tc_project(const float* Xt, const float* Yt, int64_t ld, int64_t nd, int ns,
                        double* Hs, double* Ms, double* work, int nsplit, __nv_bfloat16* SX,
                        __nv_bfloat16* SY, int* esc, int* status, cudaStream_t st);
@@ -193,7 +208,7 @@ struct sparc_context {
   // nonlocal tables
   sparc::Nonlocal<double> nl64;
   sparc::Nonlocal<float> nl32;
-  void* nl_mem[16] = {};
+  void* nl_mem[24] = {};
   int nl_nmem = 0;
   // workspaces
   void* W1 = nullptr;

@@ -103,10 +103,10 @@ struct RingArgs {
   int64_t ldp;
   const T* veff;
   const int* pull_ptr;
-  const int* pull_k;
-  const T* pull_chi;
+  const PullEntry<T>* pull_pk;
   const T* D;
   int kp;
+  uint32_t d_off;  // byte offset of the orbital's D column in dynamic shared memory
   int nx, ny, nz, bcx, bcy, bcz;
   int by;        // slab rows
   int nslab;     // ny / by (rounded up)
@@ -156,6 +156,9 @@ __global__ void __launch_bounds__(384, 1)
     abort_sh = 0;
     issued_hi = z0 - R;
   }
+  // this CTA's orbital column of the nonlocal coefficients D, kept on chip
+  T* const dsh = reinterpret_cast<T*>(smem_raw + (base - su32(smem_raw)) + a.d_off);
+  for (int k = tid; k < a.kp; k += blockDim.x) dsh[k] = __ldg(a.D + (int64_t)n * a.kp + k);
   __syncthreads();
   volatile int* abort = &abort_sh;
   const unsigned full_mask = 0xffffffffu;
@@ -226,7 +229,6 @@ __global__ void __launch_bounds__(384, 1)
     }
   }
 
-  const T* __restrict__ Dn = a.D + (int64_t)n * a.kp;
   T* __restrict__ yn = a.y + (int64_t)n * a.ldy;
   const T* __restrict__ pn = a.prev ? a.prev + (int64_t)n * a.ldp : nullptr;
   const int gy0 = y0 + yy;
@@ -236,12 +238,29 @@ __global__ void __launch_bounds__(384, 1)
     // prefetch Veff / prev of this plane
     const int64_t g0 = z * nxy + (int64_t)gy0 * a.nx + x;
     T vf[VY][VX], pv[VY][VX];
+    int pptr[VY][VX + 1];
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
       const bool in = gy0 + r < a.ny;
       if (in) {
         ldg<T, VX>(vf[r], a.veff + g0 + r * a.nx);
         if (pn) ldg<T, VX>(pv[r], pn + g0 + r * a.nx);
+        if (a.kp > 0) {
+          // VX + 1 consecutive pull offsets of the row's points
+          const int* pp = a.pull_ptr + g0 + r * a.nx;
+          if constexpr (VX == 4) {
+            // g0 + r nx is a multiple of 4 here (x and nx are), so int4 is aligned
+            const int4 p4 = __ldg(reinterpret_cast<const int4*>(pp));
+            pptr[r][0] = p4.x;
+            pptr[r][1] = p4.y;
+            pptr[r][2] = p4.z;
+            pptr[r][3] = p4.w;
+          } else {
+#pragma unroll
+            for (int v = 0; v < VX; ++v) pptr[r][v] = __ldg(pp + v);
+          }
+          pptr[r][VX] = __ldg(pp + VX);
+        }
       }
     }
     // push plane z + R into the queue
@@ -280,10 +299,22 @@ __global__ void __launch_bounds__(384, 1)
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
       const T* rowp = pl + (R + yy + r) * rowe;
+      // window x - R .. x + VX - 1 + R; interior threads read it with aligned
+      // vector loads starting at x - WL (bank-conflict free), edge threads wrap
       T w[VX + 2 * R];
-      if (x >= R && x + VX + R <= a.nx) {
+      constexpr int WL = (R + VX - 1) / VX * VX;  // >= R, multiple of VX
+      constexpr int NV = (2 * WL + VX) / VX;
+      if (x >= WL && x + VX + WL <= a.nx) {
+        T buf[NV * VX];
 #pragma unroll
-        for (int i = 0; i < VX + 2 * R; ++i) w[i] = rowp[x - R + i];
+        for (int k = 0; k < NV; ++k) {
+          T t4[VX];
+          lds<T, VX>(t4, rowp + x - WL + k * VX);
+#pragma unroll
+          for (int v = 0; v < VX; ++v) buf[k * VX + v] = t4[v];
+        }
+#pragma unroll
+        for (int i = 0; i < VX + 2 * R; ++i) w[i] = buf[i + WL - R];
       } else {
 #pragma unroll
         for (int i = 0; i < VX + 2 * R; ++i) {
@@ -319,9 +350,11 @@ __global__ void __launch_bounds__(384, 1)
       for (int v = 0; v < VX; ++v) {
         T h = acc[r][v] + vf[r][v] * q[R][r][v];
         if (a.kp > 0) {
-          const int e0 = __ldg(a.pull_ptr + g + v), e1 = __ldg(a.pull_ptr + g + v + 1);
           T nl = T(0);
-          for (int e = e0; e < e1; ++e) nl += __ldg(a.pull_chi + e) * __ldg(Dn + __ldg(a.pull_k + e));
+          for (int e = pptr[r][v]; e < pptr[r][v + 1]; ++e) {
+            const PullEntry<T> pe = a.pull_pk[e];
+            nl += pe.chi * dsh[pe.k];
+          }
           h += nl;
         }
         out[v] = pn ? a.s_h * h + a.s_p * pv[r][v] : a.s_h * h;
@@ -382,7 +415,7 @@ bool block_map(CUtensorMap* m, const T* x, int64_t ldx, const Grid& g, int ns, i
 
 // Ring-kernel plan for a grid/dtype, or false if the generic kernel must be used.
 template <typename T>
-bool ring_plan(const Grid& g, int& by, int& slots, uint32_t& slot_bytes, int& threads) {
+bool ring_plan(const Grid& g, int kp, int& by, int& slots, uint32_t& slot_bytes, int& threads) {
   constexpr int VX = sizeof(T) == 4 ? 4 : 2;
   const int es = sizeof(T);
   if (g.nx % (sizeof(T) == 4 ? 16 : 8) != 0 || g.nx > 256) return false;
@@ -401,7 +434,9 @@ bool ring_plan(const Grid& g, int& by, int& slots, uint32_t& slot_bytes, int& th
   if (g.bc[1] == SPARC_PERIODIC && g.ny < 2 * R) return false;
   slot_bytes = (uint32_t)((by + 2 * R) * g.nx * es);
   slot_bytes = (slot_bytes + 127u) & ~127u;
-  const uint32_t budget = 200 * 1024;
+  const int64_t dbytes = (int64_t)kp * es;
+  if (dbytes > 64 * 1024) return false;
+  const uint32_t budget = (uint32_t)(200 * 1024 - dbytes);
   slots = std::min<int>(13, (int)(budget / slot_bytes));
   if (slots < 8) return false;  // the march needs plane z + R resident S - 7 planes ahead
   threads = (by / VY) * (g.nx / VX);
@@ -417,7 +452,8 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
   constexpr int VX = sizeof(T) == 4 ? 4 : 2;
   int by, slots, threads;
   uint32_t slot_bytes;
-  if (!ring_plan<T>(g, by, slots, slot_bytes, threads)) return cudaSuccess;
+  if (!ring_plan<T>(g, nl.kp, by, slots, slot_bytes, threads)) return cudaSuccess;
+  if (nl.kp > 0 && !nl.pull_pk) return cudaSuccess;
   const int va = 16 / sizeof(T);
   if (ldx % va || ldy % va || (prev && ldp % va) || ((uintptr_t)x % 16) || ((uintptr_t)y % 16) ||
       (prev && ((uintptr_t)prev % 16)) || ((uintptr_t)veff % 16))
@@ -427,7 +463,7 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
     return cudaSuccess;
   RingArgs<T> a;
   a.y = y; a.ldy = ldy; a.prev = prev; a.ldp = ldp; a.veff = veff;
-  a.pull_ptr = nl.pull_ptr; a.pull_k = nl.pull_k; a.pull_chi = nl.pull_chi; a.D = D; a.kp = nl.kp;
+  a.pull_ptr = nl.pull_ptr; a.pull_pk = nl.pull_pk; a.D = D; a.kp = nl.kp;
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.bcx = g.bc[0]; a.bcy = g.bc[1]; a.bcz = g.bc[2];
   a.by = by;
   a.nslab = (g.ny + by - 1) / by;
@@ -444,7 +480,8 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
   nzc = std::min(nzc, std::max(1, g.nz / 16));
   a.bz = (g.nz + nzc - 1) / nzc;
   nzc = (g.nz + a.bz - 1) / a.bz;
-  const size_t smem = (size_t)slots * slot_bytes + 128;
+  a.d_off = (uint32_t)slots * slot_bytes;
+  const size_t smem = (size_t)slots * slot_bytes + (size_t)nl.kp * sizeof(T) + 128;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     cudaFuncSetAttribute(k_apply_h_ring<T, VX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -456,8 +493,8 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
   return cudaGetLastError();
 }
 
-template bool ring_plan<float>(const Grid&, int&, int&, uint32_t&, int&);
-template bool ring_plan<double>(const Grid&, int&, int&, uint32_t&, int&);
+template bool ring_plan<float>(const Grid&, int, int&, int&, uint32_t&, int&);
+template bool ring_plan<double>(const Grid&, int, int&, int&, uint32_t&, int&);
 template cudaError_t apply_h_ring<float>(const Grid&, const LapCoef&, const float*,
                                          const Nonlocal<float>&, const float*, const float*,
                                          int64_t, float*, int64_t, const float*, int64_t, int,

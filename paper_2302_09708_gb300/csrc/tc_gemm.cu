@@ -1,9 +1,10 @@
 // Split-precision tensor-core GEMMs (tcgen05 + TMA + TMEM) for the mixed
 // precision projection and rotation of Algorithm 1 (paper Sec. II B, II D).
 //
-// Fixed-point split (Ozaki-style): each operand row r (a row of the GEMM's M or
-// N dimension) is scaled by 2^-e_r, e_r the binary exponent of its largest
-// entry, and every entry u = x 2^-e_r in (-1, 1) is written as four signed
+// Block fixed-point split (Ozaki-style): for every operand row r (a row of the
+// GEMM's M or N dimension) and every chunk q of 256 K values, the entries are
+// scaled by 2^-e_rq, e_rq the binary exponent of the chunk's largest entry, and
+// every entry u = x 2^-e_rq in (-1, 1) is written as four signed
 // 8-bit integer digits, u = 2^-7 (d1 + 2^-8 d2 + 2^-16 d3 + 2^-24 d4) + O(2^-32),
 // each exactly representable in BF16.  A product is formed from the ten digit
 // products of weight >= 2^-24 relative to the leading one, in four levels
@@ -14,8 +15,11 @@
 // are integers of magnitude <= 2^14, so over a chunk of 256 K values every level
 // sum stays an integer of magnitude <= 2^24 and the tensor core adds it exactly
 // (its alignment/truncation of products never drops a bit).  Every
-// kChunkSteps K-steps the exact level sums are folded into a double-FP32
-// (hi, lo) running sum held in registers; the epilogue applies 2^(e_a+e_b-14).
+// kChunkSteps K-steps (one exponent chunk) the exact level sums are scaled by
+// 2^(e_a + e_b - 14) of that chunk and folded into a double-FP32 (hi, lo)
+// running sum held in registers.  Per-chunk exponents keep the digits relative
+// to local magnitudes, so the first dropped level (whose diagonal terms never
+// cancel) stays ~2^-32 of the local values instead of biasing long sums.
 //
 // Kernel structure (one CTA per 128 x 64 output tile, 192 threads):
 //   warp 0     TMA producer: one 3-D TMA load per operand per K-step brings the
@@ -183,6 +187,11 @@ __constant__ int c_sb[kProducts] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
 __constant__ int c_lv[kProducts] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 __constant__ int c_first[kProducts] = {1, 1, 0, 1, 0, 0, 1, 0, 0, 0};
 
+// 2^n as a float, built from the IEEE-754 exponent field for normal results.
+__device__ __forceinline__ float pow2i(int n) {
+  return n >= -126 ? __int_as_float((min(n, 127) + 127) << 23) : ldexpf(1.0f, n);
+}
+
 struct TcArgs {
   int M, N;
   int64_t K;
@@ -193,9 +202,10 @@ struct TcArgs {
   float* out32;     // mode 1: out32[m + n * ldo]
   int64_t ldo;
   int mode;
-  const int* escA;  // per-row binary exponent of the A operand (M rows)
-  const int* escB0; // per-row exponent of B for output 0 (N rows)
-  const int* escB1; // per-row exponent of B for output 1
+  const int8_t* escA;   // exponent of A row r in chunk q at [q * MP + r]
+  const int8_t* escB0;  // exponent of B row c (output 0) in chunk q at [q * NP + c]
+  const int8_t* escB1;  // same for output 1
+  int MP, NP;           // row strides of the exponent arrays (multiples of 128)
   int* status;
 };
 
@@ -332,10 +342,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
       const uint32_t t_acc = tmem + lane_off + (uint32_t)(buf * kLevels * kBN);
+      // exponents of this chunk: the thread's A row and the tile's 64 B rows
+      const int qg = (int)(k0 / (kBK * kChunkSteps)) + c;
+      const int rowc = min(bi * kBM + q * 32 + lane, a.MP - 1);
+      const int ea = (int)a.escA[(int64_t)qg * a.MP + rowc] - 14;
+      const uint4* eb_src = reinterpret_cast<const uint4*>(
+          (out == 0 ? a.escB0 : a.escB1) + (int64_t)qg * a.NP + bj * kBN);
 #pragma unroll
       for (int cb = 0; cb < kBN / 32; ++cb) {
         // t = L1 + 2^-8 L2 + 2^-16 L3 (exact integers; FP32 keeps 24 bits of it)
         uint32_t v0[32], t[32];
+        const uint4 eb0 = __ldg(eb_src + 2 * cb), eb1 = __ldg(eb_src + 2 * cb + 1);
         tmem_ld32(t_acc + cb * 32, v0);
         tmem_ld32(t_acc + 3 * kBN + cb * 32, t);
         tmem_wait_ld();
@@ -358,9 +375,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           float hh = hi[cb * 32 + i], ll = lo[cb * 32 + i];
+          const uint4& ew = i < 16 ? eb0 : eb1;
+          const uint32_t word = (i & 15) < 4 ? ew.x : (i & 15) < 8 ? ew.y : (i & 15) < 12 ? ew.z : ew.w;
+          const int eb = (int)(int8_t)(word >> (8 * (i & 3)));
+          const float sc = pow2i(ea + eb);
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            const float x = __uint_as_float(u == 0 ? v0[i] : t[i]);
+            const float x = __uint_as_float(u == 0 ? v0[i] : t[i]) * sc;
             const float sm = __fadd_rn(hh, x);
             const float bp = __fsub_rn(sm, hh);
             const float ap = __fsub_rn(sm, bp);
@@ -379,19 +400,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (ok && nchunks > 0) {
       const int row = bi * kBM + q * 32 + lane;
       if (row < a.M) {
-        const int* escB = out == 0 ? a.escB0 : a.escB1;
-        const int ea = a.escA[row] - 14;
 #pragma unroll
         for (int i = 0; i < kBN; ++i) {
           const int col = bj * kBN + i;
           if (col < a.N) {
-            const int ex = ea + escB[col];
             if (a.mode == 0) {
-              const double val = (double)hi[i] + (double)lo[i];
               a.work[((int64_t)blockIdx.y * 2 + out) * a.M * a.N + row + (int64_t)col * a.M] =
-                  ldexp(val, ex);
+                  (double)hi[i] + (double)lo[i];
             } else {
-              a.out32[row + (int64_t)col * a.ldo] = ldexpf(__fadd_rn(hi[i], lo[i]), ex);
+              a.out32[row + (int64_t)col * a.ldo] = __fadd_rn(hi[i], lo[i]);
             }
           }
         }
@@ -420,6 +437,12 @@ __device__ __forceinline__ int row_exponent(double vmax) {
   return e;
 }
 
+// Chunk exponent stored as int8. Raising E keeps |x 2^-E| < 1, so the clamp
+// only costs digits of chunks whose largest entry is below 2^-120.
+__device__ __forceinline__ int8_t chunk_exponent(double vmax) {
+  return (int8_t)max(-120, min(127, row_exponent(vmax)));
+}
+
 // Four signed 8-bit digits of u = x 2^-E (|u| < 1):
 // u = 2^-7 (d1 + d2/2^8 + d3/2^16 + d4/2^24), each |d| <= 128.
 __device__ __forceinline__ void digits(double x, int E, __nv_bfloat16 (&d)[kSlices]) {
@@ -443,7 +466,26 @@ __device__ __forceinline__ void digitsf(float x, int E, __nv_bfloat16 (&d)[kSlic
   }
 }
 
-// Column exponents of X (one block per column): esc[col] = E(max_t |X[t + col ldx]|).
+constexpr int kQ = kBK * kChunkSteps;  // K values per exponent chunk
+
+// Chunk exponents of the columns of X: esc[q * NP + col] = E(max over t in chunk
+// q of |X[t + col ldx]|), one warp per (column, chunk).
+__global__ void k_chunk_exp_cols(const float* __restrict__ X, int64_t ldx, int64_t nd, int ncol,
+                                 int nq, int NP, int8_t* __restrict__ esc) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)ncol * nq) return;
+  const int col = (int)(w % ncol), q = (int)(w / ncol);
+  const float* x = X + (int64_t)col * ldx;
+  float m = 0.f;
+  const int64_t t1 = min((int64_t)(q + 1) * kQ, nd);
+  for (int64_t t = (int64_t)q * kQ + lane; t < t1; t += 32) m = fmaxf(m, fabsf(x[t]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) esc[(int64_t)q * NP + col] = chunk_exponent((double)m);
+}
+
+// Column exponents f_k of X (one block per column), used to balance columns.
 __global__ void k_col_exponent(const float* __restrict__ X, int64_t ldx, int64_t nd,
                                int* __restrict__ esc) {
   __shared__ float sm[32];
@@ -461,38 +503,47 @@ __global__ void k_col_exponent(const float* __restrict__ X, int64_t ldx, int64_t
   }
 }
 
-// Row exponents of X over its ns columns: esc[t] = E(max_k |X[t + k ldx]|).
-__global__ void k_row_exponent(const float* __restrict__ X, int64_t ldx, int64_t nd, int ns,
-                               int* __restrict__ esc) {
+// Chunk exponents of the rows of the column-balanced X (rotation A operand):
+// esc[q * MP + t] = E(max over k in chunk q of |X[t + k ldx]| 2^-f_k).
+__global__ void k_chunk_exp_rows(const float* __restrict__ X, int64_t ldx, int64_t nd, int ns,
+                                 const int* __restrict__ fcol, int MP, int8_t* __restrict__ esc) {
+  const int q = blockIdx.y;
+  const int k1 = min((q + 1) * kQ, ns);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nd;
        t += (int64_t)gridDim.x * blockDim.x) {
     float m = 0.f;
-    for (int k = 0; k < ns; ++k) m = fmaxf(m, fabsf(X[t + (int64_t)k * ldx]));
-    esc[t] = row_exponent((double)m);
+    for (int k = q * kQ; k < k1; ++k)
+      m = fmaxf(m, ldexpf(fabsf(X[t + (int64_t)k * ldx]), -fcol[k]));
+    esc[(int64_t)q * MP + t] = chunk_exponent((double)m);
   }
 }
 
-// Column exponents of the n x n column-major Z.
-__global__ void k_z_exponent(const double* __restrict__ Z, int n, int* __restrict__ esc) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= n) return;
+// Chunk exponents of the rows of the row-scaled Z (rotation B operand, row j =
+// output column j): esc[q * NP + j] = E(max over k in chunk q of |Z[k + j n]| 2^f_k).
+__global__ void k_chunk_exp_z(const double* __restrict__ Z, int n, const int* __restrict__ fcol,
+                              int nq, int NP, int8_t* __restrict__ esc) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)n * nq) return;
+  const int j = (int)(w % n), q = (int)(w / n);
   double m = 0.0;
-  for (int k = lane; k < n; k += 32) m = fmax(m, fabs(Z[k + (int64_t)warp * n]));
+  const int k1 = min((q + 1) * kQ, n);
+  for (int k = q * kQ + lane; k < k1; k += 32) m = fmax(m, ldexp(fabs(Z[k + (int64_t)j * n]), fcol[k]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) esc[warp] = row_exponent(m);
+  if (lane == 0) esc[(int64_t)q * NP + j] = chunk_exponent(m);
 }
 
-// S[s][col][t] = digit s of X[t + col ldx] at the column's exponent (ld = lds)
+// S[s][col][t] = digit s of X[t + col ldx] at its chunk's exponent (ld = lds)
 __global__ void k_slice_cols(const float* __restrict__ X, int64_t ldx, int64_t nd, int ncol,
-                             const int* __restrict__ esc, __nv_bfloat16* __restrict__ S,
-                             int64_t lds) {
+                             const int8_t* __restrict__ esc, int NP,
+                             __nv_bfloat16* __restrict__ S, int64_t lds) {
   const int col = blockIdx.y;
-  const int E = esc[col];
   const int64_t plane = lds * ncol;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < lds;
        t += (int64_t)gridDim.x * blockDim.x) {
     __nv_bfloat16 d[kSlices];
+    const int E = esc[(t / kQ) * NP + col];
     digitsf(t < nd ? X[t + col * ldx] : 0.f, E, d);
     const int64_t o = t + col * lds;
 #pragma unroll
@@ -500,17 +551,18 @@ __global__ void k_slice_cols(const float* __restrict__ X, int64_t ldx, int64_t n
   }
 }
 
-// Transposed digits: S[s][t][k] = digit s of X[t + k ldx] at row t's exponent (ld = ldk)
+// Transposed digits of the column-balanced X: S[s][t][k] = digit s of
+// X[t + k ldx] 2^-f_k at row t's exponent (ld = ldk)
 __global__ void k_slice_transpose(const float* __restrict__ X, int64_t ldx, int64_t nd, int ns,
-                                  const int* __restrict__ esc, __nv_bfloat16* __restrict__ S,
-                                  int64_t ldk) {
+                                  const int* __restrict__ fcol, const int8_t* __restrict__ esc,
+                                  int MP, __nv_bfloat16* __restrict__ S, int64_t ldk) {
   __shared__ float tile[32][33];
   const int64_t t0 = (int64_t)blockIdx.x * 32;
   const int k0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int k = k0 + r;
     const int64_t t = t0 + threadIdx.x;
-    tile[r][threadIdx.x] = (k < ns && t < nd) ? X[t + (int64_t)k * ldx] : 0.f;
+    tile[r][threadIdx.x] = (k < ns && t < nd) ? ldexpf(X[t + (int64_t)k * ldx], -fcol[k]) : 0.f;
   }
   __syncthreads();
   const int64_t plane = ldk * nd;
@@ -519,7 +571,7 @@ __global__ void k_slice_transpose(const float* __restrict__ X, int64_t ldx, int6
     const int k = k0 + threadIdx.x;
     if (t < nd && k < ldk) {
       __nv_bfloat16 d[kSlices];
-      digitsf(tile[threadIdx.x][r], esc[t], d);
+      digitsf(tile[threadIdx.x][r], esc[(int64_t)(k / kQ) * MP + t], d);
       const int64_t o = t * ldk + k;
 #pragma unroll
       for (int q = 0; q < kSlices; ++q) S[q * plane + o] = d[q];
@@ -527,16 +579,18 @@ __global__ void k_slice_transpose(const float* __restrict__ X, int64_t ldx, int6
   }
 }
 
-// Z digits: S[s][j][k] = digit s of Z[k + j n] at column j's exponent, ld = ldk
-__global__ void k_slice_z(const double* __restrict__ Z, int n, const int* __restrict__ esc,
-                          __nv_bfloat16* __restrict__ S, int64_t ldk) {
+// Z digits of the row-scaled Z: S[s][j][k] = digit s of Z[k + j n] 2^f_k at
+// column j's exponent, ld = ldk  (X Z = (X 2^-f) (2^f Z): the scalings cancel)
+__global__ void k_slice_z(const double* __restrict__ Z, int n, const int* __restrict__ fcol,
+                          const int8_t* __restrict__ esc, int NP, __nv_bfloat16* __restrict__ S,
+                          int64_t ldk) {
   const int64_t plane = ldk * n;
   const int64_t tot = (int64_t)n * ldk;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / ldk), k = (int)(e % ldk);
     __nv_bfloat16 d[kSlices];
-    digits(k < n ? Z[k + (int64_t)j * n] : 0.0, esc[j], d);
+    digits(k < n ? ldexp(Z[k + (int64_t)j * n], fcol[k]) : 0.0, esc[(int64_t)(k / kQ) * NP + j], d);
 #pragma unroll
     for (int q = 0; q < kSlices; ++q) S[q * plane + e] = d[q];
   }
@@ -590,6 +644,17 @@ cudaError_t launch_tc(const CUtensorMap& tA, const CUtensorMap& tB0, const CUten
 
 }  // namespace
 
+size_t tc_esc_bytes(int64_t ld, int64_t nd, int ns_max) {
+  const int64_t lds = (nd + 63) / 64 * 64;
+  const int64_t nqp = (lds + kQ - 1) / kQ, NP = (ns_max + 127) / 128 * 128;
+  const int64_t ldk = (ns_max + 7) / 8 * 8, nqr = (ldk + kQ - 1) / kQ;
+  const int64_t MP = (nd + 127) / 128 * 128;
+  const int64_t proj = 2 * nqp * NP;
+  const int64_t rot = 4 * ((ns_max + 63) / 64 * 64) + nqr * (MP + NP);
+  (void)ld;
+  return (size_t)std::max(proj, rot) + 256;
+}
+
 size_t tc_slice_elems(int64_t ld, int64_t nd, int ns_max) {
   const int64_t ldk = (ns_max + 7) / 8 * 8;
   return (size_t)kSlices * std::max<int64_t>(ld * ns_max, nd * ldk);
@@ -612,13 +677,16 @@ cudaError_t tc_project(const float* Xt, const float* Yt, int64_t ld, int64_t nd,
   // digits of both operands, K-major (t contiguous per orbital column), each
   // orbital column at its own exponent
   const int64_t lds = (nd + 63) / 64 * 64;
-  int* escX = esc;
-  int* escY = esc + ns;
-  note_launch(), k_col_exponent<<<ns, 256, 0, st>>>(Xt, ld, nd, escX);
-  note_launch(), k_col_exponent<<<ns, 256, 0, st>>>(Yt, ld, nd, escY);
+  const int nq = (int)((lds + kQ - 1) / kQ);
+  const int NP = (ns + 127) / 128 * 128;
+  int8_t* escX = reinterpret_cast<int8_t*>(esc);
+  int8_t* escY = escX + (size_t)nq * NP;
+  const unsigned eg = (unsigned)(((int64_t)ns * nq * 32 + 255) / 256);
+  note_launch(), k_chunk_exp_cols<<<eg, 256, 0, st>>>(Xt, ld, nd, ns, nq, NP, escX);
+  note_launch(), k_chunk_exp_cols<<<eg, 256, 0, st>>>(Yt, ld, nd, ns, nq, NP, escY);
   dim3 sg((unsigned)std::min<int64_t>((lds + 255) / 256, 64), ns);
-  note_launch(), k_slice_cols<<<sg, 256, 0, st>>>(Xt, ld, nd, ns, escX, SX, lds);
-  note_launch(), k_slice_cols<<<sg, 256, 0, st>>>(Yt, ld, nd, ns, escY, SY, lds);
+  note_launch(), k_slice_cols<<<sg, 256, 0, st>>>(Xt, ld, nd, ns, escX, NP, SX, lds);
+  note_launch(), k_slice_cols<<<sg, 256, 0, st>>>(Yt, ld, nd, ns, escY, NP, SY, lds);
   CUtensorMap mXa, mXb, mYb;
   if (!make_map(&mXa, SX, (uint64_t)lds, (uint64_t)ns, (uint64_t)lds, kBM) ||
       !make_map(&mXb, SX, (uint64_t)lds, (uint64_t)ns, (uint64_t)lds, kBN) ||
@@ -629,7 +697,7 @@ cudaError_t tc_project(const float* Xt, const float* Yt, int64_t ld, int64_t nd,
   a.N = ns;
   a.K = lds;
   int64_t kc = (lds + nsplit - 1) / nsplit;
-  a.kchunk = (kc + kBK - 1) / kBK * kBK;
+  a.kchunk = (kc + kQ - 1) / kQ * kQ;  // splits start on exponent chunks
   a.upper = 1;
   a.tiles_m = (ns + kBM - 1) / kBM;
   a.work = work;
@@ -637,6 +705,8 @@ cudaError_t tc_project(const float* Xt, const float* Yt, int64_t ld, int64_t nd,
   a.escA = escX;
   a.escB0 = escY;
   a.escB1 = escX;
+  a.MP = NP;
+  a.NP = NP;
   a.status = status;
   const int tn = (ns + kBN - 1) / kBN;
   const int nsp = (int)((lds + a.kchunk - 1) / a.kchunk);
@@ -653,15 +723,21 @@ cudaError_t tc_rotate(const float* Xt, int64_t ld, int64_t nd, int ns, const dou
                       cudaStream_t st) {
   // digits of Xt per grid point t (over its ns entries) and of Z per column j
   const int64_t ldk = (ns + 7) / 8 * 8;
-  int* escT = esc;        // nd entries
-  int* escZ = esc + nd;   // ns entries
-  note_launch(), k_row_exponent<<<(unsigned)std::min<int64_t>((nd + 255) / 256, 8192), 256, 0,
-                                  st>>>(Xt, ld, nd, ns, escT);
-  note_launch(), k_z_exponent<<<(ns * 32 + 255) / 256, 256, 0, st>>>(Z, ns, escZ);
+  const int nq = (int)((ldk + kQ - 1) / kQ);
+  const int MP = (int)((nd + 127) / 128 * 128), NP = (ns + 127) / 128 * 128;
+  int* fcol = esc;  // ns entries: column exponents of Xt
+  int8_t* escT = reinterpret_cast<int8_t*>(esc + ((ns + 63) / 64 * 64));
+  int8_t* escZ = escT + (size_t)nq * MP;
+  note_launch(), k_col_exponent<<<ns, 256, 0, st>>>(Xt, ld, nd, fcol);
+  note_launch(), k_chunk_exp_rows<<<dim3((unsigned)std::min<int64_t>((nd + 255) / 256, 4096), nq),
+                                    256, 0, st>>>(Xt, ld, nd, ns, fcol, MP, escT);
+  note_launch(), k_chunk_exp_z<<<(unsigned)(((int64_t)ns * nq * 32 + 255) / 256), 256, 0, st>>>(
+      Z, ns, fcol, nq, NP, escZ);
   dim3 tg((unsigned)((nd + 31) / 32), (unsigned)((ldk + 31) / 32));
-  note_launch(), k_slice_transpose<<<tg, dim3(32, 8), 0, st>>>(Xt, ld, nd, ns, escT, SA, ldk);
+  note_launch(), k_slice_transpose<<<tg, dim3(32, 8), 0, st>>>(Xt, ld, nd, ns, fcol, escT, MP, SA,
+                                                               ldk);
   note_launch(), k_slice_z<<<(unsigned)std::min<int64_t>(((int64_t)ns * ldk + 255) / 256, 4096),
-                             256, 0, st>>>(Z, ns, escZ, SZ, ldk);
+                             256, 0, st>>>(Z, ns, fcol, escZ, NP, SZ, ldk);
   CUtensorMap mA, mZ;
   if (!make_map(&mA, SA, (uint64_t)ldk, (uint64_t)nd, (uint64_t)ldk, kBM) ||
       !make_map(&mZ, SZ, (uint64_t)ldk, (uint64_t)ns, (uint64_t)ldk, kBN))
@@ -670,7 +746,7 @@ cudaError_t tc_rotate(const float* Xt, int64_t ld, int64_t nd, int ns, const dou
   a.M = (int)nd;
   a.N = ns;
   a.K = ldk;
-  a.kchunk = (ldk + kBK - 1) / kBK * kBK;
+  a.kchunk = (ldk + kQ - 1) / kQ * kQ;
   a.upper = 0;
   a.tiles_m = (int)((nd + kBM - 1) / kBM);
   a.out32 = Xout;
@@ -679,6 +755,8 @@ cudaError_t tc_rotate(const float* Xt, int64_t ld, int64_t nd, int ns, const dou
   a.escA = escT;
   a.escB0 = escZ;
   a.escB1 = escZ;
+  a.MP = MP;
+  a.NP = NP;
   a.status = status;
   const int tn = (ns + kBN - 1) / kBN;
   return launch_tc(mA, mZ, mZ, a, dim3(a.tiles_m * tn, 1, 1), st);

@@ -67,6 +67,7 @@ class sparc_timings(ctypes.Structure):
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_hpsi",
            "sparc_spectrum_bounds", "sparc_cheb_filter", "sparc_project", "sparc_subspace_eig",
            "sparc_rotate", "sparc_chefsi_step", "sparc_get_timings", "sparc_project_noalloc",
+           "sparc_occupations", "sparc_density",
            "sparc_batch_create", "sparc_batch_destroy", "sparc_batch_last_error",
            "sparc_batch_chefsi_step", "sparc_batch_get_info"]
 
@@ -102,6 +103,8 @@ def load(build: bool = True):
     L.sparc_chefsi_step.argtypes = [vp, vp, i, i64, i, i, vp, vp, i, vp]
     L.sparc_get_timings.argtypes = [vp, ctypes.POINTER(sparc_timings)]
     L.sparc_project_noalloc.argtypes = [vp, vp, i, i64, i64, vp, vp, vp]
+    L.sparc_occupations.argtypes = [vp, vp, i, d, d, vp, vp, vp]
+    L.sparc_density.argtypes = [vp, vp, i, i64, i, vp, vp, vp]
     L.sparc_batch_create.argtypes = [vp, i, ctypes.POINTER(vp)]
     L.sparc_batch_destroy.argtypes = [vp]
     L.sparc_batch_last_error.argtypes = [vp]
@@ -224,17 +227,36 @@ def sparc_rotate(h, Xt, Xout, Zt, stream=None):
 
 
 def sparc_chefsi_step(h, X, degree, bounds=None, eig=None, stream=None):
-    """One CheFSI step; returns the Ritz values (numpy, host)."""
+    """One CheFSI step; returns the Ritz values (numpy on the host, or the
+    given device tensor `eig`, which then receives them on the device)."""
     px, ns, ld, dt = _block(X)
     eig = np.zeros(ns) if eig is None else eig
+    on_host = isinstance(eig, np.ndarray)
+    eptr = eig.ctypes.data if on_host else eig.data_ptr()
     bptr = None
     if bounds is not None:
         bb = (ctypes.c_double * 3)(*bounds)
         bptr = ctypes.cast(bb, ctypes.c_void_p)
-    _check(h, load().sparc_chefsi_step(h, px, ns, ld, dt, degree, bptr, eig.ctypes.data, 1,
+    _check(h, load().sparc_chefsi_step(h, px, ns, ld, dt, degree, bptr, eptr, int(on_host),
                                        _stream(stream) if not isinstance(X, np.ndarray) else
                                        ctypes.c_void_p(0)))
     return eig
+
+
+def sparc_occupations(h, lam, ne, kT, occ, mu, stream=None):
+    """Fermi-Dirac occupations of device Ritz values `lam` into `occ`; the
+    Fermi level goes to the one-element device tensor `mu`."""
+    _check(h, load().sparc_occupations(h, lam.data_ptr(), lam.numel(), ctypes.c_double(ne),
+                                       ctypes.c_double(kT), occ.data_ptr(), mu.data_ptr(),
+                                       _stream(stream)))
+    return occ, mu
+
+
+def sparc_density(h, X, occ, rho, stream=None):
+    px, ns, ld, dt = _block(X)
+    _check(h, load().sparc_density(h, px, ns, ld, dt, occ.data_ptr(), rho.data_ptr(),
+                                   _stream(stream)))
+    return rho
 
 
 def sparc_get_timings(h):
@@ -302,8 +324,24 @@ class Handle:
         Zt = Z.t().contiguous()  # column-major ns x ns
         return sparc_rotate(self.h, Xt, Xout, Zt, stream)
 
-    def chefsi_step(self, X, degree, bounds=None, stream=None):
-        return sparc_chefsi_step(self.h, X, degree, bounds, None, stream)
+    def chefsi_step(self, X, degree, bounds=None, stream=None, eig=None):
+        return sparc_chefsi_step(self.h, X, degree, bounds, eig, stream)
+
+    def occupations(self, lam, ne, kT=0.01, stream=None):
+        """(occ, mu) as device tensors for device Ritz values `lam`."""
+        import torch
+        if not torch.is_tensor(lam):
+            lam = torch.as_tensor(np.asarray(lam, dtype=np.float64), device="cuda")
+        lam = lam.to(torch.float64).contiguous()
+        occ = torch.empty_like(lam)
+        mu = torch.empty(1, dtype=torch.float64, device=lam.device)
+        return sparc_occupations(self.h, lam, ne, kT, occ, mu, stream)
+
+    def density(self, X, occ, stream=None):
+        """rho (device, Nd doubles) of the block X with occupations `occ`."""
+        import torch
+        rho = torch.empty(self.system.nd, dtype=torch.float64, device=X.device)
+        return sparc_density(self.h, X, occ, rho, stream)
 
     def timings(self):
         return sparc_get_timings(self.h)
