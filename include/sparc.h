@@ -97,7 +97,11 @@ typedef struct {
   int ns_max;    /* largest Ns passed to any call on this handle (>= 1)        */
   int device;    /* CUDA device ordinal                                        */
   int reserved[5]; /* reserved[0] bit 0: use the generic stencil kernel instead
-                      of the TMA plane-ring form (for cross-checking); others 0 */
+                      of the TMA plane-ring form (for cross-checking).
+                      reserved[0] bit 1 (FP64 handles): projection and rotation
+                      on the FP64 SIMT pipe instead of the FP64-accurate
+                      six-digit tensor-core split (about 2^-45 relative to
+                      sum |x_k y_k|).  Other bits and entries 0.            */
 } sparc_options;
 
 /* Stage times (ms) of the last sparc_chefsi_step on the handle (CUDA events)
@@ -264,7 +268,9 @@ int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step);
 
 /*
  * sparc_project_noalloc — the FP64 projection of sparc_project (Hs = Xt^T Yt,
- * Ms = Xt^T Xt) without a handle and without allocating any device memory.
+ * Ms = Xt^T Xt) on the FP64 SIMT pipe (the form FP64 handles use when created
+ * with sparc_options.reserved[0] bit 1), without a handle and without
+ * allocating any device memory.
  * The paper has no counterpart; this entry point exists for callers that may
  * not call cudaMalloc: code whose device memory is owned by another allocator
  * (a framework's caching pool or a pre-partitioned budget) that a raw

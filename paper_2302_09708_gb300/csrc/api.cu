@@ -217,10 +217,10 @@ int do_project(sparc_context* c, const T* Xt, int64_t ldx, const T* Yt, int64_t 
     c->err = "projection operands must share a leading dimension";
     return SPARC_ERR_INVALID_ARG;
   }
-  if (std::is_same<T, float>::value) {
+  if (c->tc_gemm) {
     int nsplit = tc_project_nsplit(ns);
-    CK(c, tc_project((const float*)Xt, (const float*)Yt, ldx, c->nd, ns, Hs, Ms, c->proj_work,
-                     nsplit, c->S1, c->S2, c->esc, c->eig.status + 2, st));
+    CK(c, tc_project(Xt, Yt, ldx, c->nd, ns, Hs, Ms, c->proj_work, nsplit, c->S1, c->S2, c->esc,
+                     c->eig.status + 2, st));
     return SPARC_OK;
   }
   int nsplit = project_nsplit(c->nd, ns);
@@ -231,12 +231,31 @@ int do_project(sparc_context* c, const T* Xt, int64_t ldx, const T* Yt, int64_t 
 template <typename T>
 int do_rotate(sparc_context* c, const T* Xt, int64_t ldt, int ns, const double* Z, T* Xo,
               int64_t ldo, cudaStream_t st) {
-  if (std::is_same<T, float>::value) {
-    CK(c, tc_rotate((const float*)Xt, ldt, c->nd, ns, Z, (float*)Xo, ldo, c->S1, c->SZ, c->esc,
-                    c->eig.status + 2, st));
+  if (c->tc_gemm) {
+    CK(c, tc_rotate(Xt, ldt, c->nd, ns, Z, Xo, ldo, c->S1, c->SZ, c->esc, c->eig.status + 2, st));
     return SPARC_OK;
   }
   CK(c, rotate_simt<T>(Xt, ldt, c->nd, ns, Z, Xo, ldo, st));
+  return SPARC_OK;
+}
+
+// Mixed precision, Rayleigh-Ritz input: Yt = H Xt evaluated in FP64 from the
+// FP32 filtered block, then the projection of (Xt, Yt).  In FP32 the stencil's
+// largest terms (~|w0| 3/h^2 |x|) cancel to ~1/10 of themselves in H x, so the
+// FP32 operator's rounding alone leaves ~1e-6 Ha in the Ritz values; with Yt in
+// FP64 the remaining error is that of the FP32 filtered span (~1e-8 Ha).
+// `mid` (optional) is recorded between the two.
+int mixed_yt_project(sparc_context* c, const float* Xt, int64_t ldt, int ns, cudaEvent_t mid,
+                     cudaStream_t st) {
+  // the FP64 copy of Xt lives in the Yt-digit buffer until those digits are made
+  double* X64 = reinterpret_cast<double*>(c->S2);
+  CK(c, (copy_block<float, double>(Xt, ldt, X64, c->ld, c->nd, ns, st)));
+  int rc = hstep<double>(c, X64, c->ld, c->Y64, c->ld, nullptr, 0, ns, 0.0, 1.0, 0.0, st);
+  if (rc) return rc;
+  if (mid) CK(c, cudaEventRecord(mid, st));
+  const int nsplit = tc_project_nsplit(ns);
+  CK(c, tc_project(Xt, ldt, c->Y64, c->ld, c->nd, ns, c->Hs, c->Ms, c->proj_work, nsplit, c->S1,
+                   c->S2, c->esc, c->eig.status + 2, st));
   return SPARC_OK;
 }
 
@@ -249,11 +268,15 @@ int do_step(sparc_context* c, T* X, int64_t ldx, int ns, int m, double a, double
   int rc = run_filter<T>(c, X, ldx, ns, m, a, b, a0, true, &Xt, &ldt, st);
   if (rc) return rc;
   CK(c, cudaEventRecord(c->ev[2], st));
-  T* Yt = Xt == (T*)c->W1 ? (T*)c->W2 : (T*)c->W1;
-  rc = hstep<T>(c, Xt, ldt, Yt, c->ld, nullptr, 0, ns, 0.0, 1.0, 0.0, st);
-  if (rc) return rc;
-  CK(c, cudaEventRecord(c->ev[3], st));
-  rc = do_project<T>(c, Xt, ldt, Yt, c->ld, ns, c->Hs, c->Ms, st);
+  if (std::is_same<T, float>::value) {
+    rc = mixed_yt_project(c, (const float*)Xt, ldt, ns, c->ev[3], st);
+  } else {
+    T* Yt = Xt == (T*)c->W1 ? (T*)c->W2 : (T*)c->W1;
+    rc = hstep<T>(c, Xt, ldt, Yt, c->ld, nullptr, 0, ns, 0.0, 1.0, 0.0, st);
+    if (rc) return rc;
+    CK(c, cudaEventRecord(c->ev[3], st));
+    rc = do_project<T>(c, Xt, ldt, Yt, c->ld, ns, c->Hs, c->Ms, st);
+  }
   if (rc) return rc;
   CK(c, cudaEventRecord(c->ev[4], st));
   CK(c, gen_eig(c->eig, c->Hs, c->Ms, ns, c->lam, c->Z, st));
@@ -302,7 +325,7 @@ void destroy_ctx(sparc_context* c) {
   for (int i = 0; i < c->nl_nmem; ++i) cudaFree(c->nl_mem[i]);
   cudaFree(c->veff64); cudaFree(c->veff32);
   cudaFree(c->W1); cudaFree(c->W2); cudaFree(c->Wstage); cudaFree(c->D);
-  cudaFree(c->S1); cudaFree(c->S2); cudaFree(c->SZ); cudaFree(c->esc);
+  cudaFree(c->S1); cudaFree(c->S2); cudaFree(c->SZ); cudaFree(c->esc); cudaFree(c->Y64);
   cudaFree(c->Hs); cudaFree(c->Ms); cudaFree(c->Z); cudaFree(c->lam); cudaFree(c->proj_work);
   cudaFree(c->lz);
   eig_free(c->eig);
@@ -450,6 +473,9 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
   }
 
   // --- workspace ----------------------------------------------------------
+  c->ring_enabled = !(opt && (opt->reserved[0] & 1));
+  // mixed handles always take the tensor-core GEMMs; FP64 handles unless bit 1
+  c->tc_gemm = c->precision == SPARC_PREC_MIXED || !(opt && (opt->reserved[0] & 2));
   const size_t es = c->precision == SPARC_PREC_MIXED ? 4 : 8;
   const size_t blk = (size_t)c->ld * c->ns_max * es;
   CK(c, cudaMalloc(&c->W1, blk));
@@ -465,23 +491,23 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
   int64_t pw = 0;
   for (int n = 1; n <= c->ns_max; ++n) {
     pw = std::max<int64_t>(pw, (int64_t)project_nsplit(nd, n) * 2 * n * n);
-    if (c->precision == SPARC_PREC_MIXED)
-      pw = std::max<int64_t>(pw, (int64_t)tc_project_nsplit(n) * 2 * n * n);
+    if (c->tc_gemm) pw = std::max<int64_t>(pw, (int64_t)tc_project_nsplit(n) * 2 * n * n);
   }
-  if (c->precision == SPARC_PREC_MIXED) {
-    const size_t se = tc_slice_elems(c->ld, nd, c->ns_max);
+  if (c->tc_gemm) {
+    const bool f64 = c->precision != SPARC_PREC_MIXED;
+    const size_t se = tc_slice_elems(c->ld, nd, c->ns_max, f64);
     CK(c, cudaMalloc(&c->S1, se * sizeof(__nv_bfloat16)));
     CK(c, cudaMalloc(&c->S2, se * sizeof(__nv_bfloat16)));
     const size_t zk = (size_t)(c->ns_max + 7) / 8 * 8;
-    CK(c, cudaMalloc(&c->SZ, 4 * zk * c->ns_max * sizeof(__nv_bfloat16)));
+    CK(c, cudaMalloc(&c->SZ, (size_t)tc_digits(f64) * zk * c->ns_max * sizeof(__nv_bfloat16)));
     CK(c, cudaMalloc(&c->esc, tc_esc_bytes(c->ld, nd, c->ns_max)));
+    if (!f64) CK(c, cudaMalloc(&c->Y64, (size_t)c->ld * c->ns_max * sizeof(double)));
   }
   c->proj_work_elems = pw;
   CK(c, cudaMalloc(&c->proj_work, pw * 8));
   CK(c, cudaMalloc(&c->lz, ((size_t)3 * nd + 1024 + 384 + std::max(kp, 1)) * 8));
   CK(c, eig_alloc(c->eig, c->ns_max));
   CK(c, cudaMemset(c->eig.status, 0, 16 * sizeof(int)));
-  c->ring_enabled = !(opt && (opt->reserved[0] & 1));
   for (auto& e : c->ev) CK(c, cudaEventCreate(&e));
   return SPARC_OK;
 }
@@ -876,7 +902,10 @@ int batch_step_impl(sparc_batch_context* b, void* const* X, const int* ns, const
     }
     const long long l0 = launch_count();
     CK(b, cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k <= mmax; ++k) {
+    // mixed precision evaluates Yt per member in FP64 (mixed_yt_project), so
+    // the batched launches stop after the last filter degree
+    const int kend = std::is_same<T, float>::value ? mmax - 1 : mmax;
+    for (int k = 0; k <= kend; ++k) {
       const uint8_t* rows = static_cast<const uint8_t*>(b->d_items) + (size_t)k * n * isz;
       cudaError_t e = batch_degree<T>(b->d_sys, rows, n, b->cta_total, b->nl_total, b->cs);
       if (e != cudaSuccess) {
@@ -892,7 +921,10 @@ int batch_step_impl(sparc_batch_context* b, void* const* X, const int* ns, const
     for (int i = 0; i < n && !rc; ++i) {
       sparc_context* c = b->hs[i];
       cudaStream_t w = b->workers[i % b->workers.size()];
-      rc = do_project<T>(c, xt[i], ldt[i], yt[i], c->ld, ns[i], c->Hs, c->Ms, w);
+      if (std::is_same<T, float>::value)
+        rc = mixed_yt_project(c, (const float*)xt[i], ldt[i], ns[i], nullptr, w);
+      else
+        rc = do_project<T>(c, xt[i], ldt[i], yt[i], c->ld, ns[i], c->Hs, c->Ms, w);
       if (!rc && gen_eig(c->eig, c->Hs, c->Ms, ns[i], c->lam, c->Z, w) != cudaSuccess) rc = SPARC_ERR_CUDA;
       if (!rc) rc = do_rotate<T>(c, xt[i], ldt[i], ns[i], c->Z, (T*)X[i], ld[i], w);
       if (rc) b->err = c->err;

@@ -82,9 +82,10 @@ __global__ void __launch_bounds__(kFermiThreads) k_fermi(const double* __restric
 }
 
 // rho over a range of points: V consecutive points per thread (one vector
-// load per orbital), orbitals [n0, n1) of this split.  FP32 blocks sum
-// f_n x^2 in FP32 over groups of 16 orbitals and add each group in FP64;
-// FP64 blocks accumulate in FP64 throughout.
+// load per orbital), orbitals [n0, n1) of this split, taken G at a time with
+// all G loads issued before the arithmetic (the loads, not the FMAs, set the
+// pace).  FP32 blocks sum f_n x^2 in FP32 within a group of G = 16 orbitals
+// and add each group in FP64; FP64 blocks accumulate in FP64 throughout.
 template <typename T, int V>
 __global__ void __launch_bounds__(256) k_density(const T* __restrict__ X, int64_t ld, int64_t nd,
                                                  int ns, int nsplit,
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(256) k_density(const T* __restrict__ X, int64_
       std::is_same<T, float>::value,
       typename std::conditional<V == 4, float4, float2>::type,
       typename std::conditional<V == 2, double2, double>::type>::type;
+  constexpr int G = std::is_same<T, float>::value ? 16 : 8;
   const int split = blockIdx.y;
   const int per = (ns + nsplit - 1) / nsplit;
   const int n0 = split * per, n1 = min(ns, n0 + per);
@@ -103,28 +105,30 @@ __global__ void __launch_bounds__(256) k_density(const T* __restrict__ X, int64_
   const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * V;
   if (i0 >= nd) return;
   const bool full = i0 + V <= nd;
-  constexpr int G = std::is_same<T, float>::value ? 16 : 1;
   for (int g0 = n0; g0 < n1; g0 += G) {
-    const int g1 = min(n1, g0 + G);
+    const int cnt = min(G, n1 - g0);
+    T x[G][V];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const T* col = X + i0 + (int64_t)(g0 + u) * ld;
+      if (u < cnt && full) {
+        const Vec w = __ldg(reinterpret_cast<const Vec*>(col));
+        const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[u][v] = wp[v];
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[u][v] = (u < cnt && i0 + v < nd) ? col[v] : T(0);
+      }
+    }
     T part[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) part[v] = T(0);
-#pragma unroll 4
-    for (int n = g0; n < g1; ++n) {
-      const T f = (T)__ldg(occ + n);
-      const T* col = X + i0 + (int64_t)n * ld;
-      T x[V];
-      if (full) {
-        const Vec w = *reinterpret_cast<const Vec*>(col);
-        const T* wp = reinterpret_cast<const T*>(&w);
 #pragma unroll
-        for (int v = 0; v < V; ++v) x[v] = wp[v];
-      } else {
+    for (int u = 0; u < G; ++u) {
+      const T f = u < cnt ? (T)__ldg(occ + g0 + u) : T(0);
 #pragma unroll
-        for (int v = 0; v < V; ++v) x[v] = i0 + v < nd ? col[v] : T(0);
-      }
-#pragma unroll
-      for (int v = 0; v < V; ++v) part[v] = fma(f * x[v], x[v], part[v]);
+      for (int v = 0; v < V; ++v) part[v] = fma(f * x[u][v], x[u][v], part[v]);
     }
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] += (double)part[v];

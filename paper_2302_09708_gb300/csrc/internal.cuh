@@ -94,8 +94,9 @@ cudaError_t lanczos_update(double* w, const double* v, double* vp, const double*
 cudaError_t lanczos_normalize(double* v, double* w, double* vp, double* alpha_beta, int j,
                               int64_t n, double* partial, cudaStream_t st);
 cudaError_t lanczos_bounds(const double* alpha_beta, int k, double* out2, cudaStream_t st);
-template <typename T>
-cudaError_t copy_block(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t nd, int ns,
+// dst = src column by column (the element type may widen, e.g. FP32 -> FP64)
+template <typename T, typename U = T>
+cudaError_t copy_block(const T* src, int64_t lds, U* dst, int64_t ldd, int64_t nd, int ns,
                        cudaStream_t st);
 
 // Dense FP64 kernels (dense.cu) -------------------------------------------
@@ -109,23 +110,36 @@ int project_nsplit(int64_t nd, int ns);
 cudaError_t project_reduce(const double* work, int nsplit, int ns, double* Hs, double* Ms,
                            cudaStream_t st);
 
-// Split-precision tensor-core GEMMs (tc_gemm.cu), FP32 operands.
-size_t tc_slice_elems(int64_t ld, int64_t nd, int ns_max);
+// Split-precision tensor-core GEMMs (tc_gemm.cu): FP32 operands take 4 BF16
+// digits (mixed precision), FP64 operands 6 digits (FP64-accurate).
+int tc_digits(bool fp64);
+size_t tc_slice_elems(int64_t ld, int64_t nd, int ns_max, bool fp64);
 size_t tc_esc_bytes(int64_t ld, int64_t nd, int ns_max);
+int tc_project_nsplit(int ns);
+// `esc`: workspace of tc_esc_bytes() bytes (block exponents).
+cudaError_t tc_project(const float* Xt, const float* Yt, int64_t ld, int64_t nd, int ns,
+                       double* Hs, double* Ms, double* work, int nsplit, __nv_bfloat16* SX,
+                       __nv_bfloat16* SY, int* esc, int* status, cudaStream_t st);
+// mixed precision with an FP64 Yt (4 digits of each operand)
+cudaError_t tc_project(const float* Xt, int64_t ldx, const double* Yt, int64_t ldy, int64_t nd,
+                       int ns, double* Hs, double* Ms, double* work, int nsplit,
+                       __nv_bfloat16* SX, __nv_bfloat16* SY, int* esc, int* status,
+                       cudaStream_t st);
+cudaError_t tc_project(const double* Xt, const double* Yt, int64_t ld, int64_t nd, int ns,
+                       double* Hs, double* Ms, double* work, int nsplit, __nv_bfloat16* SX,
+                       __nv_bfloat16* SY, int* esc, int* status, cudaStream_t st);
+cudaError_t tc_rotate(const float* Xt, int64_t ld, int64_t nd, int ns, const double* Z,
+                      float* Xout, int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc,
+                      int* status, cudaStream_t st);
+cudaError_t tc_rotate(const double* Xt, int64_t ld, int64_t nd, int ns, const double* Z,
+                      double* Xout, int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc,
+                      int* status, cudaStream_t st);
 
 // density.cu: Fermi occupations (one block) and rho = (2/h^3) sum f_n x_n^2.
 cudaError_t fermi_occupations(const double* lam, int ns, double ne, double kT, double* occ,
                               double* mu, cudaStream_t st);
 cudaError_t density(const void* X, int64_t ld, int64_t nd, int ns, bool fp32, const double* occ,
                     double h, double* rho, double* work, int64_t work_elems, cudaStream_t st);
-int tc_project_nsplit(int ns);
-// `esc`: workspace of tc_esc_bytes() bytes (block exponents).
-cudaError_t tc_project(const float* Xt, const float* Yt, int64_t ld, int64_t nd, int ns,
-                       double* Hs, double* Ms, double* work, int nsplit, __nv_bfloat16* SX,
-                       __nv_bfloat16* SY, int* esc, int* status, cudaStream_t st);
-cudaError_t tc_rotate(const float* Xt, int64_t ld, int64_t nd, int ns, const double* Z,
-                      float* Xout, int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc,
-                      int* status, cudaStream_t st);
 // Xout = Xt Z (Z column-major ns x ns)
 template <typename T>
 cudaError_t rotate_simt(const T* Xt, int64_t ld, int64_t nd, int ns, const double* Z, T* Xout,
@@ -237,5 +251,7 @@ struct sparc_context {
   bool timed = false;
   long long step_launches = 0;
   bool ring_enabled = true;  // TMA-ring stencil (options.reserved[0] bit 0 turns it off)
+  bool tc_gemm = true;       // tensor-core projection/rotation (FP64: reserved[0] bit 1 off)
+  double* Y64 = nullptr;     // mixed handles: FP64 Yt = H Xt of a step (ld x ns_max)
   std::string err;
 };

@@ -389,27 +389,29 @@ template cudaError_t nl_coefficients<float>(const Nonlocal<float>&, double, cons
 // Block copy between leading dimensions.
 // ---------------------------------------------------------------------------
 namespace {
-template <typename T>
-__global__ void k_copy_block(const T* __restrict__ src, int64_t lds, T* __restrict__ dst,
+template <typename T, typename U>
+__global__ void k_copy_block(const T* __restrict__ src, int64_t lds, U* __restrict__ dst,
                              int64_t ldd, int64_t nd) {
   const int n = blockIdx.y;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
        i += (int64_t)gridDim.x * blockDim.x)
-    dst[n * ldd + i] = src[n * lds + i];
+    dst[n * ldd + i] = (U)src[n * lds + i];
 }
 }  // namespace
 
-template <typename T>
-cudaError_t copy_block(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t nd, int ns,
+template <typename T, typename U>
+cudaError_t copy_block(const T* src, int64_t lds, U* dst, int64_t ldd, int64_t nd, int ns,
                        cudaStream_t st) {
   int bx = (int)std::min<int64_t>((nd + 255) / 256, 1024);
-  note_launch(), k_copy_block<T><<<dim3(bx, ns), 256, 0, st>>>(src, lds, dst, ldd, nd);
+  note_launch(), k_copy_block<T, U><<<dim3(bx, ns), 256, 0, st>>>(src, lds, dst, ldd, nd);
   return cudaGetLastError();
 }
-template cudaError_t copy_block<double>(const double*, int64_t, double*, int64_t, int64_t, int,
-                                        cudaStream_t);
-template cudaError_t copy_block<float>(const float*, int64_t, float*, int64_t, int64_t, int,
-                                       cudaStream_t);
+template cudaError_t copy_block<double, double>(const double*, int64_t, double*, int64_t, int64_t,
+                                                int, cudaStream_t);
+template cudaError_t copy_block<float, float>(const float*, int64_t, float*, int64_t, int64_t,
+                                              int, cudaStream_t);
+template cudaError_t copy_block<float, double>(const float*, int64_t, double*, int64_t, int64_t,
+                                               int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // FP64 vector kernels for Lanczos.  Reductions: kRedBlocks fixed partial sums

@@ -1,34 +1,39 @@
-// Split-precision tensor-core GEMMs (tcgen05 + TMA + TMEM) for the mixed
-// precision projection and rotation of Algorithm 1 (paper Sec. II B, II D).
+// Split-precision tensor-core GEMMs (tcgen05 + TMA + TMEM) for the projection
+// and rotation of Algorithm 1 (paper Sec. II B, II D), in two accuracies:
+//   FP32 operands (mixed precision): 4 digits, levels 0..3 (10 products);
+//   FP64 operands (plain form):      6 digits, levels 0..5 (21 products).
 //
 // Block fixed-point split (Ozaki-style): for every operand row r (a row of the
 // GEMM's M or N dimension) and every chunk q of 256 K values, the entries are
 // scaled by 2^-e_rq, e_rq the binary exponent of the chunk's largest entry, and
-// every entry u = x 2^-e_rq in (-1, 1) is written as four signed
-// 8-bit integer digits, u = 2^-7 (d1 + 2^-8 d2 + 2^-16 d3 + 2^-24 d4) + O(2^-32),
-// each exactly representable in BF16.  A product is formed from the ten digit
-// products of weight >= 2^-24 relative to the leading one, in four levels
-//   L0 = a1 b1,  L1 = a1 b2 + a2 b1,  L2 = a1 b3 + a2 b2 + a3 b1,
-//   L3 = a1 b4 + a2 b3 + a3 b2 + a4 b1,
-//   a b ~ 2^(e_a + e_b - 14) (L0 + 2^-8 L1 + 2^-16 L2 + 2^-24 L3),
+// every entry u = x 2^-e_rq in (-1, 1) is written as D signed 8-bit integer
+// digits, u = 2^-7 (d0 + 2^-8 d1 + 2^-16 d2 + ...) + O(2^-(8D-1)), each exactly
+// representable in BF16.  A product is formed from the digit products of
+// level l = i + j < NL,
+//   L_l = sum_{i+j=l} a_i b_j,   a b ~ 2^(e_a + e_b - 14) sum_l 2^-8l L_l,
 // each level accumulating in its own tensor-memory accumulator.  Digit products
-// are integers of magnitude <= 2^14, so over a chunk of 256 K values every level
-// sum stays an integer of magnitude <= 2^24 and the tensor core adds it exactly
-// (its alignment/truncation of products never drops a bit).  Every
-// kChunkSteps K-steps (one exponent chunk) the exact level sums are scaled by
-// 2^(e_a + e_b - 14) of that chunk and folded into a double-FP32 (hi, lo)
-// running sum held in registers.  Per-chunk exponents keep the digits relative
-// to local magnitudes, so the first dropped level (whose diagonal terms never
-// cancel) stays ~2^-32 of the local values instead of biasing long sums.
+// are integers of magnitude <= 2^14, so over a chunk of 256 K values the sums of
+// levels 0..3 stay integers of magnitude <= 2^24 and the tensor core adds them
+// exactly; levels >= 4 (FP64 form only) may round, at 2^-56 of the leading level.
+// At the end of every chunk the level sums are scaled by 2^(e_a + e_b - 14) of
+// that chunk and folded into a double-FP32 (hi, lo) running sum held in
+// registers: the leading levels by error-free TwoSum, the remaining ones first
+// combined in FP32 (Horner in 2^-8).  Per-chunk exponents keep the digits
+// relative to local magnitudes, so the first dropped level (whose diagonal terms
+// never cancel) stays ~2^-8NL of the local values instead of biasing long sums.
+// Relative to sum_k |a_k b_k| the result is accurate to ~2^-32 (FP32 form) and
+// ~2^-45 (FP64 form).  The running sums are FP32 pairs, so results below about
+// 1e-30 in magnitude lose relative accuracy (FP64 orbital entries that small
+// carry no weight in a normalised block).
 //
-// Kernel structure (one CTA per 128 x 64 output tile, 192 threads):
+// Kernel structure (one CTA per 128 x 64 output tile, 320 threads):
 //   warp 0     TMA producer: one 3-D TMA load per operand per K-step brings the
-//              four BF16 digit tiles (128-byte swizzle) into a 2-stage
-//              shared-memory ring (full/empty mbarriers);
+//              D BF16 digit tiles (swizzled) into a shared-memory ring
+//              (full/empty mbarriers);
 //   warp 1     allocates 512 TMEM columns and issues tcgen05.mma (one thread):
-//              2 buffers x 4 level accumulators (64 columns each);
-//   warps 2-5  epilogue: fold a finished accumulator buffer into (hi, lo), and
-//              finally write hi + lo.
+//              NL level accumulators of 64 columns, double-buffered when they fit;
+//   warps 2-9  epilogue: two warps per TMEM lane quarter, 32 columns each; fold
+//              a finished accumulator set into (hi, lo), finally write hi + lo.
 // Every mbarrier wait is bounded; on expiry the CTA records SPARC_ERR_TIMEOUT
 // in the status word, stops issuing work, drains what it issued (bounded) and
 // frees its tensor memory.
@@ -39,6 +44,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -46,20 +52,49 @@ namespace sparc {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 64, kBK = 64;
-constexpr int kSlices = 4;
-constexpr int kLevels = 4;
-constexpr int kStages = 2;
-constexpr int kChunkSteps = 4;
-constexpr int kProducts = 10;
-constexpr uint32_t kTileBytes = kBM * kBK * 2;                 // one A slice tile (16 KB)
-constexpr uint32_t kTileBytesB = kBN * kBK * 2;                // one B slice tile (8 KB)
-constexpr uint32_t kOpBytes = kSlices * kTileBytes;            // A operand, 3 slices
-constexpr uint32_t kStageBytes = kOpBytes + kSlices * kTileBytesB;
-constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr int kBM = 128, kBN = 64;
+constexpr int kQ = 256;  // K values per exponent chunk
 constexpr uint32_t kTmemCols = 512;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// Compile-time plan of one accuracy form: D digits, levels 0..NL-1.
+template <int D, int NL>
+struct Plan {
+  static_assert(NL <= D, "levels beyond the digits");
+  static constexpr int kD = D, kNL = NL;
+  static constexpr int kBK = D <= 4 ? 64 : 32;           // K per stage (one swizzle row)
+  static constexpr int kSwizzle = kBK * 2;                // bytes: 128 or 64
+  static constexpr int kSteps = kQ / kBK;                 // stages per exponent chunk
+  static constexpr int kProducts = NL * (NL + 1) / 2;     // digit pairs with i + j < NL
+  static constexpr int kBufs = (int)kTmemCols / (NL * kBN);  // accumulator sets in TMEM
+  static constexpr int kExact = D <= 4 ? 1 : 3;           // levels folded by TwoSum
+  static constexpr uint32_t kTileA = kBM * kBK * 2;       // one A digit tile
+  static constexpr uint32_t kTileB = kBN * kBK * 2;       // one B digit tile
+  static constexpr uint32_t kOpA = D * kTileA;
+  static constexpr uint32_t kStageBytes = D * (kTileA + kTileB);
+  static constexpr int kStages = (int)((220u * 1024u) / kStageBytes) > 4
+                                     ? 4
+                                     : (int)((220u * 1024u) / kStageBytes);
+  // 1 KB for the alignment of the ring, and a margin behind it
+  static constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 + 4096;
+  static_assert(kBufs >= 1 && kStages >= 2, "plan does not fit");
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+};
+using PlanF32 = Plan<4, 4>;
+using PlanF64 = Plan<6, 6>;
+
+// Digit pair of product p, ordered by level l = i + j, then by i.
+__host__ __device__ constexpr int prod_level(int p) {
+  int l = 0;
+  while ((l + 1) * (l + 2) / 2 <= p) ++l;
+  return l;
+}
+__host__ __device__ constexpr int prod_a(int p) {
+  return p - prod_level(p) * (prod_level(p) + 1) / 2;
+}
+__host__ __device__ constexpr int prod_b(int p) { return prod_level(p) - prod_a(p); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -118,19 +153,22 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (tcgen05 descriptor version 1).
+// Shared-memory matrix descriptor (tcgen05 version 1) of a K-major operand whose
+// rows are one swizzle span long (SW = 128 or 64 bytes): 8-row groups are
+// 8 * SW bytes apart; layout code 2 = 128-byte swizzle, 4 = 64-byte swizzle.
+template <int SW>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  static_assert(SW == 128 || SW == 64, "swizzle");
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((8 * SW) >> 4) << 32;   // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)(SW == 128 ? 2 : 4) << 61;
   return d;
 }
 
-// Instruction descriptor: BF16 x BF16 -> FP32, A and B K-major, M = 128, N = 128.
+// Instruction descriptor: BF16 x BF16 -> FP32, A and B K-major, M = 128, N = 64.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
                             ((uint32_t)(kBM >> 4) << 24);
 
@@ -147,59 +185,44 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
       : "memory");
 }
 
-#define TMEM_REGS32(r)                                                                           \
-  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),           \
-      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),    \
-      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), \
-      "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), \
-      "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-#define TMEM_IN32(r)                                                                          \
-  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),     \
-      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),       \
-      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),     \
-      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),     \
-      "r"(r[29]), "r"(r[30]), "r"(r[31])
-#define REGLIST32                                                                             \
-  "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19," \
-  " %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}"
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 " REGLIST32 ", [%32];"
-               : TMEM_REGS32(r)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%32], " REGLIST32 ";" ::TMEM_IN32(r),
-               "r"(taddr)
-               : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
-// slice pairs (a-slice, b-slice) of the six products, their magnitude level
-// and whether the product is the first of its level (starts the accumulator)
-__constant__ int c_sa[kProducts] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-__constant__ int c_sb[kProducts] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
-__constant__ int c_lv[kProducts] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
-__constant__ int c_first[kProducts] = {1, 1, 0, 1, 0, 0, 1, 0, 0, 0};
 
 // 2^n as a float, built from the IEEE-754 exponent field for normal results.
 __device__ __forceinline__ float pow2i(int n) {
   return n >= -126 ? __int_as_float((min(n, 127) + 127) << 23) : ldexpf(1.0f, n);
 }
 
+// Exact float -> double by moving the IEEE-754 fields with integer operations
+// (GB300's FP64 pipe, which would otherwise do the conversion, is 1/64 of FP32).
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)f;  // zero, subnormal, inf, nan
+  const uint64_t d = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                     ((uint64_t)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+// 2^-8l (0 <= l <= 15), from the IEEE-754 exponent field
+__device__ __forceinline__ float exp2_neg8(int l) { return __int_as_float((127 - 8 * l) << 23); }
+
 struct TcArgs {
   int M, N;
   int64_t K;
-  int64_t kchunk;   // K per split (multiple of kBK)
+  int64_t kchunk;   // K per split (multiple of kQ)
   int upper;        // 1: enumerate only tiles with bi <= bj (symmetric outputs)
-  int tiles_m;
+  int tiles_m, tiles_n;
   double* work;     // mode 0: work[(split * 2 + out) * M * N + m + n * M]
   float* out32;     // mode 1: out32[m + n * ldo]
+  double* out64;    // mode 2: out64[m + n * ldo]
   int64_t ldo;
   int mode;
   const int8_t* escA;   // exponent of A row r in chunk q at [q * MP + r]
@@ -209,11 +232,15 @@ struct TcArgs {
   int* status;
 };
 
+template <int D, int NL>
+// 10 warps are allotted registers as 12 (whole warp quads): at most 168 each
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB0,
               const __grid_constant__ CUtensorMap tB1, const TcArgs a) {
+  using P = Plan<D, NL>;
+  constexpr int kStages = P::kStages, kBufs = P::kBufs, kBK = P::kBK;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bars[2 * kStages + 5];
+  __shared__ uint64_t bars[2 * kStages + 2 * kBufs + 1];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
 
@@ -221,29 +248,36 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t full0 = smem_u32(&bars[0]);
   const uint32_t empty0 = smem_u32(&bars[kStages]);
-  const uint32_t accf0 = smem_u32(&bars[2 * kStages]);      // 2 barriers
-  const uint32_t acce0 = smem_u32(&bars[2 * kStages + 2]);  // 2 barriers
-  const uint32_t drain = smem_u32(&bars[2 * kStages + 4]);
+  const uint32_t accf0 = smem_u32(&bars[2 * kStages]);          // kBufs barriers
+  const uint32_t acce0 = smem_u32(&bars[2 * kStages + kBufs]);  // kBufs barriers
+  const uint32_t drain = smem_u32(&bars[2 * kStages + 2 * kBufs]);
 
-  const int bi = blockIdx.x % a.tiles_m;
-  const int bj = blockIdx.x / a.tiles_m;
-  // symmetric outputs: only tiles that reach the upper triangle (i <= j)
-  if (a.upper && bi * kBM > bj * kBN + kBN - 1) return;
+  int bi, bj;
+  if (a.upper) {
+    bi = blockIdx.x % a.tiles_m;
+    bj = blockIdx.x / a.tiles_m;
+    // symmetric outputs: only tiles that reach the upper triangle (i <= j)
+    if (bi * kBM > bj * kBN + kBN - 1) return;
+  } else {
+    // the column tiles of one row block run together and share its A digits in L2
+    bj = blockIdx.x % a.tiles_n;
+    bi = blockIdx.x / a.tiles_n;
+  }
   const int out = blockIdx.z;
   const CUtensorMap* tB = out == 0 ? &tB0 : &tB1;
   const int64_t k0 = (int64_t)blockIdx.y * a.kchunk;
   const int64_t k1 = min(a.K, k0 + a.kchunk);
   const int nk = k1 > k0 ? (int)((k1 - k0 + kBK - 1) / kBK) : 0;
-  const int nchunks = (nk + kChunkSteps - 1) / kChunkSteps;
+  const int nchunks = (nk + P::kSteps - 1) / P::kSteps;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kBufs; ++b) {
       mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 4);
+      mbar_init(acce0 + 8 * b, kEpiWarps);
     }
     mbar_init(drain, 1);
     abort_sh = 0;
@@ -270,11 +304,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = it % kStages;
         const uint32_t round = (uint32_t)(it / kStages);
         if (!mbar_wait(empty0 + 8 * s, (round & 1) ^ 1, abort, a.status)) break;
-        const uint32_t sa = base + s * kStageBytes;
-        mbar_expect_tx(full0 + 8 * s, kStageBytes);
+        const uint32_t sa = base + s * P::kStageBytes;
+        mbar_expect_tx(full0 + 8 * s, P::kStageBytes);
         const int kx = (int)(k0 + (int64_t)it * kBK);
         tma_load_3d(sa, &tA, kx, bi * kBM, 0, full0 + 8 * s);
-        tma_load_3d(sa + kOpBytes, tB, kx, bj * kBN, 0, full0 + 8 * s);
+        tma_load_3d(sa + P::kOpA, tB, kx, bj * kBN, 0, full0 + 8 * s);
         issued = it + 1;
       }
       if (*abort) {
@@ -293,28 +327,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int it = 0; it < nk; ++it) {
         const int s = it % kStages;
         const uint32_t round = (uint32_t)(it / kStages);
-        const int chunk = it / kChunkSteps, in_chunk = it % kChunkSteps;
-        const int buf = chunk & 1;
-        const uint32_t use = (uint32_t)(chunk >> 1);
+        const int chunk = it / P::kSteps, in_chunk = it % P::kSteps;
+        const int buf = chunk % kBufs;
+        const uint32_t use = (uint32_t)(chunk / kBufs);
         if (in_chunk == 0) {
           if (!mbar_wait(acce0 + 8 * buf, (use & 1) ^ 1, abort, a.status)) break;
           tc_fence_after();
         }
         if (!mbar_wait(full0 + 8 * s, round & 1, abort, a.status)) break;
         tc_fence_after();
-        const uint32_t sa = base + s * kStageBytes, sb = sa + kOpBytes;
+        const uint32_t sa = base + s * P::kStageBytes, sb = sa + P::kOpA;
+        // descriptors of this stage's first A and B tiles; every other operand
+        // is a compile-time offset (the address field holds addr >> 4 and the
+        // ring ends below 256 KB, so the additions never carry out of it)
+        const uint64_t da0 = smem_desc<P::kSwizzle>(sa), db0 = smem_desc<P::kSwizzle>(sb);
+        const uint32_t d0 = tmem + (uint32_t)(buf * NL * kBN);
 #pragma unroll
-        for (int p = 0; p < kProducts; ++p) {
-          const uint32_t d = tmem + (uint32_t)((buf * kLevels + c_lv[p]) * kBN);
+        for (int p = 0; p < P::kProducts; ++p) {
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk) {
-            const uint64_t da = smem_desc(sa + c_sa[p] * kTileBytes + kk * 32);
-            const uint64_t db = smem_desc(sb + c_sb[p] * kTileBytesB + kk * 32);
-            tc_mma(d, da, db, !(in_chunk == 0 && kk == 0 && c_first[p]));
+            const uint64_t da = da0 + (uint64_t)((prod_a(p) * P::kTileA + kk * 32) >> 4);
+            const uint64_t db = db0 + (uint64_t)((prod_b(p) * P::kTileB + kk * 32) >> 4);
+            tc_mma(d0 + (uint32_t)(prod_level(p) * kBN), da, db,
+                   !(in_chunk == 0 && kk == 0 && prod_a(p) == 0));
           }
         }
         tc_commit(empty0 + 8 * s);
-        if (in_chunk == kChunkSteps - 1 || it == nk - 1) tc_commit(accf0 + 8 * buf);
+        if (in_chunk == P::kSteps - 1 || it == nk - 1) tc_commit(accf0 + 8 * buf);
       }
       // all issued MMAs complete before tensor memory is released
       tc_commit(drain);
@@ -323,92 +362,101 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const int q = warp & 3;  // TMEM lane quarter of this warp
+    // ---------------- epilogue (warps 2..9) ----------------
+    const int q = warp & 3;             // TMEM lane quarter of this warp
+    const int half = (warp - 2) >> 2;   // which 32 of the tile's 64 columns
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    float hi[kBN], lo[kBN];
+    float hi[32], lo[32];
 #pragma unroll
-    for (int i = 0; i < kBN; ++i) {
+    for (int i = 0; i < 32; ++i) {
       hi[i] = 0.f;
       lo[i] = 0.f;
     }
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
-      const int buf = c & 1;
-      const uint32_t use = (uint32_t)(c >> 1);
+      const int buf = c % kBufs;
+      const uint32_t use = (uint32_t)(c / kBufs);
       if (!mbar_wait(accf0 + 8 * buf, use & 1, abort, a.status)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint32_t t_acc = tmem + lane_off + (uint32_t)(buf * kLevels * kBN);
-      // exponents of this chunk: the thread's A row and the tile's 64 B rows
-      const int qg = (int)(k0 / (kBK * kChunkSteps)) + c;
+      const uint32_t t_acc =
+          tmem + lane_off + (uint32_t)(buf * NL * kBN) + (uint32_t)(half * 32);
+      // exponents of this chunk: the thread's A row and the warp's 32 B rows
+      const int qg = (int)(k0 / kQ) + c;
       const int rowc = min(bi * kBM + q * 32 + lane, a.MP - 1);
       const int ea = (int)a.escA[(int64_t)qg * a.MP + rowc] - 14;
       const uint4* eb_src = reinterpret_cast<const uint4*>(
-          (out == 0 ? a.escB0 : a.escB1) + (int64_t)qg * a.NP + bj * kBN);
+          (out == 0 ? a.escB0 : a.escB1) + (int64_t)qg * a.NP + bj * kBN + half * 32);
+      // columns in slices of 8: all NL level loads of a slice are issued
+      // before one wait (TMEM load latency is paid once per slice)
+      constexpr int W = 8;
 #pragma unroll
-      for (int cb = 0; cb < kBN / 32; ++cb) {
-        // t = L1 + 2^-8 L2 + 2^-16 L3 (exact integers; FP32 keeps 24 bits of it)
-        uint32_t v0[32], t[32];
-        const uint4 eb0 = __ldg(eb_src + 2 * cb), eb1 = __ldg(eb_src + 2 * cb + 1);
-        tmem_ld32(t_acc + cb * 32, v0);
-        tmem_ld32(t_acc + 3 * kBN + cb * 32, t);
+      for (int cq = 0; cq < 32 / W; ++cq) {
+        const uint32_t tq = t_acc + cq * W;
+        const uint2 ew = __ldg(reinterpret_cast<const uint2*>(eb_src) + cq);
+        uint32_t L[NL][W];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) tmem_ld8(tq + l * kBN, L[l]);
         tmem_wait_ld();
-        {
-          uint32_t v[32];
-          tmem_ld32(t_acc + 2 * kBN + cb * 32, v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            t[i] = __float_as_uint(
-                __fmaf_rn(__uint_as_float(t[i]), 0.00390625f, __uint_as_float(v[i])));
-          tmem_ld32(t_acc + kBN + cb * 32, v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            t[i] = __float_as_uint(
-                __fmaf_rn(__uint_as_float(t[i]), 0.00390625f, __uint_as_float(v[i])) *
-                0.00390625f);
+        if (cq == 32 / W - 1) {
+          // every level of this buffer is in registers: hand it back to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce0 + 8 * buf);
         }
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          float hh = hi[cb * 32 + i], ll = lo[cb * 32 + i];
-          const uint4& ew = i < 16 ? eb0 : eb1;
-          const uint32_t word = (i & 15) < 4 ? ew.x : (i & 15) < 8 ? ew.y : (i & 15) < 12 ? ew.z : ew.w;
-          const int eb = (int)(int8_t)(word >> (8 * (i & 3)));
-          const float sc = pow2i(ea + eb);
+        for (int i = 0; i < W; ++i) {
+          // tail t = L_kExact + 2^-8 L_(kExact+1) + ... (Horner from the last level)
+          float t = __uint_as_float(L[NL - 1][i]);
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const float x = __uint_as_float(u == 0 ? v0[i] : t[i]) * sc;
-            const float sm = __fadd_rn(hh, x);
-            const float bp = __fsub_rn(sm, hh);
-            const float ap = __fsub_rn(sm, bp);
-            const float err = __fadd_rn(__fsub_rn(hh, ap), __fsub_rn(x, bp));
-            hh = sm;
-            ll = __fadd_rn(ll, err);
+          for (int l = NL - 2; l >= P::kExact; --l)
+            t = __fmaf_rn(t, 0.00390625f, __uint_as_float(L[l][i]));
+          // chunk value (ch, cl) = L0 + 2^-8 L1 + ... + 2^-8kExact t, the exact
+          // integer levels added error-free
+          float ch = __uint_as_float(L[0][i]), cl = 0.f;
+#pragma unroll
+          for (int l = 1; l <= P::kExact; ++l) {
+            const float x = (l < P::kExact ? __uint_as_float(L[l][i]) : t) * exp2_neg8(l);
+            if (l < P::kExact || P::kExact == 1) {
+              const float sm = __fadd_rn(ch, x);
+              const float bp = __fsub_rn(sm, ch);
+              cl = __fadd_rn(cl, __fadd_rn(__fsub_rn(ch, __fsub_rn(sm, bp)), __fsub_rn(x, bp)));
+              ch = sm;
+            } else {
+              cl = __fadd_rn(cl, x);  // six-level tail: 2^-24 of L0 and below, low word
+            }
           }
-          hi[cb * 32 + i] = hh;
-          lo[cb * 32 + i] = ll;
+          // scale by 2^(e_a + e_b - 14) and add to the running (hi, lo)
+          const int eb = (int)(int8_t)((i < 4 ? ew.x : ew.y) >> (8 * (i & 3)));
+          const float sc = pow2i(ea + eb);
+          const int j = cq * W + i;
+          const float x = ch * sc;
+          const float sm = __fadd_rn(hi[j], x);
+          const float bp = __fsub_rn(sm, hi[j]);
+          const float err = __fadd_rn(__fsub_rn(hi[j], __fsub_rn(sm, bp)), __fsub_rn(x, bp));
+          const float l2 = __fadd_rn(lo[j], __fadd_rn(err, cl * sc));
+          // renormalise so that |lo| stays within half an ulp of hi
+          hi[j] = __fadd_rn(sm, l2);
+          lo[j] = __fsub_rn(l2, __fsub_rn(hi[j], sm));
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acce0 + 8 * buf);
     }
     if (ok && nchunks > 0) {
       const int row = bi * kBM + q * 32 + lane;
       if (row < a.M) {
 #pragma unroll
-        for (int i = 0; i < kBN; ++i) {
-          const int col = bj * kBN + i;
+        for (int i = 0; i < 32; ++i) {
+          const int col = bj * kBN + half * 32 + i;
           if (col < a.N) {
             if (a.mode == 0) {
               a.work[((int64_t)blockIdx.y * 2 + out) * a.M * a.N + row + (int64_t)col * a.M] =
-                  (double)hi[i] + (double)lo[i];
-            } else {
+                  __dadd_rn(widen(hi[i]), widen(lo[i]));
+            } else if (a.mode == 1) {
               a.out32[row + (int64_t)col * a.ldo] = __fadd_rn(hi[i], lo[i]);
+            } else {
+              a.out64[row + (int64_t)col * a.ldo] = __dadd_rn(widen(hi[i]), widen(lo[i]));
             }
           }
         }
@@ -443,78 +491,92 @@ __device__ __forceinline__ int8_t chunk_exponent(double vmax) {
   return (int8_t)max(-120, min(127, row_exponent(vmax)));
 }
 
-// Four signed 8-bit digits of u = x 2^-E (|u| < 1):
-// u = 2^-7 (d1 + d2/2^8 + d3/2^16 + d4/2^24), each |d| <= 128.
-__device__ __forceinline__ void digits(double x, int E, __nv_bfloat16 (&d)[kSlices]) {
+// D signed 8-bit digits of u = x 2^-E (|u| < 1):
+// u = 2^-7 (d0 + d1/2^8 + d2/2^16 + ...), each |d| <= 128.  Every step is exact
+// in the input's own precision (FP32 input: its 24-bit mantissa spans at most
+// four digits).
+template <int D>
+__device__ __forceinline__ void digits(double x, int E, __nv_bfloat16 (&d)[D]) {
   double u = ldexp(x, 7 - E);
 #pragma unroll
-  for (int k = 0; k < kSlices; ++k) {
+  for (int k = 0; k < D; ++k) {
     const double r = rint(u);
     d[k] = __double2bfloat16(r);
     u = (u - r) * 256.0;
   }
 }
-__device__ __forceinline__ void digitsf(float x, int E, __nv_bfloat16 (&d)[kSlices]) {
-  // FP32 input: its 24-bit mantissa spans at most the first four digits, and
-  // every step below is exact in FP32
+template <int D>
+__device__ __forceinline__ void digits(float x, int E, __nv_bfloat16 (&d)[D]) {
   float u = ldexpf(x, 7 - E);
 #pragma unroll
-  for (int k = 0; k < kSlices; ++k) {
+  for (int k = 0; k < D; ++k) {
     const float r = rintf(u);
     d[k] = __float2bfloat16_rn(r);
     u = (u - r) * 256.0f;
   }
 }
 
-constexpr int kQ = kBK * kChunkSteps;  // K values per exponent chunk
+__device__ __forceinline__ float absmax(float m, float x) { return fmaxf(m, fabsf(x)); }
+__device__ __forceinline__ double absmax(double m, double x) { return fmax(m, fabs(x)); }
+__device__ __forceinline__ float warp_max(float m) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  return m;
+}
+__device__ __forceinline__ double warp_max(double m) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  return m;
+}
 
 // Chunk exponents of the columns of X: esc[q * NP + col] = E(max over t in chunk
 // q of |X[t + col ldx]|), one warp per (column, chunk).
-__global__ void k_chunk_exp_cols(const float* __restrict__ X, int64_t ldx, int64_t nd, int ncol,
+template <typename T>
+__global__ void k_chunk_exp_cols(const T* __restrict__ X, int64_t ldx, int64_t nd, int ncol,
                                  int nq, int NP, int8_t* __restrict__ esc) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= (int64_t)ncol * nq) return;
   const int col = (int)(w % ncol), q = (int)(w / ncol);
-  const float* x = X + (int64_t)col * ldx;
-  float m = 0.f;
+  const T* x = X + (int64_t)col * ldx;
+  T m = 0;
   const int64_t t1 = min((int64_t)(q + 1) * kQ, nd);
-  for (int64_t t = (int64_t)q * kQ + lane; t < t1; t += 32) m = fmaxf(m, fabsf(x[t]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int64_t t = (int64_t)q * kQ + lane; t < t1; t += 32) m = absmax(m, x[t]);
+  m = warp_max(m);
   if (lane == 0) esc[(int64_t)q * NP + col] = chunk_exponent((double)m);
 }
 
 // Column exponents f_k of X (one block per column), used to balance columns.
-__global__ void k_col_exponent(const float* __restrict__ X, int64_t ldx, int64_t nd,
+template <typename T>
+__global__ void k_col_exponent(const T* __restrict__ X, int64_t ldx, int64_t nd,
                                int* __restrict__ esc) {
-  __shared__ float sm[32];
-  const float* x = X + (int64_t)blockIdx.x * ldx;
-  float m = 0.f;
-  for (int64_t t = threadIdx.x; t < nd; t += blockDim.x) m = fmaxf(m, fabsf(x[t]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ T sm[32];
+  const T* x = X + (int64_t)blockIdx.x * ldx;
+  T m = 0;
+  for (int64_t t = threadIdx.x; t < nd; t += blockDim.x) m = absmax(m, x[t]);
+  m = warp_max(m);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float r = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, sm[w]);
+    T r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = absmax(r, sm[w]);
     esc[blockIdx.x] = row_exponent((double)r);
   }
 }
 
 // Chunk exponents of the rows of the column-balanced X (rotation A operand):
 // esc[q * MP + t] = E(max over k in chunk q of |X[t + k ldx]| 2^-f_k).
-__global__ void k_chunk_exp_rows(const float* __restrict__ X, int64_t ldx, int64_t nd, int ns,
+template <typename T>
+__global__ void k_chunk_exp_rows(const T* __restrict__ X, int64_t ldx, int64_t nd, int ns,
                                  const int* __restrict__ fcol, int MP, int8_t* __restrict__ esc) {
   const int q = blockIdx.y;
   const int k1 = min((q + 1) * kQ, ns);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nd;
        t += (int64_t)gridDim.x * blockDim.x) {
-    float m = 0.f;
+    double m = 0.0;
     for (int k = q * kQ; k < k1; ++k)
-      m = fmaxf(m, ldexpf(fabsf(X[t + (int64_t)k * ldx]), -fcol[k]));
-    esc[(int64_t)q * MP + t] = chunk_exponent((double)m);
+      m = fmax(m, ldexp(fabs((double)X[t + (int64_t)k * ldx]), -fcol[k]));
+    esc[(int64_t)q * MP + t] = chunk_exponent(m);
   }
 }
 
@@ -528,41 +590,44 @@ __global__ void k_chunk_exp_z(const double* __restrict__ Z, int n, const int* __
   const int j = (int)(w % n), q = (int)(w / n);
   double m = 0.0;
   const int k1 = min((q + 1) * kQ, n);
-  for (int k = q * kQ + lane; k < k1; k += 32) m = fmax(m, ldexp(fabs(Z[k + (int64_t)j * n]), fcol[k]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int k = q * kQ + lane; k < k1; k += 32)
+    m = fmax(m, ldexp(fabs(Z[k + (int64_t)j * n]), fcol[k]));
+  m = warp_max(m);
   if (lane == 0) esc[(int64_t)q * NP + j] = chunk_exponent(m);
 }
 
 // S[s][col][t] = digit s of X[t + col ldx] at its chunk's exponent (ld = lds)
-__global__ void k_slice_cols(const float* __restrict__ X, int64_t ldx, int64_t nd, int ncol,
+template <typename T, int D>
+__global__ void k_slice_cols(const T* __restrict__ X, int64_t ldx, int64_t nd, int ncol,
                              const int8_t* __restrict__ esc, int NP,
                              __nv_bfloat16* __restrict__ S, int64_t lds) {
   const int col = blockIdx.y;
   const int64_t plane = lds * ncol;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < lds;
        t += (int64_t)gridDim.x * blockDim.x) {
-    __nv_bfloat16 d[kSlices];
+    __nv_bfloat16 d[D];
     const int E = esc[(t / kQ) * NP + col];
-    digitsf(t < nd ? X[t + col * ldx] : 0.f, E, d);
+    digits<D>(t < nd ? X[t + col * ldx] : T(0), E, d);
     const int64_t o = t + col * lds;
 #pragma unroll
-    for (int k = 0; k < kSlices; ++k) S[k * plane + o] = d[k];
+    for (int k = 0; k < D; ++k) S[k * plane + o] = d[k];
   }
 }
 
 // Transposed digits of the column-balanced X: S[s][t][k] = digit s of
 // X[t + k ldx] 2^-f_k at row t's exponent (ld = ldk)
-__global__ void k_slice_transpose(const float* __restrict__ X, int64_t ldx, int64_t nd, int ns,
+template <typename T, int D>
+__global__ void k_slice_transpose(const T* __restrict__ X, int64_t ldx, int64_t nd, int ns,
                                   const int* __restrict__ fcol, const int8_t* __restrict__ esc,
                                   int MP, __nv_bfloat16* __restrict__ S, int64_t ldk) {
-  __shared__ float tile[32][33];
+  __shared__ T tile[32][33];
   const int64_t t0 = (int64_t)blockIdx.x * 32;
   const int k0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int k = k0 + r;
     const int64_t t = t0 + threadIdx.x;
-    tile[r][threadIdx.x] = (k < ns && t < nd) ? ldexpf(X[t + (int64_t)k * ldx], -fcol[k]) : 0.f;
+    tile[r][threadIdx.x] =
+        (k < ns && t < nd) ? (T)ldexp((double)X[t + (int64_t)k * ldx], -fcol[k]) : T(0);
   }
   __syncthreads();
   const int64_t plane = ldk * nd;
@@ -570,17 +635,18 @@ __global__ void k_slice_transpose(const float* __restrict__ X, int64_t ldx, int6
     const int64_t t = t0 + r;
     const int k = k0 + threadIdx.x;
     if (t < nd && k < ldk) {
-      __nv_bfloat16 d[kSlices];
-      digitsf(tile[threadIdx.x][r], esc[(int64_t)(k / kQ) * MP + t], d);
+      __nv_bfloat16 d[D];
+      digits<D>(tile[threadIdx.x][r], esc[(int64_t)(k / kQ) * MP + t], d);
       const int64_t o = t * ldk + k;
 #pragma unroll
-      for (int q = 0; q < kSlices; ++q) S[q * plane + o] = d[q];
+      for (int q = 0; q < D; ++q) S[q * plane + o] = d[q];
     }
   }
 }
 
 // Z digits of the row-scaled Z: S[s][j][k] = digit s of Z[k + j n] 2^f_k at
 // column j's exponent, ld = ldk  (X Z = (X 2^-f) (2^f Z): the scalings cancel)
+template <int D>
 __global__ void k_slice_z(const double* __restrict__ Z, int n, const int* __restrict__ fcol,
                           const int8_t* __restrict__ esc, int NP, __nv_bfloat16* __restrict__ S,
                           int64_t ldk) {
@@ -589,10 +655,11 @@ __global__ void k_slice_z(const double* __restrict__ Z, int n, const int* __rest
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / ldk), k = (int)(e % ldk);
-    __nv_bfloat16 d[kSlices];
-    digits(k < n ? ldexp(Z[k + (int64_t)j * n], fcol[k]) : 0.0, esc[(int64_t)(k / kQ) * NP + j], d);
+    __nv_bfloat16 d[D];
+    digits<D>(k < n ? ldexp(Z[k + (int64_t)j * n], fcol[k]) : 0.0,
+              esc[(int64_t)(k / kQ) * NP + j], d);
 #pragma unroll
-    for (int q = 0; q < kSlices; ++q) S[q * plane + e] = d[q];
+    for (int q = 0; q < D; ++q) S[q * plane + e] = d[q];
   }
 }
 
@@ -612,34 +679,161 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3-D BF16 tensor map: dims (inner, rows, slices), box (64, box_rows, slices), 128-byte swizzle.
+// 3-D BF16 tensor map of D digit planes: dims (inner, rows, D), box
+// (kBK, box_rows, D), swizzle of one kBK-element row (128 or 64 bytes).
+template <class P>
 bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
               uint32_t box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
-  cuuint64_t dims[3] = {inner, rows, (cuuint64_t)kSlices};
+  cuuint64_t dims[3] = {inner, rows, (cuuint64_t)P::kD};
   cuuint64_t strides[2] = {ld * 2, ld * rows * 2};
-  cuuint32_t box[3] = {kBK, box_rows, (cuuint32_t)kSlices};
+  cuuint32_t box[3] = {(cuuint32_t)P::kBK, box_rows, (cuuint32_t)P::kD};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
-                                      const_cast<void*>(base), dims, strides, box, estr,
-                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   P::kSwizzle == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
+template <int D, int NL>
 cudaError_t launch_tc(const CUtensorMap& tA, const CUtensorMap& tB0, const CUtensorMap& tB1,
                       const TcArgs& a, dim3 grid, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  using P = Plan<D, NL>;
+  // the shared-memory opt-in is per device: set it once on each
+  static std::mutex mu;
+  static bool done[128] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    if (!done[dev]) {
+      e = cudaFuncSetAttribute(k_tc_gemm<D, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               P::kSmemBytes);
+      if (e != cudaSuccess) return e;
+      done[dev] = true;
+    }
   }
-  note_launch(), k_tc_gemm<<<grid, kThreads, kSmemBytes, st>>>(tA, tB0, tB1, a);
+  note_launch(), k_tc_gemm<D, NL><<<grid, kThreads, P::kSmemBytes, st>>>(tA, tB0, tB1, a);
   return cudaGetLastError();
+}
+
+template <typename T>
+struct PlanOf;
+template <>
+struct PlanOf<float> {
+  using type = PlanF32;
+};
+template <>
+struct PlanOf<double> {
+  using type = PlanF64;
+};
+
+template <class P, typename TX, typename TY>
+cudaError_t tc_project_t(const TX* Xt, int64_t ldx, const TY* Yt, int64_t ldy, int64_t nd, int ns,
+                         double* Hs, double* Ms, double* work, int nsplit, __nv_bfloat16* SX,
+                         __nv_bfloat16* SY, int* esc, int* status, cudaStream_t st) {
+  constexpr int D = P::kD;
+  // digits of both operands, K-major (t contiguous per orbital column), each
+  // (orbital column, chunk) at its own exponent
+  const int64_t lds = (nd + 63) / 64 * 64;
+  const int nq = (int)((lds + kQ - 1) / kQ);
+  const int NP = (ns + 127) / 128 * 128;
+  int8_t* escX = reinterpret_cast<int8_t*>(esc);
+  int8_t* escY = escX + (size_t)nq * NP;
+  const unsigned eg = (unsigned)(((int64_t)ns * nq * 32 + 255) / 256);
+  note_launch(), k_chunk_exp_cols<TX><<<eg, 256, 0, st>>>(Xt, ldx, nd, ns, nq, NP, escX);
+  note_launch(), k_chunk_exp_cols<TY><<<eg, 256, 0, st>>>(Yt, ldy, nd, ns, nq, NP, escY);
+  dim3 sg((unsigned)std::min<int64_t>((lds + 255) / 256, 64), ns);
+  note_launch(), k_slice_cols<TX, D><<<sg, 256, 0, st>>>(Xt, ldx, nd, ns, escX, NP, SX, lds);
+  note_launch(), k_slice_cols<TY, D><<<sg, 256, 0, st>>>(Yt, ldy, nd, ns, escY, NP, SY, lds);
+  CUtensorMap mXa, mXb, mYb;
+  if (!make_map<P>(&mXa, SX, (uint64_t)lds, (uint64_t)ns, (uint64_t)lds, kBM) ||
+      !make_map<P>(&mXb, SX, (uint64_t)lds, (uint64_t)ns, (uint64_t)lds, kBN) ||
+      !make_map<P>(&mYb, SY, (uint64_t)lds, (uint64_t)ns, (uint64_t)lds, kBN))
+    return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.M = ns;
+  a.N = ns;
+  a.K = lds;
+  int64_t kc = (lds + nsplit - 1) / nsplit;
+  a.kchunk = (kc + kQ - 1) / kQ * kQ;  // splits start on exponent chunks
+  a.upper = 1;
+  a.tiles_m = (ns + kBM - 1) / kBM;
+  a.tiles_n = (ns + kBN - 1) / kBN;
+  a.work = work;
+  a.mode = 0;
+  a.escA = escX;
+  a.escB0 = escY;
+  a.escB1 = escX;
+  a.MP = NP;
+  a.NP = NP;
+  a.status = status;
+  const int nsp = (int)((lds + a.kchunk - 1) / a.kchunk);
+  // out 0: Hs = X^T Y (B = Y slices), out 1: Ms = X^T X (B = X slices); tiles
+  // entirely below the diagonal exit at once
+  cudaError_t e = launch_tc<P::kD, P::kNL>(mXa, mYb, mXb, a, dim3(a.tiles_m * a.tiles_n, nsp, 2),
+                                           st);
+  if (e != cudaSuccess) return e;
+  // the SIMT path's deterministic split reduction (upper elements, mirrored)
+  return project_reduce(work, nsp, ns, Hs, Ms, st);
+}
+
+template <typename T>
+cudaError_t tc_rotate_t(const T* Xt, int64_t ld, int64_t nd, int ns, const double* Z, T* Xout,
+                        int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc, int* status,
+                        cudaStream_t st) {
+  using P = typename PlanOf<T>::type;
+  constexpr int D = P::kD;
+  // digits of Xt per grid point t (over its ns entries) and of Z per column j
+  const int64_t ldk = (ns + 7) / 8 * 8;
+  const int nq = (int)((ldk + kQ - 1) / kQ);
+  const int MP = (int)((nd + 127) / 128 * 128), NP = (ns + 127) / 128 * 128;
+  int* fcol = esc;  // ns entries: column exponents of Xt
+  int8_t* escT = reinterpret_cast<int8_t*>(esc + ((ns + 63) / 64 * 64));
+  int8_t* escZ = escT + (size_t)nq * MP;
+  note_launch(), k_col_exponent<T><<<ns, 256, 0, st>>>(Xt, ld, nd, fcol);
+  note_launch(), k_chunk_exp_rows<T><<<dim3((unsigned)std::min<int64_t>((nd + 255) / 256, 4096),
+                                            nq),
+                                       256, 0, st>>>(Xt, ld, nd, ns, fcol, MP, escT);
+  note_launch(), k_chunk_exp_z<<<(unsigned)(((int64_t)ns * nq * 32 + 255) / 256), 256, 0, st>>>(
+      Z, ns, fcol, nq, NP, escZ);
+  dim3 tg((unsigned)((nd + 31) / 32), (unsigned)((ldk + 31) / 32));
+  note_launch(), k_slice_transpose<T, D><<<tg, dim3(32, 8), 0, st>>>(Xt, ld, nd, ns, fcol, escT,
+                                                                     MP, SA, ldk);
+  note_launch(), k_slice_z<D><<<(unsigned)std::min<int64_t>(((int64_t)ns * ldk + 255) / 256,
+                                                            4096),
+                                256, 0, st>>>(Z, ns, fcol, escZ, NP, SZ, ldk);
+  CUtensorMap mA, mZ;
+  if (!make_map<P>(&mA, SA, (uint64_t)ldk, (uint64_t)nd, (uint64_t)ldk, kBM) ||
+      !make_map<P>(&mZ, SZ, (uint64_t)ldk, (uint64_t)ns, (uint64_t)ldk, kBN))
+    return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.M = (int)nd;
+  a.N = ns;
+  a.K = ldk;
+  a.kchunk = (ldk + kQ - 1) / kQ * kQ;
+  a.upper = 0;
+  a.tiles_m = (int)((nd + kBM - 1) / kBM);
+  a.tiles_n = (ns + kBN - 1) / kBN;
+  if (std::is_same<T, float>::value) {
+    a.out32 = reinterpret_cast<float*>(Xout);
+    a.mode = 1;
+  } else {
+    a.out64 = reinterpret_cast<double*>(Xout);
+    a.mode = 2;
+  }
+  a.ldo = ldo;
+  a.escA = escT;
+  a.escB0 = escZ;
+  a.escB1 = escZ;
+  a.MP = MP;
+  a.NP = NP;
+  a.status = status;
+  return launch_tc<P::kD, P::kNL>(mA, mZ, mZ, a, dim3(a.tiles_m * a.tiles_n, 1, 1), st);
 }
 
 }  // namespace
@@ -655,9 +849,13 @@ size_t tc_esc_bytes(int64_t ld, int64_t nd, int ns_max) {
   return (size_t)std::max(proj, rot) + 256;
 }
 
-size_t tc_slice_elems(int64_t ld, int64_t nd, int ns_max) {
+int tc_digits(bool fp64) { return fp64 ? PlanF64::kD : PlanF32::kD; }
+
+size_t tc_slice_elems(int64_t ld, int64_t nd, int ns_max, bool fp64) {
   const int64_t ldk = (ns_max + 7) / 8 * 8;
-  return (size_t)kSlices * std::max<int64_t>(ld * ns_max, nd * ldk);
+  const int64_t lds = (nd + 63) / 64 * 64;
+  return (size_t)tc_digits(fp64) *
+         std::max<int64_t>(std::max(ld, lds) * ns_max, nd * ldk);
 }
 
 int tc_project_nsplit(int ns) {
@@ -674,92 +872,31 @@ int tc_project_nsplit(int ns) {
 cudaError_t tc_project(const float* Xt, const float* Yt, int64_t ld, int64_t nd, int ns,
                        double* Hs, double* Ms, double* work, int nsplit, __nv_bfloat16* SX,
                        __nv_bfloat16* SY, int* esc, int* status, cudaStream_t st) {
-  // digits of both operands, K-major (t contiguous per orbital column), each
-  // orbital column at its own exponent
-  const int64_t lds = (nd + 63) / 64 * 64;
-  const int nq = (int)((lds + kQ - 1) / kQ);
-  const int NP = (ns + 127) / 128 * 128;
-  int8_t* escX = reinterpret_cast<int8_t*>(esc);
-  int8_t* escY = escX + (size_t)nq * NP;
-  const unsigned eg = (unsigned)(((int64_t)ns * nq * 32 + 255) / 256);
-  note_launch(), k_chunk_exp_cols<<<eg, 256, 0, st>>>(Xt, ld, nd, ns, nq, NP, escX);
-  note_launch(), k_chunk_exp_cols<<<eg, 256, 0, st>>>(Yt, ld, nd, ns, nq, NP, escY);
-  dim3 sg((unsigned)std::min<int64_t>((lds + 255) / 256, 64), ns);
-  note_launch(), k_slice_cols<<<sg, 256, 0, st>>>(Xt, ld, nd, ns, escX, NP, SX, lds);
-  note_launch(), k_slice_cols<<<sg, 256, 0, st>>>(Yt, ld, nd, ns, escY, NP, SY, lds);
-  CUtensorMap mXa, mXb, mYb;
-  if (!make_map(&mXa, SX, (uint64_t)lds, (uint64_t)ns, (uint64_t)lds, kBM) ||
-      !make_map(&mXb, SX, (uint64_t)lds, (uint64_t)ns, (uint64_t)lds, kBN) ||
-      !make_map(&mYb, SY, (uint64_t)lds, (uint64_t)ns, (uint64_t)lds, kBN))
-    return cudaErrorInvalidValue;
-  TcArgs a{};
-  a.M = ns;
-  a.N = ns;
-  a.K = lds;
-  int64_t kc = (lds + nsplit - 1) / nsplit;
-  a.kchunk = (kc + kQ - 1) / kQ * kQ;  // splits start on exponent chunks
-  a.upper = 1;
-  a.tiles_m = (ns + kBM - 1) / kBM;
-  a.work = work;
-  a.mode = 0;
-  a.escA = escX;
-  a.escB0 = escY;
-  a.escB1 = escX;
-  a.MP = NP;
-  a.NP = NP;
-  a.status = status;
-  const int tn = (ns + kBN - 1) / kBN;
-  const int nsp = (int)((lds + a.kchunk - 1) / a.kchunk);
-  // out 0: Hs = X^T Y (B = Y slices), out 1: Ms = X^T X (B = X slices); tiles
-  // entirely below the diagonal exit at once
-  cudaError_t e = launch_tc(mXa, mYb, mXb, a, dim3(a.tiles_m * tn, nsp, 2), st);
-  if (e != cudaSuccess) return e;
-  // the SIMT path's deterministic split reduction (upper elements, mirrored)
-  return project_reduce(work, nsp, ns, Hs, Ms, st);
+  return tc_project_t<PlanF32>(Xt, ld, Yt, ld, nd, ns, Hs, Ms, work, nsplit, SX, SY, esc, status,
+                               st);
 }
-
+cudaError_t tc_project(const float* Xt, int64_t ldx, const double* Yt, int64_t ldy, int64_t nd,
+                       int ns, double* Hs, double* Ms, double* work, int nsplit,
+                       __nv_bfloat16* SX, __nv_bfloat16* SY, int* esc, int* status,
+                       cudaStream_t st) {
+  return tc_project_t<PlanF32>(Xt, ldx, Yt, ldy, nd, ns, Hs, Ms, work, nsplit, SX, SY, esc,
+                               status, st);
+}
+cudaError_t tc_project(const double* Xt, const double* Yt, int64_t ld, int64_t nd, int ns,
+                       double* Hs, double* Ms, double* work, int nsplit, __nv_bfloat16* SX,
+                       __nv_bfloat16* SY, int* esc, int* status, cudaStream_t st) {
+  return tc_project_t<PlanF64>(Xt, ld, Yt, ld, nd, ns, Hs, Ms, work, nsplit, SX, SY, esc, status,
+                               st);
+}
 cudaError_t tc_rotate(const float* Xt, int64_t ld, int64_t nd, int ns, const double* Z, float* Xout,
                       int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc, int* status,
                       cudaStream_t st) {
-  // digits of Xt per grid point t (over its ns entries) and of Z per column j
-  const int64_t ldk = (ns + 7) / 8 * 8;
-  const int nq = (int)((ldk + kQ - 1) / kQ);
-  const int MP = (int)((nd + 127) / 128 * 128), NP = (ns + 127) / 128 * 128;
-  int* fcol = esc;  // ns entries: column exponents of Xt
-  int8_t* escT = reinterpret_cast<int8_t*>(esc + ((ns + 63) / 64 * 64));
-  int8_t* escZ = escT + (size_t)nq * MP;
-  note_launch(), k_col_exponent<<<ns, 256, 0, st>>>(Xt, ld, nd, fcol);
-  note_launch(), k_chunk_exp_rows<<<dim3((unsigned)std::min<int64_t>((nd + 255) / 256, 4096), nq),
-                                    256, 0, st>>>(Xt, ld, nd, ns, fcol, MP, escT);
-  note_launch(), k_chunk_exp_z<<<(unsigned)(((int64_t)ns * nq * 32 + 255) / 256), 256, 0, st>>>(
-      Z, ns, fcol, nq, NP, escZ);
-  dim3 tg((unsigned)((nd + 31) / 32), (unsigned)((ldk + 31) / 32));
-  note_launch(), k_slice_transpose<<<tg, dim3(32, 8), 0, st>>>(Xt, ld, nd, ns, fcol, escT, MP, SA,
-                                                               ldk);
-  note_launch(), k_slice_z<<<(unsigned)std::min<int64_t>(((int64_t)ns * ldk + 255) / 256, 4096),
-                             256, 0, st>>>(Z, ns, fcol, escZ, NP, SZ, ldk);
-  CUtensorMap mA, mZ;
-  if (!make_map(&mA, SA, (uint64_t)ldk, (uint64_t)nd, (uint64_t)ldk, kBM) ||
-      !make_map(&mZ, SZ, (uint64_t)ldk, (uint64_t)ns, (uint64_t)ldk, kBN))
-    return cudaErrorInvalidValue;
-  TcArgs a{};
-  a.M = (int)nd;
-  a.N = ns;
-  a.K = ldk;
-  a.kchunk = (ldk + kQ - 1) / kQ * kQ;
-  a.upper = 0;
-  a.tiles_m = (int)((nd + kBM - 1) / kBM);
-  a.out32 = Xout;
-  a.ldo = ldo;
-  a.mode = 1;
-  a.escA = escT;
-  a.escB0 = escZ;
-  a.escB1 = escZ;
-  a.MP = MP;
-  a.NP = NP;
-  a.status = status;
-  const int tn = (ns + kBN - 1) / kBN;
-  return launch_tc(mA, mZ, mZ, a, dim3(a.tiles_m * tn, 1, 1), st);
+  return tc_rotate_t<float>(Xt, ld, nd, ns, Z, Xout, ldo, SA, SZ, esc, status, st);
+}
+cudaError_t tc_rotate(const double* Xt, int64_t ld, int64_t nd, int ns, const double* Z,
+                      double* Xout, int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc,
+                      int* status, cudaStream_t st) {
+  return tc_rotate_t<double>(Xt, ld, nd, ns, Z, Xout, ldo, SA, SZ, esc, status, st);
 }
 
 }  // namespace sparc

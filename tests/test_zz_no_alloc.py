@@ -38,7 +38,8 @@ def test_project_noalloc_matches_handle_projection_on_consecutive_calls():
     L = sparc.load()
     s = synth.make_config_system(1)
     nd = s.nd
-    h = sparc.Handle(s, "fp64", ns_max=64)
+    # the handle projection on the FP64 SIMT pipe, the kernel sparc_project_noalloc runs
+    h = sparc.Handle(s, "fp64", ns_max=64, options_flags=2)
     rng = np.random.default_rng(2302)
     for ns, pad in ((40, 0), (33, 5), (64, 32)):  # consecutive calls share the scratch
         ld = nd + pad
