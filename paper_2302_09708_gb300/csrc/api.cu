@@ -80,6 +80,10 @@ template <typename T>
 int upload(sparc_context* c, const T* host, size_t count, T** dev) {
   *dev = nullptr;
   if (count == 0) count = 1;
+  if (c->nl_nmem >= (int)(sizeof(c->nl_mem) / sizeof(c->nl_mem[0]))) {
+    c->err = "internal: too many operator tables";
+    return SPARC_ERR_CUDA;
+  }
   CK(c, cudaMalloc((void**)dev, count * sizeof(T)));
   c->nl_mem[c->nl_nmem++] = *dev;
   if (host) CK(c, cudaMemcpy(*dev, host, count * sizeof(T), cudaMemcpyHostToDevice));
@@ -414,6 +418,35 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
     }
   }
 
+  // grouped form of the pull table: G consecutive points per group, one slot
+  // per entry of the group's fullest point (missing entries are (0, 0))
+  auto build_groups = [&](int G, std::vector<int>& gptr, std::vector<int>& gk,
+                          std::vector<double>& gchi) {
+    const int64_t ng = (nd + G - 1) / G;
+    gptr.assign(ng + 1, 0);
+    for (int64_t q = 0; q < ng; ++q) {
+      int mx = 0;
+      for (int v = 0; v < G; ++v) {
+        const int64_t i = q * G + v;
+        if (i < nd) mx = std::max(mx, pull_ptr[i + 1] - pull_ptr[i]);
+      }
+      gptr[q + 1] = gptr[q] + mx;
+    }
+    const int64_t nslot = gptr[ng];
+    gk.assign((size_t)std::max<int64_t>(nslot, 1) * G, 0);
+    gchi.assign((size_t)std::max<int64_t>(nslot, 1) * G, 0.0);
+    for (int64_t q = 0; q < ng; ++q)
+      for (int v = 0; v < G; ++v) {
+        const int64_t i = q * G + v;
+        if (i >= nd) continue;
+        for (int e = pull_ptr[i]; e < pull_ptr[i + 1]; ++e) {
+          const int64_t slot = gptr[q] + (e - pull_ptr[i]);
+          gk[slot * G + v] = pull_k[e];
+          gchi[slot * G + v] = pull_chi[e];
+        }
+      }
+  };
+
   // --- device copies --------------------------------------------------------
   CK(c, cudaMalloc(&c->veff64, nd * sizeof(double)));
   CK(c, cudaMemcpy(c->veff64, veff, nd * sizeof(double), cudaMemcpyHostToDevice));
@@ -452,6 +485,18 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
       PullEntry<double>* d64;
       if ((rc = upload<PullEntry<double>>(c, pk64.data(), pk64.size(), &d64))) return rc;
       n64.pull_pk = d64;
+      std::vector<int> gptr, gk;
+      std::vector<double> gchi;
+      build_groups(2, gptr, gk, gchi);
+      int *dgp, *dgk;
+      double* dgc;
+      if ((rc = upload<int>(c, gptr.data(), gptr.size(), &dgp))) return rc;
+      if ((rc = upload<int>(c, gk.data(), gk.size(), &dgk))) return rc;
+      if ((rc = upload<double>(c, gchi.data(), gchi.size(), &dgc))) return rc;
+      n64.grp = 2;
+      n64.grp_ptr = dgp;
+      n64.grp_k = dgk;
+      n64.grp_chi = dgc;
     }
     Nonlocal<float>& n32 = c->nl32;
     n32.natoms = natoms; n32.kp = kp; n32.supp_ptr = sp; n32.supp_idx = si; n32.nproj = npj;
@@ -469,6 +514,19 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
       PullEntry<float>* d32;
       if ((rc = upload<PullEntry<float>>(c, pk32.data(), pk32.size(), &d32))) return rc;
       n32.pull_pk = d32;
+      std::vector<int> gptr, gk;
+      std::vector<double> gchi;
+      build_groups(4, gptr, gk, gchi);
+      std::vector<float> gchi32(gchi.begin(), gchi.end());
+      int *dgp, *dgk;
+      float* dgc;
+      if ((rc = upload<int>(c, gptr.data(), gptr.size(), &dgp))) return rc;
+      if ((rc = upload<int>(c, gk.data(), gk.size(), &dgk))) return rc;
+      if ((rc = upload<float>(c, gchi32.data(), gchi32.size(), &dgc))) return rc;
+      n32.grp = 4;
+      n32.grp_ptr = dgp;
+      n32.grp_k = dgk;
+      n32.grp_chi = dgc;
     }
   }
 

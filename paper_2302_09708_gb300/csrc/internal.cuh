@@ -61,6 +61,14 @@ struct Nonlocal {
   const int* pull_k = nullptr;
   const T* pull_chi = nullptr;
   const PullEntry<T>* pull_pk = nullptr;  // packed (k, chi) entries, same order
+  // The same entries by groups of `grp` consecutive grid points (grp = 4 for
+  // FP32, 2 for FP64): group q owns slots grp_ptr[q] .. grp_ptr[q + 1] - 1, as
+  // many as its fullest point has entries; slot s holds for each point v of
+  // the group its s-th (k, chi), or (0, 0) where the point has fewer.
+  int grp = 0;
+  const int* grp_ptr = nullptr;
+  const int* grp_k = nullptr;   // slots x grp
+  const T* grp_chi = nullptr;   // slots x grp
 };
 
 // Launchers (stencil.cu) -------------------------------------------------
@@ -222,7 +230,7 @@ struct sparc_context {
   // nonlocal tables
   sparc::Nonlocal<double> nl64;
   sparc::Nonlocal<float> nl32;
-  void* nl_mem[24] = {};
+  void* nl_mem[32] = {};
   int nl_nmem = 0;
   // workspaces
   void* W1 = nullptr;

@@ -86,6 +86,16 @@ __device__ __forceinline__ void ldg(T (&d)[V], const T* p) {
 #pragma unroll
   for (int i = 0; i < V; ++i) d[i] = s[i];
 }
+template <int V>
+__device__ __forceinline__ void ldg_idx(int (&d)[V], const int* p) {
+  if constexpr (V == 4) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(p));
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+  } else {
+    const int2 v = __ldg(reinterpret_cast<const int2*>(p));
+    d[0] = v.x; d[1] = v.y;
+  }
+}
 template <typename T, int V>
 __device__ __forceinline__ void stg(T* p, const T (&d)[V]) {
   typename Vec<T, V>::t v;
@@ -102,8 +112,9 @@ struct RingArgs {
   const T* prev;
   int64_t ldp;
   const T* veff;
-  const int* pull_ptr;
-  const PullEntry<T>* pull_pk;
+  const int* grp_ptr;  // grouped nonlocal slots, VX points per group
+  const int* grp_k;
+  const T* grp_chi;
   const T* D;
   int kp;
   uint32_t d_off;  // byte offset of the orbital's D column in dynamic shared memory
@@ -235,31 +246,21 @@ __global__ void __launch_bounds__(384, 1)
 
   for (int z = z0; z < z1; ++z) {
     if (__shfl_sync(full_mask, *abort, 0)) break;
-    // prefetch Veff / prev of this plane
+    // Veff, prev and the nonlocal slot range of this plane (used after the
+    // stencil sums, which cover their latency)
     const int64_t g0 = z * nxy + (int64_t)gy0 * a.nx + x;
     T vf[VY][VX], pv[VY][VX];
-    int pptr[VY][VX + 1];
+    int gs[VY], ge[VY];
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
-      const bool in = gy0 + r < a.ny;
-      if (in) {
+      gs[r] = ge[r] = 0;
+      if (gy0 + r < a.ny) {
         ldg<T, VX>(vf[r], a.veff + g0 + r * a.nx);
         if (pn) ldg<T, VX>(pv[r], pn + g0 + r * a.nx);
         if (a.kp > 0) {
-          // VX + 1 consecutive pull offsets of the row's points
-          const int* pp = a.pull_ptr + g0 + r * a.nx;
-          if constexpr (VX == 4) {
-            // g0 + r nx is a multiple of 4 here (x and nx are), so int4 is aligned
-            const int4 p4 = __ldg(reinterpret_cast<const int4*>(pp));
-            pptr[r][0] = p4.x;
-            pptr[r][1] = p4.y;
-            pptr[r][2] = p4.z;
-            pptr[r][3] = p4.w;
-          } else {
-#pragma unroll
-            for (int v = 0; v < VX; ++v) pptr[r][v] = __ldg(pp + v);
-          }
-          pptr[r][VX] = __ldg(pp + VX);
+          const int64_t q = (g0 + r * a.nx) / VX;
+          gs[r] = __ldg(a.grp_ptr + q);
+          ge[r] = __ldg(a.grp_ptr + q + 1);
         }
       }
     }
@@ -340,27 +341,28 @@ __global__ void __launch_bounds__(384, 1)
       if (wait(su32(&empty[sz]), round_of(z) & 1)) issue(z + S);
     }
     __syncwarp();
-    // Veff, nonlocal pull-add, recurrence, store
+    // Veff, nonlocal pull-add (one slot = VX (k, chi) pairs), recurrence, store
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
       if (gy0 + r >= a.ny) continue;
       const int64_t g = g0 + r * a.nx;
+      T h[VX];
+#pragma unroll
+      for (int v = 0; v < VX; ++v) h[v] = acc[r][v] + vf[r][v] * q[R][r][v];
+      for (int sl = gs[r]; sl < ge[r]; ++sl) {
+        int kk[VX];
+        T ch[VX];
+        ldg_idx<VX>(kk, a.grp_k + (int64_t)sl * VX);
+        ldg<T, VX>(ch, a.grp_chi + (int64_t)sl * VX);
+#pragma unroll
+        for (int v = 0; v < VX; ++v) h[v] += ch[v] * dsh[kk[v]];
+      }
       T out[VX];
 #pragma unroll
-      for (int v = 0; v < VX; ++v) {
-        T h = acc[r][v] + vf[r][v] * q[R][r][v];
-        if (a.kp > 0) {
-          T nl = T(0);
-          for (int e = pptr[r][v]; e < pptr[r][v + 1]; ++e) {
-            const PullEntry<T> pe = a.pull_pk[e];
-            nl += pe.chi * dsh[pe.k];
-          }
-          h += nl;
-        }
-        out[v] = pn ? a.s_h * h + a.s_p * pv[r][v] : a.s_h * h;
-      }
+      for (int v = 0; v < VX; ++v) out[v] = pn ? a.s_h * h[v] + a.s_p * pv[r][v] : a.s_h * h[v];
       stg<T, VX>(yn + g, out);
     }
+
 #pragma unroll
     for (int j = 0; j < 2 * R; ++j)
 #pragma unroll
@@ -453,7 +455,7 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
   int by, slots, threads;
   uint32_t slot_bytes;
   if (!ring_plan<T>(g, nl.kp, by, slots, slot_bytes, threads)) return cudaSuccess;
-  if (nl.kp > 0 && !nl.pull_pk) return cudaSuccess;
+  if (nl.kp > 0 && (!nl.grp_ptr || nl.grp != VX)) return cudaSuccess;
   const int va = 16 / sizeof(T);
   if (ldx % va || ldy % va || (prev && ldp % va) || ((uintptr_t)x % 16) || ((uintptr_t)y % 16) ||
       (prev && ((uintptr_t)prev % 16)) || ((uintptr_t)veff % 16))
@@ -463,7 +465,7 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
     return cudaSuccess;
   RingArgs<T> a;
   a.y = y; a.ldy = ldy; a.prev = prev; a.ldp = ldp; a.veff = veff;
-  a.pull_ptr = nl.pull_ptr; a.pull_pk = nl.pull_pk; a.D = D; a.kp = nl.kp;
+  a.grp_ptr = nl.grp_ptr; a.grp_k = nl.grp_k; a.grp_chi = nl.grp_chi; a.D = D; a.kp = nl.kp;
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.bcx = g.bc[0]; a.bcy = g.bc[1]; a.bcz = g.bc[2];
   a.by = by;
   a.nslab = (g.ny + by - 1) / by;
