@@ -101,7 +101,13 @@ typedef struct {
                       reserved[0] bit 1 (FP64 handles): projection and rotation
                       on the FP64 SIMT pipe instead of the FP64-accurate
                       six-digit tensor-core split (about 2^-45 relative to
-                      sum |x_k y_k|).  Other bits and entries 0.            */
+                      sum |x_k y_k|).
+                      reserved[0] bit 2 (FP64 handles): H x of FP64 blocks in
+                      double-FP32 arithmetic (48-bit pairs on the FP32 pipe,
+                      ~5x faster, ~1e-13 relative; Ritz values stay within
+                      1e-8 Ha, the subspace of nearly degenerate top states
+                      may move by ~1e-7).  Mixed handles always evaluate their
+                      FP64 Yt this way.  Other bits and entries 0.          */
 } sparc_options;
 
 /* Stage times (ms) of the last sparc_chefsi_step on the handle (CUDA events)

@@ -40,6 +40,12 @@ namespace {
 const double kW[kRadius + 1] = {-5369.0 / 1800.0, 12.0 / 7.0,   -15.0 / 56.0,  10.0 / 189.0,
                                 -1.0 / 112.0,     2.0 / 1925.0, -1.0 / 16632.0};
 
+// (hi, lo) FP32 pair of a double: hi = nearest float, lo = nearest float to the rest
+float2 df_pair(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 struct Fail {
   int code;
 };
@@ -109,6 +115,13 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
   const T* veff = std::is_same<T, double>::value ? (const T*)c->veff64 : (const T*)c->veff32;
   T* D = (T*)c->D;
   CK(c, nl_coefficients<T>(nl, c->h * c->h * c->h, x, ldx, ns, D, st));
+  if (std::is_same<T, double>::value && c->ring_enabled && c->df_stencil) {
+    bool used = false;
+    CK(c, apply_h_ring_df(c->grid, c->lap, c->veff_df, c->nl64, (const double*)D,
+                          (const double*)x, ldx, (double*)y, ldy, (const double*)prev, ldp, ns,
+                          shift, s_h, s_p, c->eig.status + 3, st, &used));
+    if (used) return SPARC_OK;
+  }
   CK(c, apply_h<T>(c->grid, c->lap, veff, nl, D, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
                    c->ring_enabled ? c->eig.status + 3 : nullptr, st));
   return SPARC_OK;
@@ -327,7 +340,7 @@ int stage_out(sparc_context* c, void* X, int ns, int64_t ld, int dtype, cudaStre
 void destroy_ctx(sparc_context* c) {
   if (!c) return;
   for (int i = 0; i < c->nl_nmem; ++i) cudaFree(c->nl_mem[i]);
-  cudaFree(c->veff64); cudaFree(c->veff32);
+  cudaFree(c->veff64); cudaFree(c->veff32); cudaFree(c->veff_df);
   cudaFree(c->W1); cudaFree(c->W2); cudaFree(c->Wstage); cudaFree(c->D);
   cudaFree(c->S1); cudaFree(c->S2); cudaFree(c->SZ); cudaFree(c->esc); cudaFree(c->Y64);
   cudaFree(c->Hs); cudaFree(c->Ms); cudaFree(c->Z); cudaFree(c->lam); cudaFree(c->proj_work);
@@ -450,6 +463,12 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
   // --- device copies --------------------------------------------------------
   CK(c, cudaMalloc(&c->veff64, nd * sizeof(double)));
   CK(c, cudaMemcpy(c->veff64, veff, nd * sizeof(double), cudaMemcpyHostToDevice));
+  {
+    std::vector<float2> vdf(nd);
+    for (int64_t i = 0; i < nd; ++i) vdf[i] = df_pair(veff[i]);
+    CK(c, cudaMalloc(&c->veff_df, nd * sizeof(float2)));
+    CK(c, cudaMemcpy(c->veff_df, vdf.data(), nd * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   std::vector<float> f32(std::max<int64_t>(std::max<int64_t>(nd, nent), nchi_tot) + 1);
   if (c->precision == SPARC_PREC_MIXED) {
     for (int64_t i = 0; i < nd; ++i) f32[i] = (float)veff[i];
@@ -497,6 +516,11 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
       n64.grp_ptr = dgp;
       n64.grp_k = dgk;
       n64.grp_chi = dgc;
+      std::vector<float2> gdf(gchi.size());
+      for (size_t t = 0; t < gchi.size(); ++t) gdf[t] = df_pair(gchi[t]);
+      float2* dgdf;
+      if ((rc = upload<float2>(c, gdf.data(), gdf.size(), &dgdf))) return rc;
+      n64.grp_chi_df = dgdf;
     }
     Nonlocal<float>& n32 = c->nl32;
     n32.natoms = natoms; n32.kp = kp; n32.supp_ptr = sp; n32.supp_idx = si; n32.nproj = npj;
@@ -532,6 +556,9 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
 
   // --- workspace ----------------------------------------------------------
   c->ring_enabled = !(opt && (opt->reserved[0] & 1));
+  // double-FP32 stencil: always for the mixed form's FP64 Yt, opt-in (bit 2)
+  // for FP64 handles, whose subspace target needs the full 53 bits
+  c->df_stencil = c->precision == SPARC_PREC_MIXED || (opt && (opt->reserved[0] & 4));
   // mixed handles always take the tensor-core GEMMs; FP64 handles unless bit 1
   c->tc_gemm = c->precision == SPARC_PREC_MIXED || !(opt && (opt->reserved[0] & 2));
   const size_t es = c->precision == SPARC_PREC_MIXED ? 4 : 8;

@@ -69,6 +69,7 @@ struct Nonlocal {
   const int* grp_ptr = nullptr;
   const int* grp_k = nullptr;   // slots x grp
   const T* grp_chi = nullptr;   // slots x grp
+  const float2* grp_chi_df = nullptr;  // FP64 tables: chi as (hi, lo) FP32 pairs
 };
 
 // Launchers (stencil.cu) -------------------------------------------------
@@ -87,6 +88,17 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
                          const T* D, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
                          int64_t ldp, int ns, double shift, double s_h, double s_p, int* status,
                          cudaStream_t st, bool* used);
+// Ring plan (stencil_tma.cu): slab rows, ring slots, slot bytes and threads for
+// a grid and element type, or false when the generic kernel must run.
+template <typename T>
+bool ring_plan(const Grid& g, int kp, int& by, int& slots, uint32_t& slot_bytes, int& threads);
+// FP64 blocks in double-FP32 arithmetic (stencil_df.cu); *used = false when
+// the grid or the buffers do not fit the ring form.
+cudaError_t apply_h_ring_df(const Grid& g, const LapCoef& lc, const float2* veff_df,
+                            const Nonlocal<double>& nl, const double* D, const double* x,
+                            int64_t ldx, double* y, int64_t ldy, const double* prev, int64_t ldp,
+                            int ns, double shift, double s_h, double s_p, int* status,
+                            cudaStream_t st, bool* used);
 
 // D[n * kp + k] = gamma_k h^3 sum_s chi[s][k] x[idx_s + n ldx]
 template <typename T>
@@ -261,5 +273,7 @@ struct sparc_context {
   bool ring_enabled = true;  // TMA-ring stencil (options.reserved[0] bit 0 turns it off)
   bool tc_gemm = true;       // tensor-core projection/rotation (FP64: reserved[0] bit 1 off)
   double* Y64 = nullptr;     // mixed handles: FP64 Yt = H Xt of a step (ld x ns_max)
+  float2* veff_df = nullptr; // Veff as (hi, lo) FP32 pairs for the double-FP32 stencil
+  bool df_stencil = false;   // FP64 H x in double-FP32 arithmetic (mixed Yt; reserved[0] bit 2)
   std::string err;
 };

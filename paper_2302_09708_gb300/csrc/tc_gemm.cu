@@ -495,14 +495,34 @@ __device__ __forceinline__ int8_t chunk_exponent(double vmax) {
 // u = 2^-7 (d0 + d1/2^8 + d2/2^16 + ...), each |d| <= 128.  Every step is exact
 // in the input's own precision (FP32 input: its 24-bit mantissa spans at most
 // four digits).
+// FP64 input: integer arithmetic on the IEEE-754 fields (GB300's FP64 pipe is
+// 1/64 of its FP32 rate): F = x 2^(7 + 8(D-1) - E) rounded to an integer
+// (|F| < 2^(7 + 8(D-1))), then d_k = round(F / 2^s), F -= d_k 2^s for
+// s = 8(D-1-k); the remainders stay within half a digit, so |d_k| <= 128.
 template <int D>
 __device__ __forceinline__ void digits(double x, int E, __nv_bfloat16 (&d)[D]) {
-  double u = ldexp(x, 7 - E);
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF);
+  long long F = 0;
+  if (e != 0 && e != 0x7FF) {  // zero and subnormals give zero digits
+    const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = e - 1075 + 7 + 8 * (D - 1) - E;  // F = m 2^sh
+    unsigned long long f = 0;
+    if (sh >= 0) f = sh < 11 ? (m << sh) : 0ull;  // |x| < 2^E keeps sh < 0 in practice
+    else if (sh > -64) f = (m >> (-sh)) + ((m >> (-sh - 1)) & 1ull);  // round half up
+    F = (u >> 63) ? -(long long)f : (long long)f;
+  }
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    const double r = rint(u);
-    d[k] = __double2bfloat16(r);
-    u = (u - r) * 256.0;
+    const int s = 8 * (D - 1 - k);
+    long long dk;
+    if (s > 0) {
+      dk = (F + (1ll << (s - 1))) >> s;
+      F -= dk << s;
+    } else {
+      dk = F;
+    }
+    d[k] = __float2bfloat16_rn((float)(int)dk);
   }
 }
 template <int D>
@@ -516,16 +536,34 @@ __device__ __forceinline__ void digits(float x, int E, __nv_bfloat16 (&d)[D]) {
   }
 }
 
+// |x| 2^-f as an order-preserving integer key (the IEEE-754 bits of the
+// magnitude, exponent lowered by f; 0 for zero and values that would leave the
+// normal range downwards).  key_exponent gives frexp's exponent of the value.
+__device__ __forceinline__ long long mag_key(double x, int f = 0) {
+  const long long b = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll;
+  const long long e = b >> 52;
+  if (e == 0) return 0;
+  const long long e2 = e - f;
+  if (e2 <= 0) return 0;
+  if (e2 >= 0x7FF) return 0x7FEFFFFFFFFFFFFFll;
+  return b - ((long long)f << 52);
+}
+__device__ __forceinline__ int key_exponent(long long k) {
+  return k == 0 ? 0 : (int)(k >> 52) - 1022;  // m 2^e, m in [0.5, 1)
+}
+__device__ __forceinline__ int8_t chunk_exponent_key(long long k) {
+  return (int8_t)max(-120, min(127, key_exponent(k)));
+}
+__device__ __forceinline__ long long warp_max(long long m) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  return m;
+}
+
 __device__ __forceinline__ float absmax(float m, float x) { return fmaxf(m, fabsf(x)); }
-__device__ __forceinline__ double absmax(double m, double x) { return fmax(m, fabs(x)); }
 __device__ __forceinline__ float warp_max(float m) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  return m;
-}
-__device__ __forceinline__ double warp_max(double m) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   return m;
 }
 
@@ -539,28 +577,40 @@ __global__ void k_chunk_exp_cols(const T* __restrict__ X, int64_t ldx, int64_t n
   if (w >= (int64_t)ncol * nq) return;
   const int col = (int)(w % ncol), q = (int)(w / ncol);
   const T* x = X + (int64_t)col * ldx;
-  T m = 0;
   const int64_t t1 = min((int64_t)(q + 1) * kQ, nd);
-  for (int64_t t = (int64_t)q * kQ + lane; t < t1; t += 32) m = absmax(m, x[t]);
-  m = warp_max(m);
-  if (lane == 0) esc[(int64_t)q * NP + col] = chunk_exponent((double)m);
+  if constexpr (std::is_same<T, double>::value) {
+    long long m = 0;
+    for (int64_t t = (int64_t)q * kQ + lane; t < t1; t += 32) m = max(m, mag_key(x[t]));
+    m = warp_max(m);
+    if (lane == 0) esc[(int64_t)q * NP + col] = chunk_exponent_key(m);
+  } else {
+    T m = 0;
+    for (int64_t t = (int64_t)q * kQ + lane; t < t1; t += 32) m = absmax(m, x[t]);
+    m = warp_max(m);
+    if (lane == 0) esc[(int64_t)q * NP + col] = chunk_exponent((double)m);
+  }
 }
 
 // Column exponents f_k of X (one block per column), used to balance columns.
 template <typename T>
 __global__ void k_col_exponent(const T* __restrict__ X, int64_t ldx, int64_t nd,
                                int* __restrict__ esc) {
-  __shared__ T sm[32];
+  // magnitudes compared as integer keys (order-preserving for both types)
+  __shared__ long long sm[32];
   const T* x = X + (int64_t)blockIdx.x * ldx;
-  T m = 0;
-  for (int64_t t = threadIdx.x; t < nd; t += blockDim.x) m = absmax(m, x[t]);
+  long long m = 0;
+  for (int64_t t = threadIdx.x; t < nd; t += blockDim.x) {
+    if constexpr (std::is_same<T, double>::value) m = max(m, mag_key(x[t]));
+    else m = max(m, (long long)(__float_as_uint(x[t]) & 0x7FFFFFFFu));
+  }
   m = warp_max(m);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    T r = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = absmax(r, sm[w]);
-    esc[blockIdx.x] = row_exponent((double)r);
+    long long r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, sm[w]);
+    if constexpr (std::is_same<T, double>::value) esc[blockIdx.x] = key_exponent(r);
+    else esc[blockIdx.x] = row_exponent((double)__uint_as_float((unsigned)r));
   }
 }
 
@@ -573,10 +623,16 @@ __global__ void k_chunk_exp_rows(const T* __restrict__ X, int64_t ldx, int64_t n
   const int k1 = min((q + 1) * kQ, ns);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nd;
        t += (int64_t)gridDim.x * blockDim.x) {
-    double m = 0.0;
-    for (int k = q * kQ; k < k1; ++k)
-      m = fmax(m, ldexp(fabs((double)X[t + (int64_t)k * ldx]), -fcol[k]));
-    esc[(int64_t)q * MP + t] = chunk_exponent(m);
+    if constexpr (std::is_same<T, double>::value) {
+      long long m = 0;
+      for (int k = q * kQ; k < k1; ++k) m = max(m, mag_key(X[t + (int64_t)k * ldx], fcol[k]));
+      esc[(int64_t)q * MP + t] = chunk_exponent_key(m);
+    } else {
+      float m = 0.f;
+      for (int k = q * kQ; k < k1; ++k)
+        m = fmaxf(m, ldexpf(fabsf(X[t + (int64_t)k * ldx]), -fcol[k]));
+      esc[(int64_t)q * MP + t] = chunk_exponent((double)m);
+    }
   }
 }
 
@@ -588,12 +644,12 @@ __global__ void k_chunk_exp_z(const double* __restrict__ Z, int n, const int* __
   const int lane = threadIdx.x & 31;
   if (w >= (int64_t)n * nq) return;
   const int j = (int)(w % n), q = (int)(w / n);
-  double m = 0.0;
+  long long m = 0;
   const int k1 = min((q + 1) * kQ, n);
   for (int k = q * kQ + lane; k < k1; k += 32)
-    m = fmax(m, ldexp(fabs(Z[k + (int64_t)j * n]), fcol[k]));
+    m = max(m, mag_key(Z[k + (int64_t)j * n], -fcol[k]));
   m = warp_max(m);
-  if (lane == 0) esc[(int64_t)q * NP + j] = chunk_exponent(m);
+  if (lane == 0) esc[(int64_t)q * NP + j] = chunk_exponent_key(m);
 }
 
 // S[s][col][t] = digit s of X[t + col ldx] at its chunk's exponent (ld = lds)
@@ -620,14 +676,14 @@ template <typename T, int D>
 __global__ void k_slice_transpose(const T* __restrict__ X, int64_t ldx, int64_t nd, int ns,
                                   const int* __restrict__ fcol, const int8_t* __restrict__ esc,
                                   int MP, __nv_bfloat16* __restrict__ S, int64_t ldk) {
+  // digits of x 2^-f at exponent E are the digits of x at exponent E + f
   __shared__ T tile[32][33];
   const int64_t t0 = (int64_t)blockIdx.x * 32;
   const int k0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int k = k0 + r;
     const int64_t t = t0 + threadIdx.x;
-    tile[r][threadIdx.x] =
-        (k < ns && t < nd) ? (T)ldexp((double)X[t + (int64_t)k * ldx], -fcol[k]) : T(0);
+    tile[r][threadIdx.x] = (k < ns && t < nd) ? X[t + (int64_t)k * ldx] : T(0);
   }
   __syncthreads();
   const int64_t plane = ldk * nd;
@@ -636,7 +692,8 @@ __global__ void k_slice_transpose(const T* __restrict__ X, int64_t ldx, int64_t 
     const int k = k0 + threadIdx.x;
     if (t < nd && k < ldk) {
       __nv_bfloat16 d[D];
-      digits<D>(tile[threadIdx.x][r], esc[(int64_t)(k / kQ) * MP + t], d);
+      const int f = k < ns ? fcol[k] : 0;
+      digits<D>(tile[threadIdx.x][r], (int)esc[(int64_t)(k / kQ) * MP + t] + f, d);
       const int64_t o = t * ldk + k;
 #pragma unroll
       for (int q = 0; q < D; ++q) S[q * plane + o] = d[q];
@@ -656,8 +713,9 @@ __global__ void k_slice_z(const double* __restrict__ Z, int n, const int* __rest
        e += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / ldk), k = (int)(e % ldk);
     __nv_bfloat16 d[D];
-    digits<D>(k < n ? ldexp(Z[k + (int64_t)j * n], fcol[k]) : 0.0,
-              esc[(int64_t)(k / kQ) * NP + j], d);
+    // digits of z 2^f at exponent E are the digits of z at exponent E - f
+    digits<D>(k < n ? Z[k + (int64_t)j * n] : 0.0,
+              (int)esc[(int64_t)(k / kQ) * NP + j] - (k < n ? fcol[k] : 0), d);
 #pragma unroll
     for (int q = 0; q < D; ++q) S[q * plane + e] = d[q];
   }
