@@ -432,18 +432,35 @@ __device__ int sturm(const double* __restrict__ d, const double* __restrict__ e2
   return cnt;
 }
 
+// Eigenvalue j of the tridiagonal matrix by multisection: the 8 lanes of a
+// group evaluate Sturm counts at 8 interior points of [lo, hi] at once, and the
+// interval shrinks 9-fold per round (bisection's 2-fold per count, with 8 times
+// the parallelism for the latency-bound count recurrence).  Stops at the same
+// relative width as plain bisection: 2 eps max(|lo|, |hi|).
+constexpr int kMsLanes = 8;
 __global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e2, int n,
                          const double* __restrict__ scal, double* __restrict__ lam) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  double lo = scal[0], hi = scal[1], pivmin = scal[2];
-  for (int it = 0; it < 256; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (!(mid > lo && mid < hi)) break;
+  const int g = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kMsLanes);
+  const int l = threadIdx.x % kMsLanes;
+  const unsigned gmask = 0xFFu << ((threadIdx.x & 31) & ~(kMsLanes - 1));
+  const int j = min(g, n - 1);  // surplus groups repeat the last eigenvalue, unwritten
+  double lo = scal[0], hi = scal[1];
+  const double pivmin = scal[2];
+  for (int it = 0; it < 64; ++it) {
     if (hi - lo <= 2.0 * 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
-    if (sturm(d, e2, n, mid, pivmin) > j) hi = mid; else lo = mid;
+    const double step = (hi - lo) / (kMsLanes + 1);
+    const double x = lo + (l + 1) * step;
+    const bool above = sturm(d, e2, n, x, pivmin) > j;  // lam_j < x
+    const unsigned b = __ballot_sync(gmask, above) & gmask;
+    // the first lane whose point lies above lam_j bounds it from above
+    const int first = b ? __ffs(b) - 1 - ((threadIdx.x & 31) & ~(kMsLanes - 1)) : kMsLanes;
+    const double nlo = first == 0 ? lo : lo + first * step;
+    const double nhi = first == kMsLanes ? hi : lo + (first + 1) * step;
+    if (!(nlo >= lo && nhi <= hi && nlo < nhi)) break;  // no progress left in FP64
+    lo = nlo;
+    hi = nhi;
   }
-  lam[j] = 0.5 * (lo + hi);
+  if (g < n && l == 0) lam[j] = 0.5 * (lo + hi);
 }
 
 // Cluster bookkeeping: clus[j] = first index of j's cluster, clus[n + j] = its size.
@@ -793,7 +810,7 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
   // 4. eigenvalues of T (ascending)
   double* e2 = w.tau + n;
   note_launch(), k_gersh<<<1, 1024, 0, st>>>(w.d, w.e, n, e2, w.scal);
-  note_launch(), k_bisect<<<(n + 31) / 32, 32, 0, st>>>(w.d, e2, n, w.scal, lam);
+  note_launch(), k_bisect<<<(n * kMsLanes + 127) / 128, 128, 0, st>>>(w.d, e2, n, w.scal, lam);
   // 5. eigenvectors of T into W (column-major); factors in lu (4 n x n)
   note_launch(), k_clusters<<<1, 32, 0, st>>>(lam, n, w.scal, w.clus);
   double* VT = w.W;

@@ -3,8 +3,7 @@
 // every sum and product carried as an unevaluated pair hi + lo of FP32 numbers
 // (48-bit significand) on the FP32 pipe.  GB300 runs FP64 at 1/64 of the FP32
 // rate, so the FP64 stencil (≈ 42 FP64 instructions per point) is bound by its
-// FP64 pipe; in pair arithmetic the same point costs ≈ 550 FP32 instructions,
-// about 1/5 of the time.  Errors: each pair operation is accurate to ≈ 2^-48
+// FP64 pipe; in pair arithmetic the same point costs ≈ 400 FP32 instructions.  Errors: each pair operation is accurate to ≈ 2^-48
 // of its operands, so H x agrees with FP64 arithmetic to ≈ 1e-13 relative
 // (FP64's own rounding, amplified by the stencil's cancellation, is ≈ 3e-14).
 //
@@ -58,6 +57,31 @@ __device__ __forceinline__ df mul(df a, df b) {
   return fast_two_sum(p, e);
 }
 __device__ __forceinline__ df fma(df a, df b, df c) { return add(mul(a, b), c); }
+
+// Unnormalised accumulator: the high parts are summed error-free (TwoSum), the
+// low parts and the rounding errors in a plain FP32 word, which is 2^-24 below
+// and needs no more than FP32 accuracy.  Equivalent in accuracy to a chain of
+// pair additions at about 2/3 of the cost.
+struct acc_t {
+  float h, l;
+};
+__device__ __forceinline__ void acc_add(acc_t& a, df v) {
+  const df s = two_sum(a.h, v.h);
+  a.h = s.h;
+  a.l = __fadd_rn(a.l, __fadd_rn(s.l, v.l));
+}
+// a += w * v (w, v pairs): the product's high part exactly (FMA), its cross
+// terms into the low word
+__device__ __forceinline__ void acc_fma(acc_t& a, df w, acc_t v) {
+  const float p = __fmul_rn(w.h, v.h);
+  float e = __fmaf_rn(w.h, v.h, -p);
+  e = __fmaf_rn(w.h, v.l, e);
+  e = __fmaf_rn(w.l, v.h, e);
+  const df s = two_sum(a.h, p);
+  a.h = s.h;
+  a.l = __fadd_rn(a.l, __fadd_rn(s.l, e));
+}
+__device__ __forceinline__ df normalise(acc_t a) { return fast_two_sum(a.h, a.l); }
 
 // 2^n as a float for -126 <= n <= 127
 __device__ __forceinline__ float pow2f(int n) { return __int_as_float((n + 127) << 23); }
@@ -283,7 +307,57 @@ __global__ void __launch_bounds__(384, 1)
 
   for (int z = z0; ok && z < z1; ++z) {
     const int64_t g0 = z * nxy + (int64_t)gy0 * a.nx + x;
-    // Veff, prev and the nonlocal slot range of this plane
+    // plane z + R: wait, convert, push into the queue
+    if (!arrive_convert(z + R)) break;
+    {
+      const df* row = slot_ptr(slot_of(z + R));
+#pragma unroll
+      for (int r = 0; r < VY; ++r) lds2(q[2 * R][r], row + (R + yy + r) * rowe + x);
+    }
+    const df* pl = slot_ptr(slot_of(z));
+    acc_t acc[VY][VX];
+#pragma unroll
+    for (int r = 0; r < VY; ++r)
+#pragma unroll
+      for (int v = 0; v < VX; ++v) {
+        const df c = mul(a.diag_minus_shift, q[R][r][v]);
+        acc[r][v] = {c.h, c.l};
+      }
+    // per row and distance: y and z neighbours from the slot and the queue,
+    // x neighbours read singly (periodic wrap or zero ghosts)
+#pragma unroll
+    for (int r = 0; r < VY; ++r) {
+      const df* rowp = pl + (R + yy + r) * rowe;
+#pragma unroll
+      for (int p = 1; p <= R; ++p) {
+        df up[VX], dn[VX];
+        lds2(up, pl + (R + yy + r + p) * rowe + x);
+        lds2(dn, pl + (R + yy + r - p) * rowe + x);
+#pragma unroll
+        for (int v = 0; v < VX; ++v) {
+          int xl = x + v - p, xr = x + v + p;
+          bool il = true, ir = true;
+          if (xl < 0) {
+            if (a.bcx == SPARC_DIRICHLET) il = false;
+            else xl += a.nx;
+          }
+          if (xr >= a.nx) {
+            if (a.bcx == SPARC_DIRICHLET) ir = false;
+            else xr -= a.nx;
+          }
+          acc_t sm = {up[v].h, up[v].l};
+          acc_add(sm, dn[v]);
+          acc_add(sm, q[R + p][r][v]);
+          acc_add(sm, q[R - p][r][v]);
+          acc_add(sm, il ? rowp[xl] : df{0.f, 0.f});
+          acc_add(sm, ir ? rowp[xr] : df{0.f, 0.f});
+          acc_fma(acc[r][v], a.off[p], sm);
+        }
+      }
+    }
+    release(z);
+    // Veff, prev and the nonlocal slot range of this plane (loaded after the
+    // stencil sums: the registers go to the queue and the neighbour sums)
     float4 vf4[VY];
     double2 pv2[VY];
     int gs[VY], ge[VY];
@@ -300,52 +374,6 @@ __global__ void __launch_bounds__(384, 1)
         }
       }
     }
-    // plane z + R: wait, convert, push into the queue
-    if (!arrive_convert(z + R)) break;
-    {
-      const df* row = slot_ptr(slot_of(z + R));
-#pragma unroll
-      for (int r = 0; r < VY; ++r) lds2(q[2 * R][r], row + (R + yy + r) * rowe + x);
-    }
-    const df* pl = slot_ptr(slot_of(z));
-    df acc[VY][VX];
-#pragma unroll
-    for (int r = 0; r < VY; ++r)
-#pragma unroll
-      for (int v = 0; v < VX; ++v) acc[r][v] = mul(a.diag_minus_shift, q[R][r][v]);
-#pragma unroll
-    for (int p = 1; p <= R; ++p) {
-#pragma unroll
-      for (int r = 0; r < VY; ++r) {
-        df up[VX], dn[VX], lf[VX], rt[VX];
-        lds2(up, pl + (R + yy + r + p) * rowe + x);
-        lds2(dn, pl + (R + yy + r - p) * rowe + x);
-        // x neighbours (periodic wrap or zero ghosts)
-        const df* rowp = pl + (R + yy + r) * rowe;
-#pragma unroll
-        for (int v = 0; v < VX; ++v) {
-          int xl = x + v - p, xr = x + v + p;
-          bool il = true, ir = true;
-          if (xl < 0) {
-            if (a.bcx == SPARC_DIRICHLET) il = false;
-            else xl += a.nx;
-          }
-          if (xr >= a.nx) {
-            if (a.bcx == SPARC_DIRICHLET) ir = false;
-            else xr -= a.nx;
-          }
-          lf[v] = il ? rowp[xl] : df{0.f, 0.f};
-          rt[v] = ir ? rowp[xr] : df{0.f, 0.f};
-        }
-#pragma unroll
-        for (int v = 0; v < VX; ++v) {
-          df sm = add(add(up[v], dn[v]), add(q[R + p][r][v], q[R - p][r][v]));
-          sm = add(sm, add(lf[v], rt[v]));
-          acc[r][v] = fma(a.off[p], sm, acc[r][v]);
-        }
-      }
-    }
-    release(z);
     // Veff, nonlocal pull-add, recurrence, store as FP64
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
@@ -353,7 +381,7 @@ __global__ void __launch_bounds__(384, 1)
       df h[VX];
       const df vf[VX] = {{vf4[r].x, vf4[r].y}, {vf4[r].z, vf4[r].w}};
 #pragma unroll
-      for (int v = 0; v < VX; ++v) h[v] = fma(vf[v], q[R][r][v], acc[r][v]);
+      for (int v = 0; v < VX; ++v) h[v] = fma(vf[v], q[R][r][v], normalise(acc[r][v]));
       for (int sl = gs[r]; sl < ge[r]; ++sl) {
         const int2 kk = __ldg(reinterpret_cast<const int2*>(a.grp_k + (int64_t)sl * VX));
         const float4 c4 = __ldg(reinterpret_cast<const float4*>(a.grp_chi + (int64_t)sl * VX));
