@@ -31,6 +31,12 @@ METRIC = "CheFSI step time & Hpsi GB/s; mixed-FP32/batched vs FP64 speedup at <=
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 pipe of GB300: 2 FP64 FMA per SM per clock (4 FLOP), 152 SMs, 2070 MHz max.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+# DRAM bytes (read + write) per orbital of one stencil launch of a filter degree
+# on the 96^3 bulk grid, and the FP64-pipe activity, from the ncu captures
+# summarised in profiles/k_apply_h_ring_*_bulk96.md (scaled by orbital count)
+RING64_DRAM_BYTES_PER_ORBITAL = None
+RING64_FP64_PIPE_ACTIVE = None
+RING32_DRAM_BYTES_PER_ORBITAL = None
 
 
 def parse():
@@ -45,6 +51,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-systems", type=int, default=64)
+    p.add_argument("--variants", default="all",
+                   help="comma-separated forms to compare with the headline FP64 path, or all")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--ns", type=int, default=0, help="override Ns (profiling on a smaller case)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
@@ -328,20 +336,33 @@ def main():
     # dominant kernel roofline (FP64 path: the FP64 pipe is the binding roof)
     dom = max(("filter", "project", "rotate"), key=lambda k: stage_rate[k]["ms"])
     pk = peaks()
-    if dom == "filter":
-        # K1 per degree: 48 FP64 flops per point per orbital (symmetric pair sums)
-        flops = 48.0 * nd * ns * m
-        ach = flops / (st_ms["filter_ms"] / 1e3) / 1e12
-        roof = {"kernel": "k_apply_h<double> (fused stencil+Veff+nonlocal+recurrence)",
-                "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    if dom == "filter" and prec == "fp64":
+        # one filter degree = k_nl_coef + k_apply_h_ring<double,2>: 48 FP64 flops
+        # per point-orbital (36 neighbours as pair sums, 7 weights, Veff,
+        # recurrence); FP64 arithmetic, so the FP64 pipe is the roof
+        ach = 48.0 * nd * ns * m / (st_ms["filter_ms"] / 1e3) / 1e12
+        roof = {"kernel": "filter degree: k_nl_coef<double> + k_apply_h_ring<double,2>",
+                "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 4 FP64 FLOP/clk x 2.07 GHz (FP64 pipe)",
+                "algorithmic_bytes": 24 * nd * ns,
+                "traffic": RING64_DRAM_BYTES_PER_ORBITAL * ns if RING64_DRAM_BYTES_PER_ORBITAL
+                else None,
+                "fp64_pipe_active_ncu": RING64_FP64_PIPE_ACTIVE}
+    elif dom == "filter":
+        ach = filt_gbs
+        roof = {"kernel": "filter degree: k_nl_coef<float> + k_apply_h_ring<float,4>",
+                "bound": "hbm", "achieved": ach, "peak": pk.get("hbm_gbs", 6674.5),
+                "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "algorithmic_bytes": 12 * nd * ns,
+                "traffic": RING32_DRAM_BYTES_PER_ORBITAL * ns if RING32_DRAM_BYTES_PER_ORBITAL
+                else None}
     else:
         ms_ = st_ms[dom + "_ms"]
         ach = (proj_flops if dom == "project" else rot_flops) / (ms_ / 1e3) / 1e12
-        roof = {"kernel": "k_project_partial<double>" if dom == "project" else "k_rotate<double>",
-                "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+        roof = {"kernel": "k_tc_gemm (" + dom + ")", "bound": "tensor", "achieved": ach,
+                "peak": pk.get("bf16_tflops", 1908.3), "unit": "TFLOP/s (useful)",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)", "traffic": None}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["peak_source"] = "derived: 152 SMs x 4 FP64 FLOP/clk x 2.07 GHz (FP64 pipe)"
-    roof["traffic"] = None
     roof["hbm_frac_filter"] = filt_gbs / pk.get("hbm_gbs", 6674.5)
 
     clocks = clk.summary()
@@ -367,14 +388,17 @@ def main():
         he.close()
         del Xh, Xn
 
-    # ---- mixed precision on the same system ---------------------------------
-    mixed = None
+    # ---- other forms on the same system (mixed precision first) --------------
+    variants = None
     if not args.no_mixed and prec == "fp64":
         try:
-            mixed = run_mixed(system, X0, ns, m, args, dev, stream, h)
+            variants = run_variants(system, X0, ns, m, args, dev, stream, h)
         except Exception as exc:  # report, do not hide
-            mixed = {"error": repr(exc)}
+            variants = {"error": repr(exc)}
     h.close()
+    mixed = variants.get("mixed") if isinstance(variants, dict) else None
+    if isinstance(mixed, dict) and "ms_per_step" in mixed:
+        mixed["speedup_vs_fp64"] = (t_max / args.steps * 1e3) / mixed["ms_per_step"]
 
     batched = None
     if not args.no_batch and world == 1 and args.batch_systems > 0:
@@ -408,6 +432,7 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
         "mixed": mixed,
+        "variants": {k: v for k, v in variants.items() if k != "mixed"} if isinstance(variants, dict) else variants,
         "batched": batched,
         "cpu_baseline": cpu,
         "setup_s": setup_s,
@@ -420,54 +445,87 @@ def main():
     return 0
 
 
-def run_mixed(system, X0, ns, m, args, dev, stream, h64):
-    """Mixed precision (FP32 orbitals and filtering) on the same system: time
-    per step and Ritz-value error against the FP64 GPU path (itself checked
-    against the oracle by the test suite) from the same start and bounds."""
+def fermi_occupied(lam, ne, kT=0.01):
+    """States with Fermi-Dirac occupation above 1e-6 at the electron count ne
+    (mu by bisection), the set on which the mixed-precision target is read."""
+    import numpy as np
+    lo, hi = float(lam.min()) - 1.0, float(lam.max()) + 1.0
+    for _ in range(200):
+        mu = 0.5 * (lo + hi)
+        c = 2.0 * np.sum(1.0 / (1.0 + np.exp(np.clip((lam - mu) / kT, -700, 700))))
+        lo, hi = (mu, hi) if c < ne else (lo, mu)
+    f = 1.0 / (1.0 + np.exp(np.clip((lam - mu) / kT, -700, 700)))
+    return f > 1e-6
+
+
+VARIANTS = (
+    ("mixed", "mixed", 0,
+     "FP32 orbitals and filtering, FP64 Yt (double-FP32 stencil), four-digit tensor-core GEMMs"),
+    ("fp64_double_fp32_stencil", "fp64", 4,
+     "FP64 blocks, H x in double-FP32 arithmetic (options bit 2), six-digit tensor-core GEMMs"),
+    ("fp64_simt_gemm", "fp64", 2,
+     "FP64 blocks, FP64 arithmetic throughout: FP64 stencil and FP64 SIMT GEMMs (options bit 1)"),
+)
+
+
+def run_variants(system, X0, ns, m, args, dev, stream, h64):
+    """Other forms of the step on the same system: Ritz values against the
+    headline FP64 path from the same start and bounds (3 steps), then the time
+    per step.  The headline path is checked against the oracle by the tests."""
     import numpy as np
     import torch
 
-    from paper_2302_09708_gb300 import sparc
+    from paper_2302_09708_gb300 import sparc, synth
 
     a0, b = h64.spectrum_bounds(32, 0)
-    hm = sparc.Handle(system, "mixed", ns_max=ns, device=dev.index)
-    X32 = torch.from_numpy(X0).to(dev, torch.float32)
-    X64 = torch.from_numpy(X0).to(dev)
     nsteps = 3
+    X64 = torch.from_numpy(X0).to(dev)
     a = a0 + 0.1 * (b - a0)
-    errs = []
-    lam64 = lam32 = None
-    for s in range(nsteps):
-        lam64 = h64.chefsi_step(X64, m, bounds=(a, b, a0))
-        lam32 = hm.chefsi_step(X32, m, bounds=(a, b, a0))
-        errs.append(float(np.max(np.abs(lam64 - lam32))))
-        a = float(lam64[-1])
-    # occupied-state error (Ne = 2 round((Ns - 5)/1.2), Fermi-Dirac kT = 0.01 Ha)
-    from paper_2302_09708_gb300 import synth
-    ne = synth.electrons_for(ns)
-    occ = np.arange(ns) < ne // 2 + 8
-    err_occ = float(np.max(np.abs(lam64 - lam32)[occ]))
-    # timing
-    for _ in range(max(0, args.warmup - nsteps)):
-        hm.chefsi_step(X32, m)
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    stage = []
-    for _ in range(args.steps):
-        hm.chefsi_step(X32, m)
-        stage.append(hm.timings())
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    t = e0.elapsed_time(e1) / 1e3 / args.steps
-    st = {k: statistics.median(x[k] for x in stage) for k in stage[0] if k != "launches"}
-    filt_bytes = (2 + 3 * (m - 1)) * system.nd * ns * 4
-    hm.close()
-    return {"ms_per_step": t * 1e3, "stage_ms": st,
-            "filter_GBps": filt_bytes / (st["filter_ms"] / 1e3) / 1e9,
-            "ritz_err_vs_fp64_gpu_per_step": errs, "ritz_err_occupied": err_occ,
-            "note": "errors vs the FP64 GPU path from the same start and bounds"}
+    ref, cut = [], []
+    for _ in range(nsteps):
+        cut.append(a)
+        lam = h64.chefsi_step(X64, m, bounds=(a, b, a0))
+        ref.append(lam)
+        a = float(lam[-1])
+    del X64
+    torch.cuda.empty_cache()
+    occ = fermi_occupied(ref[-1], synth.electrons_for(ns))
+    out = {"note": "Ritz-value differences vs the headline FP64 GPU path from the same start "
+                   "and bounds; occupied = Fermi-Dirac f > 1e-6 at kT = 0.01 Ha"}
+    for key, prec, flags, what in VARIANTS:
+        if args.variants != "all" and key not in args.variants.split(","):
+            continue
+        try:
+            hv = sparc.Handle(system, prec, ns_max=ns, device=dev.index, options_flags=flags)
+            Xv = torch.from_numpy(X0).to(dev, torch.float32 if prec == "mixed" else torch.float64)
+            errs = []
+            for s_ in range(nsteps):
+                lam = hv.chefsi_step(Xv, m, bounds=(cut[s_], b, a0))
+                errs.append(float(np.max(np.abs(lam - ref[s_]))))
+            err_occ = float(np.max(np.abs(lam - ref[-1])[occ]))
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stage = []
+            for _ in range(args.steps):
+                hv.chefsi_step(Xv, m)
+                stage.append(hv.timings())
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t = e0.elapsed_time(e1) / 1e3 / args.steps
+            st = {k: statistics.median(x[k] for x in stage) for k in stage[0] if k != "launches"}
+            es = 4 if prec == "mixed" else 8
+            filt_bytes = (2 + 3 * (m - 1)) * system.nd * ns * es
+            out[key] = {"what": what, "ms_per_step": t * 1e3, "stage_ms": st,
+                        "filter_GBps": filt_bytes / (st["filter_ms"] / 1e3) / 1e9,
+                        "ritz_err_vs_fp64_gpu_per_step": errs, "ritz_err_occupied": err_occ}
+            hv.close()
+            del Xv
+            torch.cuda.empty_cache()
+        except Exception as exc:  # report, do not hide
+            out[key] = {"error": repr(exc)}
+    return out
 
 
 def run_batched(args, dev, stream):

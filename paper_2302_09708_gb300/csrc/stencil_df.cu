@@ -382,11 +382,25 @@ __global__ void __launch_bounds__(384, 1)
       const df vf[VX] = {{vf4[r].x, vf4[r].y}, {vf4[r].z, vf4[r].w}};
 #pragma unroll
       for (int v = 0; v < VX; ++v) h[v] = fma(vf[v], q[R][r][v], normalise(acc[r][v]));
-      for (int sl = gs[r]; sl < ge[r]; ++sl) {
-        const int2 kk = __ldg(reinterpret_cast<const int2*>(a.grp_k + (int64_t)sl * VX));
-        const float4 c4 = __ldg(reinterpret_cast<const float4*>(a.grp_chi + (int64_t)sl * VX));
-        h[0] = fma(df{c4.x, c4.y}, dsh[kk.x], h[0]);
-        h[1] = fma(df{c4.z, c4.w}, dsh[kk.y], h[1]);
+      // up to four slots' loads in flight before their products
+      for (int sl = gs[r]; sl < ge[r]; sl += 4) {
+        int2 kk[4];
+        float4 c4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (sl + u < ge[r]) {
+            kk[u] = __ldg(reinterpret_cast<const int2*>(a.grp_k + (int64_t)(sl + u) * VX));
+            c4[u] = __ldg(reinterpret_cast<const float4*>(a.grp_chi + (int64_t)(sl + u) * VX));
+          } else {
+            kk[u] = make_int2(0, 0);
+            c4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          h[0] = fma(df{c4[u].x, c4[u].y}, dsh[kk[u].x], h[0]);
+          h[1] = fma(df{c4[u].z, c4[u].w}, dsh[kk[u].y], h[1]);
+        }
       }
       double out[VX];
 #pragma unroll

@@ -349,13 +349,28 @@ __global__ void __launch_bounds__(384, 1)
       T h[VX];
 #pragma unroll
       for (int v = 0; v < VX; ++v) h[v] = acc[r][v] + vf[r][v] * q[R][r][v];
-      for (int sl = gs[r]; sl < ge[r]; ++sl) {
-        int kk[VX];
-        T ch[VX];
-        ldg_idx<VX>(kk, a.grp_k + (int64_t)sl * VX);
-        ldg<T, VX>(ch, a.grp_chi + (int64_t)sl * VX);
+      // up to four slots' loads in flight before their FMAs (the loads are L2
+      // round trips; one at a time they would serialise)
+      for (int sl = gs[r]; sl < ge[r]; sl += 4) {
+        int kk[4][VX];
+        T ch[4][VX];
 #pragma unroll
-        for (int v = 0; v < VX; ++v) h[v] += ch[v] * dsh[kk[v]];
+        for (int u = 0; u < 4; ++u) {
+          if (sl + u < ge[r]) {
+            ldg_idx<VX>(kk[u], a.grp_k + (int64_t)(sl + u) * VX);
+            ldg<T, VX>(ch[u], a.grp_chi + (int64_t)(sl + u) * VX);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+              kk[u][v] = 0;
+              ch[u][v] = T(0);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < VX; ++v) h[v] += ch[u][v] * dsh[kk[u][v]];
       }
       T out[VX];
 #pragma unroll

@@ -26,7 +26,10 @@
 // 1e-30 in magnitude lose relative accuracy (FP64 orbital entries that small
 // carry no weight in a normalised block).
 //
-// Kernel structure (one CTA per 128 x 64 output tile, 320 threads):
+// Kernel structure: persistent, one CTA of 320 threads per SM walks the work
+// items (128 x 64 output tile, K split, output) with a grid stride; the
+// pipeline counters run on across items, so one tile's TMA loads overlap the
+// previous tile's epilogue:
 //   warp 0     TMA producer: one 3-D TMA load per operand per K-step brings the
 //              D BF16 digit tiles (swizzled) into a shared-memory ring
 //              (full/empty mbarriers);
@@ -220,6 +223,8 @@ struct TcArgs {
   int64_t kchunk;   // K per split (multiple of kQ)
   int upper;        // 1: enumerate only tiles with bi <= bj (symmetric outputs)
   int tiles_m, tiles_n;
+  int nout;         // outputs per tile (2 for the projection: Hs and Ms)
+  int ntiles_upper; // upper-triangle tiles (symmetric outputs)
   double* work;     // mode 0: work[(split * 2 + out) * M * N + m + n * M]
   float* out32;     // mode 1: out32[m + n * ldo]
   double* out64;    // mode 2: out64[m + n * ldo]
@@ -252,23 +257,45 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t acce0 = smem_u32(&bars[2 * kStages + kBufs]);  // kBufs barriers
   const uint32_t drain = smem_u32(&bars[2 * kStages + 2 * kBufs]);
 
-  int bi, bj;
-  if (a.upper) {
-    bi = blockIdx.x % a.tiles_m;
-    bj = blockIdx.x / a.tiles_m;
-    // symmetric outputs: only tiles that reach the upper triangle (i <= j)
-    if (bi * kBM > bj * kBN + kBN - 1) return;
-  } else {
-    // the column tiles of one row block run together and share its A digits in L2
-    bj = blockIdx.x % a.tiles_n;
-    bi = blockIdx.x / a.tiles_n;
-  }
-  const int out = blockIdx.z;
-  const CUtensorMap* tB = out == 0 ? &tB0 : &tB1;
-  const int64_t k0 = (int64_t)blockIdx.y * a.kchunk;
-  const int64_t k1 = min(a.K, k0 + a.kchunk);
-  const int nk = k1 > k0 ? (int)((k1 - k0 + kBK - 1) / kBK) : 0;
-  const int nchunks = (nk + P::kSteps - 1) / P::kSteps;
+  // Work items (persistent CTAs walk them with a grid stride): item w is
+  // (tile, split, output) with the tile fastest, so the CTAs running together
+  // share a split's K range (projection) or a row block's A digits (rotation)
+  // in L2.  Every role decodes the same sequence; stage and accumulator
+  // counters run on across items.
+  // symmetric outputs list only the tiles that reach the upper triangle
+  // (bi * 128 <= bj * 64 + 63): column bj holds bj / 2 + 1 of them
+  const int ntiles = a.upper ? a.ntiles_upper : a.tiles_m * a.tiles_n;
+  const int nsplit = (int)((a.K + a.kchunk - 1) / a.kchunk);
+  const int nitems = ntiles * nsplit * a.nout;
+  struct Item {
+    int bi, bj, out;
+    int64_t k0;
+    int nk;
+    bool skip;
+  };
+  auto decode = [&](int w) {
+    Item it;
+    const int tile = w % ntiles, rest = w / ntiles;
+    it.out = rest % a.nout;
+    const int split = rest / a.nout;
+    if (a.upper) {
+      int t = tile, bj = 0;
+      while (bj + 1 < a.tiles_n && t >= min(a.tiles_m, (bj * kBN + kBN - 1) / kBM + 1)) {
+        t -= min(a.tiles_m, (bj * kBN + kBN - 1) / kBM + 1);
+        ++bj;
+      }
+      it.bi = t;
+      it.bj = bj;
+    } else {
+      it.bj = tile % a.tiles_n;
+      it.bi = tile / a.tiles_n;
+    }
+    it.skip = false;
+    it.k0 = (int64_t)split * a.kchunk;
+    const int64_t k1 = min(a.K, it.k0 + a.kchunk);
+    it.nk = k1 > it.k0 ? (int)((k1 - it.k0 + kBK - 1) / kBK) : 0;
+    return it;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -299,21 +326,28 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      int issued = 0;
-      for (int it = 0; it < nk; ++it) {
-        const int s = it % kStages;
-        const uint32_t round = (uint32_t)(it / kStages);
-        if (!mbar_wait(empty0 + 8 * s, (round & 1) ^ 1, abort, a.status)) break;
-        const uint32_t sa = base + s * P::kStageBytes;
-        mbar_expect_tx(full0 + 8 * s, P::kStageBytes);
-        const int kx = (int)(k0 + (int64_t)it * kBK);
-        tma_load_3d(sa, &tA, kx, bi * kBM, 0, full0 + 8 * s);
-        tma_load_3d(sa + P::kOpA, tB, kx, bj * kBN, 0, full0 + 8 * s);
-        issued = it + 1;
+      int g = 0;  // stages issued so far (all items)
+      bool ok = true;
+      for (int w = blockIdx.x; ok && w < nitems; w += gridDim.x) {
+        const Item itm = decode(w);
+        const CUtensorMap* tB = itm.out == 0 ? &tB0 : &tB1;
+        for (int it = 0; it < itm.nk; ++it, ++g) {
+          const int s = g % kStages;
+          const uint32_t round = (uint32_t)(g / kStages);
+          if (!mbar_wait(empty0 + 8 * s, (round & 1) ^ 1, abort, a.status)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sa = base + s * P::kStageBytes;
+          mbar_expect_tx(full0 + 8 * s, P::kStageBytes);
+          const int kx = (int)(itm.k0 + (int64_t)it * kBK);
+          tma_load_3d(sa, &tA, kx, itm.bi * kBM, 0, full0 + 8 * s);
+          tma_load_3d(sa + P::kOpA, tB, kx, itm.bj * kBN, 0, full0 + 8 * s);
+        }
       }
       if (*abort) {
         // drain: the loads already issued must land before the CTA exits
-        for (int it = max(0, issued - kStages); it < issued; ++it) {
+        for (int it = max(0, g - kStages); it < g; ++it) {
           const long long t0 = clock64();
           while (!mbar_test(full0 + 8 * (it % kStages), (uint32_t)(it / kStages) & 1) &&
                  clock64() - t0 < kWaitCycles) {
@@ -324,36 +358,51 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      for (int it = 0; it < nk; ++it) {
-        const int s = it % kStages;
-        const uint32_t round = (uint32_t)(it / kStages);
-        const int chunk = it / P::kSteps, in_chunk = it % P::kSteps;
-        const int buf = chunk % kBufs;
-        const uint32_t use = (uint32_t)(chunk / kBufs);
-        if (in_chunk == 0) {
-          if (!mbar_wait(acce0 + 8 * buf, (use & 1) ^ 1, abort, a.status)) break;
+      int g = 0;   // stages consumed so far
+      int gc = 0;  // accumulator chunks started so far
+      bool ok = true;
+      for (int w = blockIdx.x; ok && w < nitems; w += gridDim.x) {
+        const Item itm = decode(w);
+        for (int it = 0; it < itm.nk; ++it, ++g) {
+          const int s = g % kStages;
+          const uint32_t round = (uint32_t)(g / kStages);
+          const int in_chunk = it % P::kSteps;
+          const int buf = gc % kBufs;
+          const uint32_t use = (uint32_t)(gc / kBufs);
+          if (in_chunk == 0) {
+            if (!mbar_wait(acce0 + 8 * buf, (use & 1) ^ 1, abort, a.status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          if (!mbar_wait(full0 + 8 * s, round & 1, abort, a.status)) {
+            ok = false;
+            break;
+          }
           tc_fence_after();
-        }
-        if (!mbar_wait(full0 + 8 * s, round & 1, abort, a.status)) break;
-        tc_fence_after();
-        const uint32_t sa = base + s * P::kStageBytes, sb = sa + P::kOpA;
-        // descriptors of this stage's first A and B tiles; every other operand
-        // is a compile-time offset (the address field holds addr >> 4 and the
-        // ring ends below 256 KB, so the additions never carry out of it)
-        const uint64_t da0 = smem_desc<P::kSwizzle>(sa), db0 = smem_desc<P::kSwizzle>(sb);
-        const uint32_t d0 = tmem + (uint32_t)(buf * NL * kBN);
+          const uint32_t sa = base + s * P::kStageBytes, sb = sa + P::kOpA;
+          // descriptors of this stage's first A and B tiles; every other operand
+          // is a compile-time offset (the address field holds addr >> 4 and the
+          // ring ends below 256 KB, so the additions never carry out of it)
+          const uint64_t da0 = smem_desc<P::kSwizzle>(sa), db0 = smem_desc<P::kSwizzle>(sb);
+          const uint32_t d0 = tmem + (uint32_t)(buf * NL * kBN);
 #pragma unroll
-        for (int p = 0; p < P::kProducts; ++p) {
+          for (int p = 0; p < P::kProducts; ++p) {
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {
-            const uint64_t da = da0 + (uint64_t)((prod_a(p) * P::kTileA + kk * 32) >> 4);
-            const uint64_t db = db0 + (uint64_t)((prod_b(p) * P::kTileB + kk * 32) >> 4);
-            tc_mma(d0 + (uint32_t)(prod_level(p) * kBN), da, db,
-                   !(in_chunk == 0 && kk == 0 && prod_a(p) == 0));
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+              const uint64_t da = da0 + (uint64_t)((prod_a(p) * P::kTileA + kk * 32) >> 4);
+              const uint64_t db = db0 + (uint64_t)((prod_b(p) * P::kTileB + kk * 32) >> 4);
+              tc_mma(d0 + (uint32_t)(prod_level(p) * kBN), da, db,
+                     !(in_chunk == 0 && kk == 0 && prod_a(p) == 0));
+            }
+          }
+          tc_commit(empty0 + 8 * s);
+          if (in_chunk == P::kSteps - 1 || it == itm.nk - 1) {
+            tc_commit(accf0 + 8 * buf);
+            ++gc;
           }
         }
-        tc_commit(empty0 + 8 * s);
-        if (in_chunk == P::kSteps - 1 || it == nk - 1) tc_commit(accf0 + 8 * buf);
       }
       // all issued MMAs complete before tensor memory is released
       tc_commit(drain);
@@ -366,16 +415,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;             // TMEM lane quarter of this warp
     const int half = (warp - 2) >> 2;   // which 32 of the tile's 64 columns
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    bool ok = true;
+    int gc = 0;  // accumulator chunks consumed so far (all items)
+    for (int w = blockIdx.x; ok && w < nitems; w += gridDim.x) {
+    const Item itm = decode(w);
+    if (itm.skip) continue;
+    const int bi = itm.bi, bj = itm.bj, out = itm.out;
+    const int nchunks = (itm.nk + P::kSteps - 1) / P::kSteps;
     float hi[32], lo[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       hi[i] = 0.f;
       lo[i] = 0.f;
     }
-    bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-      const int buf = c % kBufs;
-      const uint32_t use = (uint32_t)(c / kBufs);
+    for (int c = 0; c < nchunks && ok; ++c, ++gc) {
+      const int buf = gc % kBufs;
+      const uint32_t use = (uint32_t)(gc / kBufs);
       if (!mbar_wait(accf0 + 8 * buf, use & 1, abort, a.status)) {
         ok = false;
         break;
@@ -384,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t t_acc =
           tmem + lane_off + (uint32_t)(buf * NL * kBN) + (uint32_t)(half * 32);
       // exponents of this chunk: the thread's A row and the warp's 32 B rows
-      const int qg = (int)(k0 / kQ) + c;
+      const int qg = (int)(itm.k0 / kQ) + c;
       const int rowc = min(bi * kBM + q * 32 + lane, a.MP - 1);
       const int ea = (int)a.escA[(int64_t)qg * a.MP + rowc] - 14;
       const uint4* eb_src = reinterpret_cast<const uint4*>(
@@ -445,13 +500,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (ok && nchunks > 0) {
       const int row = bi * kBM + q * 32 + lane;
+      const int split = (int)(itm.k0 / a.kchunk);
       if (row < a.M) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int col = bj * kBN + half * 32 + i;
           if (col < a.N) {
             if (a.mode == 0) {
-              a.work[((int64_t)blockIdx.y * 2 + out) * a.M * a.N + row + (int64_t)col * a.M] =
+              a.work[((int64_t)split * 2 + out) * a.M * a.N + row + (int64_t)col * a.M] =
                   __dadd_rn(widen(hi[i]), widen(lo[i]));
             } else if (a.mode == 1) {
               a.out32[row + (int64_t)col * a.ldo] = __fadd_rn(hi[i], lo[i]);
@@ -462,6 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
+    }  // items
   }
   tc_fence_before();
   __syncthreads();
@@ -762,9 +819,11 @@ cudaError_t launch_tc(const CUtensorMap& tA, const CUtensorMap& tB0, const CUten
   // the shared-memory opt-in is per device: set it once on each
   static std::mutex mu;
   static bool done[128] = {};
+  static int sms[128] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  int nsm;
   {
     std::lock_guard<std::mutex> lock(mu);
     if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
@@ -772,10 +831,19 @@ cudaError_t launch_tc(const CUtensorMap& tA, const CUtensorMap& tB0, const CUten
       e = cudaFuncSetAttribute(k_tc_gemm<D, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                P::kSmemBytes);
       if (e != cudaSuccess) return e;
+      e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
       done[dev] = true;
     }
+    nsm = sms[dev];
   }
-  note_launch(), k_tc_gemm<D, NL><<<grid, kThreads, P::kSmemBytes, st>>>(tA, tB0, tB1, a);
+  // persistent CTAs: one per SM (shared memory allows no second), at most one
+  // per work item
+  const long long items = (long long)(a.upper ? a.ntiles_upper : a.tiles_m * a.tiles_n) *
+                          ((a.K + a.kchunk - 1) / a.kchunk) * a.nout;
+  const unsigned ctas = (unsigned)std::max(1LL, std::min<long long>(items, nsm));
+  (void)grid;
+  note_launch(), k_tc_gemm<D, NL><<<ctas, kThreads, P::kSmemBytes, st>>>(tA, tB0, tB1, a);
   return cudaGetLastError();
 }
 
@@ -829,6 +897,10 @@ cudaError_t tc_project_t(const TX* Xt, int64_t ldx, const TY* Yt, int64_t ldy, i
   a.escB1 = escX;
   a.MP = NP;
   a.NP = NP;
+  a.nout = 2;
+  a.ntiles_upper = 0;
+  for (int bj = 0; bj < a.tiles_n; ++bj)
+    a.ntiles_upper += std::min(a.tiles_m, (bj * kBN + kBN - 1) / kBM + 1);
   a.status = status;
   const int nsp = (int)((lds + a.kchunk - 1) / a.kchunk);
   // out 0: Hs = X^T Y (B = Y slices), out 1: Ms = X^T X (B = X slices); tiles
@@ -890,6 +962,7 @@ cudaError_t tc_rotate_t(const T* Xt, int64_t ld, int64_t nd, int ns, const doubl
   a.escB1 = escZ;
   a.MP = MP;
   a.NP = NP;
+  a.nout = 1;
   a.status = status;
   return launch_tc<P::kD, P::kNL>(mA, mZ, mZ, a, dim3(a.tiles_m * a.tiles_n, 1, 1), st);
 }
@@ -923,7 +996,8 @@ int tc_project_nsplit(int ns) {
     for (int bi = 0; bi < tm; ++bi)
       if (bi * kBM <= bj * kBN + kBN - 1) ++tiles;
   tiles *= 2;  // Hs and Ms
-  int s = (2 * 152 + tiles - 1) / tiles;
+  // enough (tile, split) items for the persistent CTAs to balance: ~4 per SM
+  int s = (4 * 152 + tiles - 1) / tiles;
   return std::max(1, std::min(s, 64));
 }
 
