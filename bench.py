@@ -33,10 +33,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per orbital of one stencil launch of a filter degree
 # on the 96^3 bulk grid, and the FP64-pipe activity, from the ncu captures
-# summarised in profiles/k_apply_h_ring_*_bulk96.md (scaled by orbital count)
-RING64_DRAM_BYTES_PER_ORBITAL = None
-RING64_FP64_PIPE_ACTIVE = None
-RING32_DRAM_BYTES_PER_ORBITAL = None
+# summarised in profiles/k_apply_h_ring_fp64_bulk96.md (scaled by orbital count)
+RING64_DRAM_BYTES_PER_ORBITAL = 2.3108e+07  # (1.0550 + 0.4240) GB / 64 orbitals
+RING64_FP64_PIPE_ACTIVE = 0.846
+RING32_DRAM_BYTES_PER_ORBITAL = None  # no capture of the current FP32 kernel
 
 
 def parse():
