@@ -552,6 +552,15 @@ __device__ __forceinline__ int8_t chunk_exponent(double vmax) {
 // u = 2^-7 (d0 + d1/2^8 + d2/2^16 + ...), each |d| <= 128.  Every step is exact
 // in the input's own precision (FP32 input: its 24-bit mantissa spans at most
 // four digits).
+// BF16 of an integer digit |d| <= 128 without a conversion instruction (on
+// GB300 those run on the FP64 pipe): d + 1.5 * 2^23 is exact as a float whose
+// low mantissa bits hold d, and a float with at most 8 significant bits is
+// its BF16 bit pattern in the upper half word.
+__device__ __forceinline__ __nv_bfloat16 digit_bf16(int d) {
+  const float f = __fsub_rn(__int_as_float(0x4B400000 + d), 12582912.0f);
+  return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
+}
+
 // FP64 input: integer arithmetic on the IEEE-754 fields (GB300's FP64 pipe is
 // 1/64 of its FP32 rate): F = x 2^(7 + 8(D-1) - E) rounded to an integer
 // (|F| < 2^(7 + 8(D-1))), then d_k = round(F / 2^s), F -= d_k 2^s for
@@ -579,7 +588,7 @@ __device__ __forceinline__ void digits(double x, int E, __nv_bfloat16 (&d)[D]) {
     } else {
       dk = F;
     }
-    d[k] = __float2bfloat16_rn((float)(int)dk);
+    d[k] = digit_bf16((int)dk);
   }
 }
 template <int D>
@@ -588,7 +597,7 @@ __device__ __forceinline__ void digits(float x, int E, __nv_bfloat16 (&d)[D]) {
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const float r = rintf(u);
-    d[k] = __float2bfloat16_rn(r);
+    d[k] = __ushort_as_bfloat16((unsigned short)(__float_as_uint(r) >> 16));  // exact: |r| <= 128
     u = (u - r) * 256.0f;
   }
 }
