@@ -279,7 +279,7 @@ __global__ void k_house_tail(const double* A, double* Hv, double* d, double* e, 
 
 // ---------------------------------------------------------------------------
 // Persistent form of the Householder reduction: one cooperative launch runs all
-// n - 2 steps, separated by a grid barrier (3 per step) instead of 3 kernel
+// n - 2 steps, separated by grid barriers (2 per step) instead of 3 kernel
 // launches per step.  The barrier waits are bounded: on expiry the kernel
 // records SPARC_ERR_TIMEOUT in status[4] and every block leaves the loop.
 // ---------------------------------------------------------------------------
@@ -322,6 +322,10 @@ __device__ bool grid_barrier(const GridBar& gb, unsigned nblocks, int* abort_sh)
 __global__ void __launch_bounds__(256)
     k_house_persistent(double* __restrict__ A, double* __restrict__ Hv, double* d, double* e,
                        double* __restrict__ p, int n, GridBar gb) {
+  // every block forms the step's reflector itself, in shared memory (the
+  // column it reads was completed by the previous step's barrier), so a step
+  // needs two grid barriers: after p = A v and after the rank-2 update
+  extern __shared__ double vsh[];
   __shared__ double sh[32];
   __shared__ int abort_sh;
   if (threadIdx.x == 0) abort_sh = 0;
@@ -332,49 +336,48 @@ __global__ void __launch_bounds__(256)
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int k = 0; k + 2 < n; ++k) {
     const double* col = A + (int64_t)k * n;
-    double* hv = Hv + (int64_t)k * n;
+    double acc = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += col[i] * col[i];
+    const double xn = sqrt(block_sum_d(acc, sh));
+    const double x0 = col[k + 1];
+    const double alpha = x0 >= 0.0 ? -xn : xn;
+    double vn2 = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const double v = col[i] - (i == k + 1 ? alpha : 0.0);
+      vn2 += v * v;
+    }
+    const double vn = sqrt(block_sum_d(vn2, sh));
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
+      vsh[i] = (xn > 0.0 && vn > 0.0) ? (col[i] - (i == k + 1 ? alpha : 0.0)) / vn : 0.0;
+    __syncthreads();  // the whole reflector is in shared memory from here on
     if (blockIdx.x == 0) {
-      double acc = 0.0;
-      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += col[i] * col[i];
-      const double xn = sqrt(block_sum_d(acc, sh));
-      const double x0 = col[k + 1];
-      const double alpha = x0 >= 0.0 ? -xn : xn;
-      double vn2 = 0.0;
-      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-        const double v = col[i] - (i == k + 1 ? alpha : 0.0);
-        vn2 += v * v;
-      }
-      const double vn = sqrt(block_sum_d(vn2, sh));
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double v = 0.0;
-        if (i > k && xn > 0.0 && vn > 0.0) v = (col[i] - (i == k + 1 ? alpha : 0.0)) / vn;
-        hv[i] = v;
-      }
+      double* hv = Hv + (int64_t)k * n;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) hv[i] = i > k ? vsh[i] : 0.0;
       if (threadIdx.x == 0) {
         d[k] = col[k];
         e[k] = xn > 0.0 ? alpha : 0.0;
       }
     }
-    if (!grid_barrier(gb, nb, &abort_sh)) return;
     // p = A v on the trailing block (warp per row)
     for (int i = k + 1 + gwarp; i < n; i += nwarps) {
       const double* row = A + (int64_t)i * n;
       double s2 = 0.0;
-      for (int j = k + 1 + lane; j < n; j += 32) s2 += row[j] * hv[j];
+      for (int j = k + 1 + lane; j < n; j += 32) s2 += row[j] * vsh[j];
       s2 = warp_sum_d(s2);
       if (lane == 0) p[i] = s2;
     }
     if (!grid_barrier(gb, nb, &abort_sh)) return;
-    double acc = 0.0;
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += hv[i] * p[i];
+    acc = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += vsh[i] * p[i];
     const double K = block_sum_d(acc, sh);
     const int m = n - k - 1;
     const int64_t mm = (int64_t)m * m;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < mm;
          t += (int64_t)gridDim.x * blockDim.x) {
       const int i = k + 1 + (int)(t % m), j = k + 1 + (int)(t / m);
-      const double qi = p[i] - K * hv[i], qj = p[j] - K * hv[j];
-      A[i + (int64_t)j * n] -= 2.0 * (hv[i] * qj + qi * hv[j]);
+      const double vi = vsh[i], vj = vsh[j];
+      const double qi = p[i] - K * vi, qj = p[j] - K * vj;
+      A[i + (int64_t)j * n] -= 2.0 * (vi * qj + qi * vj);
     }
     if (!grid_barrier(gb, nb, &abort_sh)) return;
   }
@@ -778,7 +781,14 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_house_persistent, 256, 0);
+    const size_t vbytes = (size_t)n * sizeof(double);
+    if (vbytes > 48 * 1024)
+      cudaFuncSetAttribute(k_house_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)std::min<size_t>(vbytes, 200 * 1024));
+    if (vbytes <= 200 * 1024)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_house_persistent, 256, vbytes);
+    else
+      per_sm = 0;  // the reflector would not fit in shared memory: per-step kernels
     if (coop && sms > 0 && per_sm > 0) {
       int blocks = sms * std::min(per_sm, 2);
       GridBar gb{reinterpret_cast<unsigned*>(w.status + 8), reinterpret_cast<unsigned*>(w.status + 9),
@@ -791,8 +801,8 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
       int nn_ = n;
       void* args[] = {&Ap, &Hv, &dp, &ep, &p, &nn_, &gb};
       note_launch();
-      if (cudaLaunchCooperativeKernel((void*)k_house_persistent, dim3(blocks), dim3(256), args, 0,
-                                      st) == cudaSuccess)
+      if (cudaLaunchCooperativeKernel((void*)k_house_persistent, dim3(blocks), dim3(256), args,
+                                      vbytes, st) == cudaSuccess)
         coop_done = true;
       else
         cudaGetLastError();

@@ -312,13 +312,17 @@ template cudaError_t apply_h<float>(const Grid&, const LapCoef&, const float*,
                                     double, int*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// K2: nonlocal coefficients.  One CTA per (atom, group of orbitals); threads
-// stride over the atom's support points; fixed-order block reduction.
+// K2: nonlocal coefficients D[n][k] = gamma_k h^3 sum_t chi_k(t) x_n(t).  One
+// CTA per (atom, group of kNlOrb orbitals): threads stride over the atom's
+// support points, load the point's projector values once and apply them to
+// every orbital of the group; warp partial sums go through shared memory and
+// are added in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int kNlThreads = 256;
-constexpr int kNlOrb = 4;
+constexpr int kNlOrb = 8;
+constexpr int kNlProj = 4;  // projectors per pass
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -331,7 +335,7 @@ template <typename T>
 __global__ void __launch_bounds__(kNlThreads)
     k_nl_coef(const Nonlocal<T> nl, double h3, const T* __restrict__ x, int64_t ldx, int ns,
               T* __restrict__ D) {
-  __shared__ T red[4][kNlThreads / 32];
+  __shared__ T red[kNlThreads / 32][kNlOrb][kNlProj];
   const int J = blockIdx.x;
   const int64_t s0 = nl.supp_ptr[J];
   const int nsup = (int)(nl.supp_ptr[J + 1] - s0);
@@ -341,31 +345,46 @@ __global__ void __launch_bounds__(kNlThreads)
   const int* __restrict__ idx = nl.supp_idx + s0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nb = blockIdx.y * kNlOrb;
-  for (int n = nb; n < min(nb + kNlOrb, ns); ++n) {
-    const T* __restrict__ xn = x + (int64_t)n * ldx;
-    for (int qb = 0; qb < np; qb += 4) {
-      T acc[4] = {T(0), T(0), T(0), T(0)};
-      for (int t = threadIdx.x; t < nsup; t += kNlThreads) {
-        T xv = __ldg(xn + __ldg(idx + t));
+  const int norb = min(kNlOrb, ns - nb);
+  const T* __restrict__ xb = x + (int64_t)nb * ldx;
+  for (int qb = 0; qb < np; qb += kNlProj) {
+    T acc[kNlOrb][kNlProj];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (qb + q < np) acc[q] += __ldg(chi + (int64_t)(qb + q) * nsup + t) * xv;
-      }
+    for (int n = 0; n < kNlOrb; ++n)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        T v = warp_sum(acc[q]);
-        if (lane == 0) red[q][wid] = v;
-      }
-      __syncthreads();
-      if (threadIdx.x < 4 && qb + (int)threadIdx.x < np) {
-        int q = threadIdx.x;
-        T v = T(0);
-        for (int w = 0; w < kNlThreads / 32; ++w) v += red[q][w];
-        int k = k0 + qb + q;
-        D[(int64_t)n * nl.kp + k] = T(v * (nl.gamma[k] * h3));
-      }
-      __syncthreads();
+      for (int q = 0; q < kNlProj; ++q) acc[n][q] = T(0);
+    for (int t = threadIdx.x; t < nsup; t += kNlThreads) {
+      const int64_t i = __ldg(idx + t);
+      T c[kNlProj];
+#pragma unroll
+      for (int q = 0; q < kNlProj; ++q)
+        c[q] = qb + q < np ? __ldg(chi + (int64_t)(qb + q) * nsup + t) : T(0);
+      T xv[kNlOrb];
+#pragma unroll
+      for (int n = 0; n < kNlOrb; ++n) xv[n] = n < norb ? __ldg(xb + (int64_t)n * ldx + i) : T(0);
+#pragma unroll
+      for (int n = 0; n < kNlOrb; ++n)
+#pragma unroll
+        for (int q = 0; q < kNlProj; ++q) acc[n][q] += c[q] * xv[n];
     }
+#pragma unroll
+    for (int n = 0; n < kNlOrb; ++n)
+#pragma unroll
+      for (int q = 0; q < kNlProj; ++q) {
+        const T v = warp_sum(acc[n][q]);
+        if (lane == 0) red[wid][n][q] = v;
+      }
+    __syncthreads();
+    if (threadIdx.x < kNlOrb * kNlProj) {
+      const int n = threadIdx.x / kNlProj, q = threadIdx.x % kNlProj;
+      if (n < norb && qb + q < np) {
+        T v = T(0);
+        for (int w = 0; w < kNlThreads / 32; ++w) v += red[w][n][q];
+        const int k = k0 + qb + q;
+        D[(int64_t)(nb + n) * nl.kp + k] = T(v * (nl.gamma[k] * h3));
+      }
+    }
+    __syncthreads();
   }
 }
 
