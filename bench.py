@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--config", type=int, default=2)
+    p.add_argument("--workload", default="bulk96",
+                   help="bulk96 (96^3 bulk, Ns 1300), bulk24 (24^3, Ns 40) or slab64x64x160")
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -209,8 +210,8 @@ def run_reference(args, world, rank):
         return 0
     from paper_2302_09708_gb300 import synth
 
-    cfg = synth.CONFIGS[2 if args.config == 3 else args.config]
-    system = synth.make_config_system(args.config)
+    cfg = synth.WORKLOADS[args.workload]
+    system = synth.make_workload_system(args.workload)
     ns, m = cfg["ns"], cfg["degree"]
     budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     times = []
@@ -254,11 +255,11 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sparc.load()
-    cfg = synth.CONFIGS[2 if args.config == 3 else args.config]
-    system = synth.make_config_system(args.config)
+    cfg = synth.WORKLOADS[args.workload]
+    system = synth.make_workload_system(args.workload)
     ns, m = (args.ns or cfg["ns"]), cfg["degree"]
     nd = system.nd
-    seed = synth.config_seed(args.config) + rank
+    seed = synth.workload_seed(args.workload) + rank
     t_setup = time.perf_counter()
     X0 = synth.random_orbitals(nd, ns, seed=seed)
     setup_s = time.perf_counter() - t_setup
@@ -423,7 +424,10 @@ def main():
         "config": {"workload": cfg["name"] + (f" (Ns overridden to {ns})" if args.ns else ""),
                    "precision": prec, "grid": list(system.shape),
                    "h": system.h, "natoms": system.natoms, "ns": ns, "degree": m,
-                   "l2": "inputs larger than L2 (9.2 GB block)", "bounds": "library (Lanczos 32, "
+                   "l2": (f"inputs larger than L2 ({nd * ns * s_bytes / 1e9:.1f} GB block)"
+                          if nd * ns * s_bytes > 2 * 129e6 else
+                          "inputs fit in L2 (small workload; no flush)"),
+                   "bounds": "library (Lanczos 32, "
                    "cut-off = previous max Ritz value)", "parallelism": f"replicas x{world}"},
         "stages": stage_rate,
         "hpsi_gbs": hx_gbs,

@@ -231,33 +231,37 @@ def electrons_for(ns: int) -> int:
 
 
 # ---------------------------------------------------------------------------
-# Named workloads.  Seeds are SEED_BASE + 1000 * config + system_index.
+# Named workloads.  Each has its own seed block: seed = SEED_BASE + offset +
+# system index.
 # ---------------------------------------------------------------------------
-CONFIGS = {
-    1: dict(name="24^3 periodic, h=0.5, 8 random atoms, Ns=40, m=20",
-            shape=(24, 24, 24), h=0.5, bc=(PERIODIC,) * 3, ns=40, degree=20, steps=1),
-    2: dict(name="96^3 periodic bulk, h=0.4, 216 atoms (6^3 jittered SC), Ns=1300, m=20",
-            shape=(96, 96, 96), h=0.4, bc=(PERIODIC,) * 3, ns=1300, degree=20, steps=3),
-    4: dict(name="64x64x160 slab (periodic xy, Dirichlet z), h=0.35, 600 atoms, Ns=4800, m=24",
-            shape=(64, 64, 160), h=0.35, bc=(PERIODIC, PERIODIC, DIRICHLET), ns=4800,
-            degree=24, steps=1),
+WORKLOADS = {
+    "bulk24": dict(name="24^3 periodic, h=0.5, 8 random atoms, Ns=40, m=20", seed_offset=1000,
+                   shape=(24, 24, 24), h=0.5, bc=(PERIODIC,) * 3, ns=40, degree=20, steps=1),
+    "bulk96": dict(name="96^3 periodic bulk, h=0.4, 216 atoms (6^3 jittered SC), Ns=1300, m=20",
+                   seed_offset=2000, shape=(96, 96, 96), h=0.4, bc=(PERIODIC,) * 3, ns=1300,
+                   degree=20, steps=3),
+    "slab64x64x160": dict(name="64x64x160 slab (periodic xy, Dirichlet z), h=0.35, 600 atoms, "
+                               "Ns=4800, m=24", seed_offset=4000, shape=(64, 64, 160), h=0.35,
+                          bc=(PERIODIC, PERIODIC, DIRICHLET), ns=4800, degree=24, steps=1),
 }
+BATCH_SEED_OFFSET = 5000  # the 64 uneven systems of the batched form
 
 
-def config_seed(config_id: int, index: int = 0) -> int:
-    return SEED_BASE + 1000 * config_id + index
+def workload_seed(workload: str, index: int = 0) -> int:
+    return SEED_BASE + WORKLOADS[workload]["seed_offset"] + index
 
 
-def make_config_system(config_id: int) -> System:
-    """The synthetic system of a named workload (configs 1, 2 and 4; 3 reuses 2)."""
-    cid = 2 if config_id == 3 else config_id
-    c = CONFIGS[cid]
-    seed = config_seed(cid)
+def make_workload_system(workload: str) -> System:
+    """The synthetic system of a named workload: the 24^3 bulk with 8 random
+    atoms, the 96^3 bulk with 216 atoms on a jittered simple-cubic lattice, or
+    the 64 x 64 x 160 slab with 600 atoms in the central 60 % of z."""
+    c = WORKLOADS[workload]
+    seed = workload_seed(workload)
     shape, h, bc = c["shape"], c["h"], c["bc"]
-    if cid == 1:
+    if workload == "bulk24":
         return random_system(shape, h, bc, 8, seed, name=c["name"])
     rng = np.random.default_rng(seed + 500)
-    if cid == 2:
+    if workload == "bulk96":
         pos = jittered_lattice((6, 6, 6), 6.4, (3.2, 3.2, 3.2), 0.5, rng)
     else:  # slab: 10 x 10 x 6 lattice in x, y and z in [0.2, 0.8] Lz
         lx, lz = shape[0] * h, (shape[2] - 1) * h
@@ -272,7 +276,7 @@ def make_config_system(config_id: int) -> System:
 def batch_members(count: int = 64, seed: int | None = None):
     """Uneven small systems for the batched form: N^3 grids, N ~ U{24..48}, h = 0.5,
     periodic, 4..40 atoms, Ns ~ U{40..300}, degree ~ U{16..24}."""
-    rng = np.random.default_rng(config_seed(5) if seed is None else seed)
+    rng = np.random.default_rng(SEED_BASE + BATCH_SEED_OFFSET if seed is None else seed)
     out = []
     for i in range(count):
         n = int(rng.integers(24, 49))
@@ -281,5 +285,5 @@ def batch_members(count: int = 64, seed: int | None = None):
         ns = min(ns, n ** 3 // 4)
         m = int(rng.integers(16, 25))
         out.append(dict(shape=(n, n, n), h=0.5, bc=(PERIODIC,) * 3, natoms=a, ns=ns, degree=m,
-                        seed=config_seed(5, i + 1)))
+                        seed=SEED_BASE + BATCH_SEED_OFFSET + i + 1))
     return out

@@ -103,15 +103,15 @@ def test_density_of_no_orbitals_is_zero():
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("mixed", 1e-6)])
 def test_density_after_step_vs_oracle(precision, tol):
-    """Config-1 system: one CheFSI step, occupations and density on the GPU
+    """24^3 bulk system: one CheFSI step, occupations and density on the GPU
     against the oracle's step, occupations and density (the density is
     invariant under rotations within degenerate levels)."""
-    s = synth.make_config_system(1)
+    s = synth.make_workload_system("bulk24")
     o = oracle.Oracle(s)
     ns, m = 40, 20
     a0, b, *_ = o.lanczos(32, 0)
     a = a0 + 0.1 * (b - a0)
-    X0 = synth.random_orbitals(s.nd, ns, seed=synth.config_seed(1))
+    X0 = synth.random_orbitals(s.nd, ns, seed=synth.workload_seed("bulk24"))
     rX, rlam = o.chefsi_step(X0, m, a, b, a0)
     for _ in range(2):
         rX, rlam = o.chefsi_step(rX, m, rlam[-1], b, a0)

@@ -23,7 +23,7 @@ SAMPLE = [0, 1, 517, 1299]
 
 @pytest.fixture(scope="module")
 def system():
-    return synth.make_config_system(2)
+    return synth.make_workload_system("bulk96")
 
 
 @pytest.fixture(scope="module")

@@ -23,7 +23,7 @@ from paper_2302_09708_gb300 import sparc  # noqa: E402
 DEV = torch.device("cuda:0")
 
 SYSTEMS = {
-    "cfg1": lambda: synth.make_config_system(1),
+    "bulk24": lambda: synth.make_workload_system("bulk24"),
     "ragged_periodic": lambda: synth.random_system((13, 17, 19), 0.5, (0, 0, 0), 3, seed=41),
     "dirichlet_z": lambda: synth.random_system((20, 18, 27), 0.45, (0, 0, 1), 4, seed=42),
     "all_dirichlet_odd": lambda: synth.random_system((15, 13, 14), 0.5, (1, 1, 1), 2, seed=43),
@@ -82,7 +82,7 @@ def test_hpsi_leading_dimension(ld_pad):
     assert np.all(Y[:, s.nd:] == 7.0)  # rows beyond Nd are never written
 
 
-@pytest.mark.parametrize("name", ["cfg1", "dirichlet_z", "wide_x", "ring_periodic",
+@pytest.mark.parametrize("name", ["bulk24", "dirichlet_z", "wide_x", "ring_periodic",
                                   "ring_dirichlet_y"])
 def test_hpsi_fp32(name):
     s = SYSTEMS[name]()
@@ -101,7 +101,7 @@ def bounds_for(o):
     return a0, b, a0 + 0.1 * (b - a0)
 
 
-@pytest.mark.parametrize("name", ["cfg1", "dirichlet_z", "free"])
+@pytest.mark.parametrize("name", ["bulk24", "dirichlet_z", "free"])
 def test_spectrum_bounds(name):
     s = SYSTEMS[name]()
     o = oracle.Oracle(s)
@@ -113,7 +113,7 @@ def test_spectrum_bounds(name):
         assert abs(b - rb) < 1e-9 * max(1, abs(rb)), (b, rb)
 
 
-@pytest.mark.parametrize("name,degree", [("cfg1", 20), ("dirichlet_z", 7), ("ragged_periodic", 1),
+@pytest.mark.parametrize("name,degree", [("bulk24", 20), ("dirichlet_z", 7), ("ragged_periodic", 1),
                                          ("wide_x", 12), ("ring_periodic", 9),
                                          ("ring_dirichlet_y", 4)])
 def test_cheb_filter_fp64(name, degree):
@@ -133,7 +133,7 @@ def test_cheb_filter_fp64(name, degree):
 
 
 def test_cheb_filter_host_buffer_matches_device():
-    s = SYSTEMS["cfg1"]()
+    s = SYSTEMS["bulk24"]()
     o = oracle.Oracle(s)
     a0, b, a = bounds_for(o)
     X = synth.random_orbitals(s.nd, 4, seed=8)
@@ -151,7 +151,7 @@ def test_project_and_rotate_fp64(flags):
     only differs from the oracle); flags 0 = six-digit tensor-core split, whose
     error is bounded by 2^-42 sum_k |x_k| |y_k| entrywise (about 2^-45 expected:
     the first dropped digit level is 2^-48 of the chunk maxima)."""
-    s = SYSTEMS["cfg1"]()
+    s = SYSTEMS["bulk24"]()
     ns = 40
     rng = np.random.default_rng(4)
     X, Y = rng.standard_normal((2, ns, s.nd))
@@ -179,7 +179,7 @@ def test_project_and_rotate_fp64(flags):
         assert np.all(eR <= bR), np.max(eR / bR)
 
 
-@pytest.mark.parametrize("name,ns", [("ragged_periodic", 200), ("cfg1", 129), ("wide_x", 1),
+@pytest.mark.parametrize("name,ns", [("ragged_periodic", 200), ("bulk24", 129), ("wide_x", 1),
                                      ("dirichlet_z", 300)])
 def test_project_rotate_fp64_tensor_cores_vs_simt(name, ns):
     """Six-digit tensor-core projection/rotation against the FP64 SIMT kernels
@@ -260,9 +260,9 @@ def test_subspace_eig_not_spd():
     assert np.allclose(lam.cpu().numpy(), oracle.gen_eig(H, M)[0], atol=1e-10)
 
 
-@pytest.mark.parametrize("name,ns,degree,flags", [("cfg1", 40, 20, 0), ("dirichlet_z", 24, 10, 0),
+@pytest.mark.parametrize("name,ns,degree,flags", [("bulk24", 40, 20, 0), ("dirichlet_z", 24, 10, 0),
                                                   ("ragged_periodic", 9, 8, 0), ("free", 33, 15, 0),
-                                                  ("wide_x", 1, 6, 0), ("cfg1", 40, 20, 2),
+                                                  ("wide_x", 1, 6, 0), ("bulk24", 40, 20, 2),
                                                   ("dirichlet_z", 24, 10, 2)])
 def test_chefsi_step_fp64(name, ns, degree, flags):
     s = SYSTEMS[name]()
@@ -281,13 +281,13 @@ def test_chefsi_step_fp64(name, ns, degree, flags):
     assert t["total_ms"] > 0 and t["filter_ms"] > 0
 
 
-def test_chefsi_three_steps_cfg1_default_bounds():
+def test_chefsi_three_steps_bulk24_default_bounds():
     """Three steps with library-chosen bounds (cached Lanczos, cutoff = previous
     largest Ritz value) against the oracle fed the same bounds."""
-    s = SYSTEMS["cfg1"]()
+    s = SYSTEMS["bulk24"]()
     o = oracle.Oracle(s)
     ns, m = 40, 20
-    X0 = synth.random_orbitals(s.nd, ns, seed=synth.config_seed(1))
+    X0 = synth.random_orbitals(s.nd, ns, seed=synth.workload_seed("bulk24"))
     h = sparc.Handle(s, "fp64", ns_max=ns)
     a0, b = h.spectrum_bounds(32, 0)
     ra0, rb, *_ = o.lanczos(32, 0)
@@ -321,7 +321,7 @@ def test_chefsi_step_host_buffer_and_determinism():
 
 
 def test_invalid_arguments():
-    s = SYSTEMS["cfg1"]()
+    s = SYSTEMS["bulk24"]()
     h = sparc.Handle(s, "fp64", ns_max=4)
     X = to_dev(np.zeros((4, s.nd)))
     with pytest.raises(sparc.SparcError) as ei:
@@ -340,7 +340,7 @@ def test_invalid_arguments():
 # rotation (three BF16 slices per operand, six slice products, double-FP32
 # accumulation) against the oracle evaluated on the same FP32 inputs.
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("name,ns", [("cfg1", 40), ("ragged_periodic", 200), ("cfg1", 129),
+@pytest.mark.parametrize("name,ns", [("bulk24", 40), ("ragged_periodic", 200), ("bulk24", 129),
                                      ("wide_x", 1)])
 def test_project_mixed_tensor_cores(name, ns):
     s = SYSTEMS[name]()
@@ -356,7 +356,7 @@ def test_project_mixed_tensor_cores(name, ns):
     assert eH < 1e-7 and eM < 1e-7, (eH, eM)
 
 
-@pytest.mark.parametrize("name,ns", [("cfg1", 40), ("ragged_periodic", 200), ("dirichlet_z", 7)])
+@pytest.mark.parametrize("name,ns", [("bulk24", 40), ("ragged_periodic", 200), ("dirichlet_z", 7)])
 def test_rotate_mixed_tensor_cores(name, ns):
     s = SYSTEMS[name]()
     rng = np.random.default_rng(ns + 1)
@@ -369,7 +369,7 @@ def test_rotate_mixed_tensor_cores(name, ns):
     assert err < 1e-6, err
 
 
-@pytest.mark.parametrize("name,ns,degree", [("cfg1", 40, 20), ("dirichlet_z", 24, 10),
+@pytest.mark.parametrize("name,ns,degree", [("bulk24", 40, 20), ("dirichlet_z", 24, 10),
                                             ("ring_periodic", 30, 12)])
 def test_chefsi_step_mixed_vs_oracle(name, ns, degree):
     """Mixed precision step against the FP64 oracle: the Ritz values of the
@@ -391,7 +391,7 @@ def test_chefsi_step_mixed_vs_oracle(name, ns, degree):
     assert np.max(np.abs(X1 @ X1.T - np.eye(ns))) < 1e-4
 
 
-@pytest.mark.parametrize("name", ["ring_periodic", "ring_dirichlet_y", "cfg1"])
+@pytest.mark.parametrize("name", ["ring_periodic", "ring_dirichlet_y", "bulk24"])
 def test_ring_and_generic_stencil_agree(name):
     """The TMA plane-ring form and the generic form of the stencil kernel give
     the same H X: in FP64 arithmetic (default) up to summation order, in the
@@ -418,7 +418,7 @@ def test_ring_and_generic_stencil_agree(name):
     assert float((F[0] - F[1]).abs().max()) <= 1e-11 * float(F[1].abs().max())
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ring_periodic"])
+@pytest.mark.parametrize("name", ["bulk24", "ring_periodic"])
 def test_chefsi_step_fp64_double_fp32_stencil(name):
     """FP64 handle with the double-FP32 stencil (options bit 2): Ritz values
     and subspace of a step stay within the FP64 targets (1e-8 Ha, 1e-7)."""

@@ -49,7 +49,7 @@ def test_reference_arm_under_torchrun_prints_one_line_on_rank0():
     env = dict(os.environ, OMP_NUM_THREADS="2")
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(free_port()),
-           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "1",
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "bulk24",
            "--gpus", "2", "--steps", "1", "--warmup", "0"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]

@@ -36,7 +36,7 @@ def _noalloc(L, X, Y, ns, nd, ld):
 
 def test_project_noalloc_matches_handle_projection_on_consecutive_calls():
     L = sparc.load()
-    s = synth.make_config_system(1)
+    s = synth.make_workload_system("bulk24")
     nd = s.nd
     # the handle projection on the FP64 SIMT pipe, the kernel sparc_project_noalloc runs
     h = sparc.Handle(s, "fp64", ns_max=64, options_flags=2)
