@@ -111,10 +111,18 @@ typedef struct {
 } sparc_options;
 
 /* Stage times (ms) of the last sparc_chefsi_step on the handle (CUDA events)
- * and the number of library kernels it launched. */
+ * and the number of library kernels it launched.  bounds_ms includes the
+ * host-to-device staging of a host block; total_ms runs from the call's first
+ * event to the end of the rotation.  stage_in_ms / stage_out_ms: the event-
+ * timed host-to-device and device-to-host copies of a host block (0 for
+ * device blocks).  host_ms: wall time of the whole call on the host clock,
+ * from entry to return (for host blocks this includes the final copy and
+ * synchronisation; for device blocks the step's own synchronisation on its
+ * status word). */
 typedef struct {
   float bounds_ms, filter_ms, hx_ms, project_ms, eig_ms, rotate_ms, total_ms;
   int64_t launches;
+  float stage_in_ms, stage_out_ms, host_ms;
 } sparc_timings;
 
 /*
@@ -271,6 +279,25 @@ int sparc_batch_chefsi_step(sparc_batch b, void* const* X, const int* ns, const 
 
 /* Kernel launches per batched step (nodes of the captured graph). */
 int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step);
+
+/*
+ * sparc_host_alloc / sparc_host_free — page-locked host memory for orbital
+ * blocks that are staged through sparc_chefsi_step / sparc_cheb_filter (not a
+ * step of the method; a host-side convenience).  The block comes from an
+ * anonymous private mapping, 2 MiB aligned, hinted for transparent huge pages
+ * and registered with cudaHostRegister (portable).  Host blocks pinned this way
+ * keep the full copy-engine rate across steps; on Grace-Blackwell systems,
+ * blocks from cudaHostAlloc were measured to drop to a fifth or less of it for
+ * the first pass after a step that streams hundreds of GB through HBM.
+ * bytes > 0; *out receives the block (uninitialised) or NULL on error.
+ * sparc_host_free takes a pointer from sparc_host_alloc (NULL is a no-op) and
+ * must not be called while a copy from or to the block is in flight.
+ * Thread-safe.  Errors: INVALID_ARG (bytes == 0, out NULL, unknown pointer),
+ * OOM (mmap failed), CUDA (registration failed, e.g. no device); the message
+ * is available from sparc_last_error(NULL).
+ */
+int sparc_host_alloc(size_t bytes, void** out);
+int sparc_host_free(void* p);
 
 /*
  * sparc_project_noalloc — the FP64 projection of sparc_project (Hs = Xt^T Yt,

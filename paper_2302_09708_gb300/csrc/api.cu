@@ -7,9 +7,13 @@
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
+#include <sys/mman.h>
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <chrono>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -322,8 +326,10 @@ int stage_in(sparc_context* c, const void* X, int ns, int64_t ld, int dtype, voi
              int64_t* ldd, cudaStream_t st) {
   size_t es = elem_size(dtype);
   if (!c->Wstage) CK(c, cudaMalloc(&c->Wstage, (size_t)c->ld * c->ns_max * es));
+  CK(c, cudaEventRecord(c->ev_stage[0], st));
   CK(c, cudaMemcpy2DAsync(c->Wstage, c->ld * es, X, ld * es, c->nd * es, ns,
                           cudaMemcpyHostToDevice, st));
+  CK(c, cudaEventRecord(c->ev_stage[1], st));
   *dev = c->Wstage;
   *ldd = c->ld;
   return SPARC_OK;
@@ -331,8 +337,10 @@ int stage_in(sparc_context* c, const void* X, int ns, int64_t ld, int dtype, voi
 
 int stage_out(sparc_context* c, void* X, int ns, int64_t ld, int dtype, cudaStream_t st) {
   size_t es = elem_size(dtype);
+  CK(c, cudaEventRecord(c->ev_stage[2], st));
   CK(c, cudaMemcpy2DAsync(X, ld * es, c->Wstage, c->ld * es, c->nd * es, ns,
                           cudaMemcpyDeviceToHost, st));
+  CK(c, cudaEventRecord(c->ev_stage[3], st));
   CK(c, cudaStreamSynchronize(st));
   return SPARC_OK;
 }
@@ -347,6 +355,8 @@ void destroy_ctx(sparc_context* c) {
   cudaFree(c->lz);
   eig_free(c->eig);
   for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->ev_stage)
     if (e) cudaEventDestroy(e);
   delete c;
 }
@@ -594,6 +604,7 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
   CK(c, eig_alloc(c->eig, c->ns_max));
   CK(c, cudaMemset(c->eig.status, 0, 16 * sizeof(int)));
   for (auto& e : c->ev) CK(c, cudaEventCreate(&e));
+  for (auto& e : c->ev_stage) CK(c, cudaEventCreate(&e));
   return SPARC_OK;
 }
 
@@ -623,6 +634,79 @@ int sparc_destroy(sparc_handle h) {
   if (!h) return SPARC_OK;
   cudaSetDevice(h->device);
   destroy_ctx(h);
+  return SPARC_OK;
+}
+
+// Page-locked host blocks: an anonymous private mapping (2 MiB aligned, with a
+// transparent-huge-page hint) registered with CUDA.  Kept in a registry so
+// that sparc_host_free can find the mapping's base and length.
+namespace {
+struct HostMapping {
+  void* base;
+  size_t len;
+};
+std::mutex g_host_mu;
+std::map<void*, HostMapping> g_host_maps;
+}  // namespace
+
+int sparc_host_alloc(size_t bytes, void** out) {
+  if (!out) {
+    g_create_err = "invalid argument: out is NULL";
+    return SPARC_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (bytes == 0) {
+    g_create_err = "invalid argument: bytes must be > 0";
+    return SPARC_ERR_INVALID_ARG;
+  }
+  const size_t align = size_t(2) << 20;
+  if (bytes > SIZE_MAX - 2 * align) {
+    g_create_err = "invalid argument: bytes too large";
+    return SPARC_ERR_INVALID_ARG;
+  }
+  const size_t len = bytes + align;
+  void* base = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+  if (base == MAP_FAILED) {
+    g_create_err = "mmap of the host block failed";
+    return SPARC_ERR_OOM;
+  }
+  char* p = (char*)(((uintptr_t)base + align - 1) & ~(uintptr_t)(align - 1));
+#ifdef MADV_HUGEPAGE
+  madvise(p, bytes, MADV_HUGEPAGE);  // a hint: failure leaves ordinary pages
+#endif
+  cudaError_t e = cudaHostRegister(p, bytes, cudaHostRegisterPortable);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    munmap(base, len);
+    g_create_err = std::string("cudaHostRegister: ") + cudaGetErrorString(e);
+    return SPARC_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_host_mu);
+  g_host_maps[p] = HostMapping{base, len};
+  *out = p;
+  return SPARC_OK;
+}
+
+int sparc_host_free(void* p) {
+  if (!p) return SPARC_OK;
+  HostMapping m;
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    auto it = g_host_maps.find(p);
+    if (it == g_host_maps.end()) {
+      g_create_err = "invalid argument: pointer was not returned by sparc_host_alloc";
+      return SPARC_ERR_INVALID_ARG;
+    }
+    m = it->second;
+    g_host_maps.erase(it);
+  }
+  cudaError_t e = cudaHostUnregister(p);
+  munmap(m.base, m.len);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    g_create_err = std::string("cudaHostUnregister: ") + cudaGetErrorString(e);
+    return SPARC_ERR_CUDA;
+  }
   return SPARC_OK;
 }
 
@@ -738,6 +822,8 @@ int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   ARG(c, degree >= 1 && degree <= 1000, "degree must be in [1, 1000]");
   CK(c, cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
+  const auto wall0 = std::chrono::steady_clock::now();
+  c->staged = false;
   const long long launches0 = launch_count();
   CK(c, cudaEventRecord(c->ev[0], st));
   CK(c, cudaMemsetAsync(c->eig.status + 2, 0, 2 * sizeof(int), st));
@@ -769,7 +855,10 @@ int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
     rc = do_step<float>(c, (float*)Xd, ldd, ns, degree, a, b, a0, eig, eig_on_host, st);
   if (rc) return rc;
   c->step_launches = launch_count() - launches0;
-  if (host) return stage_out(c, X, ns, ld, dtype, st);
+  if (host && (rc = stage_out(c, X, ns, ld, dtype, st))) return rc;
+  c->staged = host;
+  c->host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0)
+                   .count();
   return SPARC_OK;
 }
 
@@ -819,6 +908,12 @@ int sparc_get_timings(sparc_handle c, sparc_timings* t) {
   t->rotate_ms = ms[5];
   CK(c, cudaEventElapsedTime(&t->total_ms, c->ev[0], c->ev[6]));
   t->launches = c->step_launches;
+  t->stage_in_ms = t->stage_out_ms = 0.0f;
+  if (c->staged) {
+    CK(c, cudaEventElapsedTime(&t->stage_in_ms, c->ev_stage[0], c->ev_stage[1]));
+    CK(c, cudaEventElapsedTime(&t->stage_out_ms, c->ev_stage[2], c->ev_stage[3]));
+  }
+  t->host_ms = (float)c->host_ms;
   return SPARC_OK;
 }
 

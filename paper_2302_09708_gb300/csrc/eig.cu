@@ -388,7 +388,6 @@ __global__ void __launch_bounds__(256)
 // scal[2] = pivmin.
 // ---------------------------------------------------------------------------
 __global__ void k_gersh(const double* d, const double* e, int n, double* e2, double* scal) {
-  __shared__ double sh[32];
   double lo = 1e300, hi = -1e300, emax = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
@@ -418,7 +417,6 @@ __global__ void k_gersh(const double* d, const double* e, int n, double* e2, dou
     scal[2] = fmax(2.2250738585072014e-308 * fmax(1.0, emax), 1e-300);
     scal[3] = tnorm;
   }
-  (void)sh;
 }
 
 __device__ int sturm(const double* __restrict__ d, const double* __restrict__ e2, int n,

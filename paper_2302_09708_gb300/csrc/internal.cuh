@@ -268,7 +268,10 @@ struct sparc_context {
   double prev_max = 0.0;
   // timings
   cudaEvent_t ev[7] = {};
+  cudaEvent_t ev_stage[4] = {};  // host-buffer staging: in start/end, out start/end
   bool timed = false;
+  bool staged = false;           // the last step staged a host block
+  double host_ms = 0.0;          // wall time of the last sparc_chefsi_step call
   long long step_launches = 0;
   bool ring_enabled = true;  // TMA-ring stencil (options.reserved[0] bit 0 turns it off)
   bool tc_gemm = true;       // tensor-core projection/rotation (FP64: reserved[0] bit 1 off)

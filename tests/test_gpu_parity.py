@@ -318,6 +318,17 @@ def test_chefsi_step_host_buffer_and_determinism():
     Xh = X0.copy()
     lamh = h.chefsi_step(Xh, 10, bounds=(a, b, a0))
     assert np.array_equal(Xh, outs[0][0]) and np.array_equal(lamh, outs[0][1])
+    # a page-locked block from the library's host allocator
+    Xp = sparc.host_empty(X0.shape)
+    Xp[:] = X0
+    lamp = h.chefsi_step(Xp, 10, bounds=(a, b, a0))
+    assert np.array_equal(Xp, outs[0][0]) and np.array_equal(lamp, outs[0][1])
+    t = h.timings()
+    assert t["stage_in_ms"] > 0 and t["stage_out_ms"] > 0 and t["host_ms"] >= t["total_ms"] * 0.999
+    Xd = to_dev(X0)
+    h.chefsi_step(Xd, 10, bounds=(a, b, a0))
+    t = h.timings()
+    assert t["stage_in_ms"] == 0 and t["stage_out_ms"] == 0 and t["host_ms"] > 0
 
 
 def test_invalid_arguments():
