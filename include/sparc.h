@@ -285,10 +285,14 @@ int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step);
  * blocks that are staged through sparc_chefsi_step / sparc_cheb_filter (not a
  * step of the method; a host-side convenience).  The block comes from an
  * anonymous private mapping, 2 MiB aligned, hinted for transparent huge pages
- * and registered with cudaHostRegister (portable).  Host blocks pinned this way
- * keep the full copy-engine rate across steps; on Grace-Blackwell systems,
- * blocks from cudaHostAlloc were measured to drop to a fifth or less of it for
- * the first pass after a step that streams hundreds of GB through HBM.
+ * and registered with cudaHostRegister (portable).  Measured on a
+ * Grace-Blackwell node (9.2 GB block, one 96^3 FP64 handle with Ns = 1300
+ * holding ~55 GB of device memory): 190-210 GB/s each way, also on the first
+ * copy after a step, where blocks from cudaHostAlloc fell to 20-45 GB/s.  With
+ * a second such handle alive (~120 GB of device memory) the same registered
+ * block fell to ~10 GB/s even without steps, while cudaHostAlloc blocks kept
+ * 190 GB/s between steps; prefer cudaHostAlloc memory in processes that hold
+ * several large handles.
  * bytes > 0; *out receives the block (uninitialised) or NULL on error.
  * sparc_host_free takes a pointer from sparc_host_alloc (NULL is a no-op) and
  * must not be called while a copy from or to the block is in flight.
