@@ -281,29 +281,6 @@ int sparc_batch_chefsi_step(sparc_batch b, void* const* X, const int* ns, const 
 int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step);
 
 /*
- * sparc_host_alloc / sparc_host_free — page-locked host memory for orbital
- * blocks that are staged through sparc_chefsi_step / sparc_cheb_filter (not a
- * step of the method; a host-side convenience).  The block comes from an
- * anonymous private mapping, 2 MiB aligned, hinted for transparent huge pages
- * and registered with cudaHostRegister (portable).  Measured on a
- * Grace-Blackwell node (9.2 GB block, one 96^3 FP64 handle with Ns = 1300
- * holding ~55 GB of device memory): 190-210 GB/s each way, also on the first
- * copy after a step, where blocks from cudaHostAlloc fell to 20-45 GB/s.  With
- * a second such handle alive (~120 GB of device memory) the same registered
- * block fell to ~10 GB/s even without steps, while cudaHostAlloc blocks kept
- * 190 GB/s between steps; prefer cudaHostAlloc memory in processes that hold
- * several large handles.
- * bytes > 0; *out receives the block (uninitialised) or NULL on error.
- * sparc_host_free takes a pointer from sparc_host_alloc (NULL is a no-op) and
- * must not be called while a copy from or to the block is in flight.
- * Thread-safe.  Errors: INVALID_ARG (bytes == 0, out NULL, unknown pointer),
- * OOM (mmap failed), CUDA (registration failed, e.g. no device); the message
- * is available from sparc_last_error(NULL).
- */
-int sparc_host_alloc(size_t bytes, void** out);
-int sparc_host_free(void* p);
-
-/*
  * sparc_project_noalloc — the FP64 projection of sparc_project (Hs = Xt^T Yt,
  * Ms = Xt^T Xt) on the FP64 SIMT pipe (the form FP64 handles use when created
  * with sparc_options.reserved[0] bit 1), without a handle and without

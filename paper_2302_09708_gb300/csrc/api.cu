@@ -7,12 +7,9 @@
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
-#include <sys/mman.h>
 
 #include <algorithm>
 #include <atomic>
-#include <map>
-#include <mutex>
 #include <chrono>
 #include <type_traits>
 #include <string>
@@ -634,79 +631,6 @@ int sparc_destroy(sparc_handle h) {
   if (!h) return SPARC_OK;
   cudaSetDevice(h->device);
   destroy_ctx(h);
-  return SPARC_OK;
-}
-
-// Page-locked host blocks: an anonymous private mapping (2 MiB aligned, with a
-// transparent-huge-page hint) registered with CUDA.  Kept in a registry so
-// that sparc_host_free can find the mapping's base and length.
-namespace {
-struct HostMapping {
-  void* base;
-  size_t len;
-};
-std::mutex g_host_mu;
-std::map<void*, HostMapping> g_host_maps;
-}  // namespace
-
-int sparc_host_alloc(size_t bytes, void** out) {
-  if (!out) {
-    g_create_err = "invalid argument: out is NULL";
-    return SPARC_ERR_INVALID_ARG;
-  }
-  *out = nullptr;
-  if (bytes == 0) {
-    g_create_err = "invalid argument: bytes must be > 0";
-    return SPARC_ERR_INVALID_ARG;
-  }
-  const size_t align = size_t(2) << 20;
-  if (bytes > SIZE_MAX - 2 * align) {
-    g_create_err = "invalid argument: bytes too large";
-    return SPARC_ERR_INVALID_ARG;
-  }
-  const size_t len = bytes + align;
-  void* base = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
-  if (base == MAP_FAILED) {
-    g_create_err = "mmap of the host block failed";
-    return SPARC_ERR_OOM;
-  }
-  char* p = (char*)(((uintptr_t)base + align - 1) & ~(uintptr_t)(align - 1));
-#ifdef MADV_HUGEPAGE
-  madvise(p, bytes, MADV_HUGEPAGE);  // a hint: failure leaves ordinary pages
-#endif
-  cudaError_t e = cudaHostRegister(p, bytes, cudaHostRegisterPortable);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    munmap(base, len);
-    g_create_err = std::string("cudaHostRegister: ") + cudaGetErrorString(e);
-    return SPARC_ERR_CUDA;
-  }
-  std::lock_guard<std::mutex> lk(g_host_mu);
-  g_host_maps[p] = HostMapping{base, len};
-  *out = p;
-  return SPARC_OK;
-}
-
-int sparc_host_free(void* p) {
-  if (!p) return SPARC_OK;
-  HostMapping m;
-  {
-    std::lock_guard<std::mutex> lk(g_host_mu);
-    auto it = g_host_maps.find(p);
-    if (it == g_host_maps.end()) {
-      g_create_err = "invalid argument: pointer was not returned by sparc_host_alloc";
-      return SPARC_ERR_INVALID_ARG;
-    }
-    m = it->second;
-    g_host_maps.erase(it);
-  }
-  cudaError_t e = cudaHostUnregister(p);
-  munmap(m.base, m.len);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    g_create_err = std::string("cudaHostUnregister: ") + cudaGetErrorString(e);
-    return SPARC_ERR_CUDA;
-  }
   return SPARC_OK;
 }
 

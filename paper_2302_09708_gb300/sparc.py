@@ -68,7 +68,7 @@ class sparc_timings(ctypes.Structure):
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_hpsi",
            "sparc_spectrum_bounds", "sparc_cheb_filter", "sparc_project", "sparc_subspace_eig",
            "sparc_rotate", "sparc_chefsi_step", "sparc_get_timings", "sparc_project_noalloc",
-           "sparc_occupations", "sparc_density", "sparc_host_alloc", "sparc_host_free",
+           "sparc_occupations", "sparc_density",
            "sparc_batch_create", "sparc_batch_destroy", "sparc_batch_last_error",
            "sparc_batch_chefsi_step", "sparc_batch_get_info"]
 
@@ -106,8 +106,6 @@ def load(build: bool = True):
     L.sparc_project_noalloc.argtypes = [vp, vp, i, i64, i64, vp, vp, vp]
     L.sparc_occupations.argtypes = [vp, vp, i, d, d, vp, vp, vp]
     L.sparc_density.argtypes = [vp, vp, i, i64, i, vp, vp, vp]
-    L.sparc_host_alloc.argtypes = [ctypes.c_size_t, ctypes.POINTER(vp)]
-    L.sparc_host_free.argtypes = [vp]
     L.sparc_batch_create.argtypes = [vp, i, ctypes.POINTER(vp)]
     L.sparc_batch_destroy.argtypes = [vp]
     L.sparc_batch_last_error.argtypes = [vp]
@@ -266,41 +264,6 @@ def sparc_get_timings(h):
     t = sparc_timings()
     _check(h, load().sparc_get_timings(h, ctypes.byref(t)))
     return {n: getattr(t, n) for n, _ in sparc_timings._fields_}
-
-
-class HostBuffer:
-    """A page-locked host allocation from sparc_host_alloc, freed on close or
-    garbage collection."""
-
-    def __init__(self, nbytes):
-        ptr = ctypes.c_void_p()
-        rc = load().sparc_host_alloc(ctypes.c_size_t(nbytes), ctypes.byref(ptr))
-        if rc != SPARC_OK:
-            raise SparcError(rc, load().sparc_last_error(None).decode())
-        self.ptr, self.nbytes = ptr.value, nbytes
-
-    def close(self):
-        if self.ptr:
-            load().sparc_host_free(ctypes.c_void_p(self.ptr))
-            self.ptr = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
-
-
-def host_empty(shape, dtype=np.float64):
-    """An uninitialised C-ordered numpy array in page-locked host memory
-    (sparc_host_alloc), e.g. an (ns, ld) orbital block to stage through
-    chefsi_step.  The allocation lives as long as the array."""
-    dtype = np.dtype(dtype)
-    n = int(np.prod(shape)) * dtype.itemsize
-    buf = HostBuffer(max(n, 1))
-    raw = (ctypes.c_char * max(n, 1)).from_address(buf.ptr)
-    raw.owner = buf  # the ctypes array keeps the allocation alive
-    return np.frombuffer(raw, dtype=dtype, count=int(np.prod(shape))).reshape(shape)
 
 
 class Handle:

@@ -58,13 +58,3 @@ def test_create_rejects_bad_grid_without_gpu():
 def test_destroy_null_is_noop():
     assert sparc.load().sparc_destroy(None) == sparc.SPARC_OK
 
-
-def test_host_alloc_rejects_bad_arguments_without_gpu():
-    L = sparc.load()
-    out = ctypes.c_void_p(1)
-    assert L.sparc_host_alloc(ctypes.c_size_t(0), ctypes.byref(out)) == sparc.SPARC_ERR_INVALID_ARG
-    assert out.value is None
-    assert L.sparc_host_alloc(ctypes.c_size_t(64), None) == sparc.SPARC_ERR_INVALID_ARG
-    assert L.sparc_host_free(None) == sparc.SPARC_OK
-    assert L.sparc_host_free(ctypes.c_void_p(0x1000)) == sparc.SPARC_ERR_INVALID_ARG
-    assert b"sparc_host_alloc" in L.sparc_last_error(None)

@@ -318,9 +318,8 @@ def test_chefsi_step_host_buffer_and_determinism():
     Xh = X0.copy()
     lamh = h.chefsi_step(Xh, 10, bounds=(a, b, a0))
     assert np.array_equal(Xh, outs[0][0]) and np.array_equal(lamh, outs[0][1])
-    # a page-locked block from the library's host allocator
-    Xp = sparc.host_empty(X0.shape)
-    Xp[:] = X0
+    # a page-locked host block (torch pinned memory)
+    Xp = torch.from_numpy(X0.copy()).pin_memory().numpy()
     lamp = h.chefsi_step(Xp, 10, bounds=(a, b, a0))
     assert np.array_equal(Xp, outs[0][0]) and np.array_equal(lamp, outs[0][1])
     t = h.timings()
