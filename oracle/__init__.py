@@ -13,6 +13,10 @@ Chebyshev scalar identity, extremal free-electron eigenvalues for Lanczos,
 scipy's generalised eigensolver, and convergence of repeated steps to the exact
 lowest eigenpairs.  The occupation/density step is pinned by its sum rule and
 by the zero-temperature limit.
+
+``oracle/kpoint.py`` holds the complex form of the step at a Bloch wavevector
+k (numpy complex128, same restrictions), with its own pins in
+``tests/test_oracle_kpoint.py``.
 """
 from __future__ import annotations
 
