@@ -16,7 +16,8 @@ by the zero-temperature limit.
 
 ``oracle/kpoint.py`` holds the complex form of the step at a Bloch wavevector
 k (numpy complex128, same restrictions), with its own pins in
-``tests/test_oracle_kpoint.py``.
+``tests/test_oracle_kpoint.py``; ``oracle/forces.py`` the nonlocal
+Hellmann-Feynman forces on the atoms (pins in ``tests/test_oracle_forces.py``).
 """
 from __future__ import annotations
 

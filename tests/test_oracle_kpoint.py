@@ -11,6 +11,7 @@ import pytest
 import scipy.linalg as sl
 
 import oracle
+from analytic import analytic_projectors
 from oracle import kpoint
 from paper_2302_09708_gb300 import synth
 
@@ -47,40 +48,6 @@ def bloch_fd1d(n, periodic, kL):
     return A
 
 
-def analytic_bloch_projectors(s, k):
-    """Each atom's projectors rebuilt from their analytic form, g_0 Y_00 and
-    g_1 Y_1m (m-order y, z, x) with g = exp(-r^2 / 2 sigma^2) and a cut-off at
-    RC. The Bloch sum runs over the 27 nearest lattice images with weights
-    exp(i k.T), and each is normalised to h^3 sum |chi|^2 = 1 (the phases have
-    modulus one). Returns a list of (Nd x 4 matrix, gammas) per atom."""
-    nx, ny, nz = s.shape
-    L = np.array(s.shape, dtype=np.float64) * s.h
-    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    r = np.stack([ix.ravel() * s.h, iy.ravel() * s.h, iz.ravel() * s.h], axis=1)
-    out = []
-    y00, y1 = 0.5 / math.sqrt(math.pi), math.sqrt(3.0 / (4.0 * math.pi))
-    for J in range(s.natoms):
-        real = np.zeros((s.nd, 4))
-        bloch = np.zeros((s.nd, 4), dtype=np.complex128)
-        for tx in (-1, 0, 1):
-            for ty in (-1, 0, 1):
-                for tz in (-1, 0, 1):
-                    t = np.array([tx, ty, tz], dtype=np.float64)
-                    if any(t[d] != 0 and s.bc[d] != P for d in range(3)):
-                        continue
-                    T = t * L
-                    dvec = r - s.positions[J] - T
-                    r2 = np.sum(dvec * dvec, axis=1)
-                    g = np.where(r2 <= synth.RC ** 2, np.exp(-r2 / (2 * synth.SIGMA ** 2)), 0.0)
-                    cols = np.stack([g * y00, g * y1 * dvec[:, 1], g * y1 * dvec[:, 2],
-                                     g * y1 * dvec[:, 0]], axis=1)
-                    real += cols
-                    bloch += cols * np.exp(1j * float(k @ T))
-        norm = np.sqrt(s.h ** 3 * np.sum(real * real, axis=0))
-        out.append((bloch / norm[None, :], s.gamma[int(s.proj_ptr[J]):int(s.proj_ptr[J + 1])]))
-    return out
-
-
 def dense_hk(s, k):
     """H(k) assembled independently: Kronecker sum of 1-D Bloch FD matrices,
     diag(Veff) and explicit projector outer products."""
@@ -92,7 +59,7 @@ def dense_hk(s, k):
     lap = (np.kron(Iz, np.kron(Iy, Ax)) + np.kron(Iz, np.kron(Ay, Ix))
            + np.kron(Az, np.kron(Iy, Ix)))
     H = -0.5 / s.h ** 2 * lap + np.diag(s.veff)
-    for phi, gam in analytic_bloch_projectors(s, k):
+    for phi, gam in analytic_projectors(s, k):
         H += s.h ** 3 * (phi * gam[None, :]) @ phi.conj().T
     return H
 
