@@ -242,6 +242,26 @@ int sparc_density(sparc_handle h, const void* X, int ns, int64_t ld, int dtype, 
                   double* rho, void* stream);
 
 /*
+ * sparc_nonlocal_forces — nonlocal Hellmann-Feynman forces on the atoms (the
+ * force kernels the paper runs on the GPU beside the filter, Sec. III: the
+ * gradient of the orbitals, then the nonlocal projectors applied to it):
+ *   F_Jd = -4 sum_n occ_n sum_p gamma_Jp (h^3 <chi_Jp|X_n>) (h^3 <chi_Jp|D_d X_n>),
+ * for real orbitals with spin degeneracy 2, with D_d the radius-6 central first
+ * derivative along axis d (x, y, z) under the grid's boundary conditions.
+ * - X: device block (dtype of the handle, ld >= Nd, 0 <= ns <= ns_max).
+ * - occ: ns device doubles.
+ * - F: 3 * natoms device doubles (output), atom-major (F[3 J + d]) in Ha/bohr.
+ *   ns = 0 gives F = 0; a handle without atoms returns at once and F may be
+ *   NULL.
+ * Arithmetic is FP64 for both dtypes (FP32 blocks are widened on load), with a
+ * fixed summation order: results are deterministic. The handle's filter
+ * workspace is scratch and must hold natoms * ns * 3 doubles (else
+ * INVALID_ARG). Errors: INVALID_ARG, CUDA.  Asynchronous.
+ */
+int sparc_nonlocal_forces(sparc_handle h, const void* X, int ns, int64_t ld, int dtype,
+                          const double* occ, double* F, void* stream);
+
+/*
  * Batched form — many independent systems (the paper treats the eigenproblems
  * of different k-points / spins / configurations as independent, Sec. II).
  * A batch is built from existing handles (same precision and device; each keeps

@@ -818,6 +818,32 @@ int sparc_density(sparc_handle c, const void* X, int ns, int64_t ld, int dtype, 
   return SPARC_OK;
 }
 
+int sparc_nonlocal_forces(sparc_handle c, const void* X, int ns, int64_t ld, int dtype,
+                          const double* occ, double* F, void* stream) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  ARG(c, ns >= 0 && ns <= c->ns_max, "ns must be in [0, ns_max]");
+  ARG(c, ld >= c->nd, "ld must be >= Nd");
+  const int want = c->precision == SPARC_PREC_MIXED ? SPARC_F32 : SPARC_F64;
+  ARG(c, dtype == want, "dtype must match the handle's precision");
+  const int natoms = c->nl64.natoms;
+  if (natoms == 0) return SPARC_OK;
+  ARG(c, F != nullptr && is_device_ptr(F), "F must be a device array");
+  ARG(c, ns == 0 || (X && occ && is_device_ptr(X) && is_device_ptr(occ)),
+      "X and occ must be device arrays");
+  // scratch: the W1 filter buffer holds natoms x ns x 3 doubles
+  const int64_t work_doubles = c->ld * (int64_t)c->ns_max * (int64_t)elem_size(want) / 8;
+  ARG(c, (int64_t)natoms * 3 * ns <= work_doubles, "too many atoms for the handle's workspace");
+  CK(c, cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == SPARC_F64)
+    CK(c, nonlocal_forces<double>(c->grid, c->h, c->nl64, (const double*)X, ld, ns, occ, F,
+                                  (double*)c->W1, st));
+  else
+    CK(c, nonlocal_forces<float>(c->grid, c->h, c->nl64, (const float*)X, ld, ns, occ, F,
+                                 (double*)c->W1, st));
+  return SPARC_OK;
+}
+
 int sparc_get_timings(sparc_handle c, sparc_timings* t) {
   if (!c || !t) return SPARC_ERR_INVALID_ARG;
   ARG(c, c->timed, "no step has run on this handle");

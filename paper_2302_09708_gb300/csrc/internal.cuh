@@ -158,6 +158,12 @@ cudaError_t tc_rotate(const double* Xt, int64_t ld, int64_t nd, int ns, const do
 // density.cu: Fermi occupations (one block) and rho = (2/h^3) sum f_n x_n^2.
 cudaError_t fermi_occupations(const double* lam, int ns, double ne, double kT, double* occ,
                               double* mu, cudaStream_t st);
+// Nonlocal forces F (natoms x 3 doubles) of the orbitals X (forces.cu); `part`
+// is scratch of natoms * ns * 3 doubles.
+template <typename T>
+cudaError_t nonlocal_forces(const Grid& g, double h, const Nonlocal<double>& nl, const T* X,
+                            int64_t ld, int ns, const double* occ, double* F, double* part,
+                            cudaStream_t st);
 cudaError_t density(const void* X, int64_t ld, int64_t nd, int ns, bool fp32, const double* occ,
                     double h, double* rho, double* work, int64_t work_elems, cudaStream_t st);
 // Xout = Xt Z (Z column-major ns x ns)

@@ -68,7 +68,7 @@ class sparc_timings(ctypes.Structure):
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_hpsi",
            "sparc_spectrum_bounds", "sparc_cheb_filter", "sparc_project", "sparc_subspace_eig",
            "sparc_rotate", "sparc_chefsi_step", "sparc_get_timings", "sparc_project_noalloc",
-           "sparc_occupations", "sparc_density",
+           "sparc_occupations", "sparc_density", "sparc_nonlocal_forces",
            "sparc_batch_create", "sparc_batch_destroy", "sparc_batch_last_error",
            "sparc_batch_chefsi_step", "sparc_batch_get_info"]
 
@@ -106,6 +106,7 @@ def load(build: bool = True):
     L.sparc_project_noalloc.argtypes = [vp, vp, i, i64, i64, vp, vp, vp]
     L.sparc_occupations.argtypes = [vp, vp, i, d, d, vp, vp, vp]
     L.sparc_density.argtypes = [vp, vp, i, i64, i, vp, vp, vp]
+    L.sparc_nonlocal_forces.argtypes = [vp, vp, i, i64, i, vp, vp, vp]
     L.sparc_batch_create.argtypes = [vp, i, ctypes.POINTER(vp)]
     L.sparc_batch_destroy.argtypes = [vp]
     L.sparc_batch_last_error.argtypes = [vp]
@@ -260,6 +261,15 @@ def sparc_density(h, X, occ, rho, stream=None):
     return rho
 
 
+def sparc_nonlocal_forces(h, X, occ, F, stream=None):
+    """Nonlocal forces of the block X with occupations `occ` into the device
+    tensor F (natoms x 3 doubles)."""
+    px, ns, ld, dt = _block(X)
+    _check(h, load().sparc_nonlocal_forces(h, px, ns, ld, dt, occ.data_ptr(), F.data_ptr(),
+                                           _stream(stream)))
+    return F
+
+
 def sparc_get_timings(h):
     t = sparc_timings()
     _check(h, load().sparc_get_timings(h, ctypes.byref(t)))
@@ -343,6 +353,13 @@ class Handle:
         import torch
         rho = torch.empty(self.system.nd, dtype=torch.float64, device=X.device)
         return sparc_density(self.h, X, occ, rho, stream)
+
+    def nonlocal_forces(self, X, occ, stream=None):
+        """F (device, natoms x 3 doubles, Ha/bohr) of the block X with occupations `occ`."""
+        import torch
+        F = torch.zeros((max(self.system.natoms, 1), 3), dtype=torch.float64, device=X.device)
+        sparc_nonlocal_forces(self.h, X, occ, F, stream)
+        return F[: self.system.natoms]
 
     def timings(self):
         return sparc_get_timings(self.h)
