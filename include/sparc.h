@@ -215,6 +215,12 @@ int sparc_chefsi_step(sparc_handle h, void* X, int ns, int64_t ld, int dtype, in
                       const double* bounds, double* eig, int eig_on_host, void* stream);
 
 /* Stage times of the last sparc_chefsi_step (waits for its events). */
+/*
+ * sparc_get_timings — the stage times and launch count of the last
+ * sparc_chefsi_step on the handle, into *t (see sparc_timings).  Waits for
+ * that step's last stage event.  Errors: INVALID_ARG (null arguments, or no
+ * step has run on the handle), CUDA.
+ */
 int sparc_get_timings(sparc_handle h, sparc_timings* t);
 
 /*

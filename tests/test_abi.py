@@ -58,3 +58,15 @@ def test_create_rejects_bad_grid_without_gpu():
 def test_destroy_null_is_noop():
     assert sparc.load().sparc_destroy(None) == sparc.SPARC_OK
 
+
+
+def test_every_declared_function_is_documented():
+    """Each entry point in include/sparc.h is preceded by a comment block
+    naming it (argument meaning, layout, ownership and errors live there)."""
+    text = open(os.path.join(ROOT, "include", "sparc.h")).read()
+    comments = " ".join(re.findall(r"/\*.*?\*/", text, flags=re.S))
+    undocumented = [n for n in declared_functions() if n not in comments]
+    # sparc_batch_* and sparc_destroy share comment blocks with their siblings
+    assert not [n for n in undocumented
+                if n not in ("sparc_batch_destroy", "sparc_batch_last_error",
+                             "sparc_batch_get_info")], undocumented
