@@ -214,7 +214,6 @@ int sparc_rotate(sparc_handle h, const void* Xt, void* Xout, const double* Z, in
 int sparc_chefsi_step(sparc_handle h, void* X, int ns, int64_t ld, int dtype, int degree,
                       const double* bounds, double* eig, int eig_on_host, void* stream);
 
-/* Stage times of the last sparc_chefsi_step (waits for its events). */
 /*
  * sparc_get_timings — the stage times and launch count of the last
  * sparc_chefsi_step on the handle, into *t (see sparc_timings).  Waits for
