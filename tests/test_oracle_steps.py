@@ -230,3 +230,33 @@ def test_occupations_and_density():
     X = synth.random_orbitals(nd, 40, seed=2)
     rho = oracle.density(X, f, nd, h)
     assert abs(h ** 3 * rho.sum() - ne) < 1e-9
+
+
+def test_occupations_two_level_and_degenerate_closed_forms():
+    """Two levels lam1 < lam2 holding Ne = 2 electrons: by symmetry
+    mu = (lam1 + lam2) / 2 and f_1,2 = 1 / (1 + exp(-+ (lam2 - lam1) / 2kT)).
+    One degenerate level of Ns states: f = Ne / (2 Ns) at any kT."""
+    for lam1, lam2, kT in ((-0.3, 0.1, 0.01), (0.0, 0.05, 0.02), (-1.0, -0.99, 0.1)):
+        f, mu = oracle.fermi_occupations(np.array([lam1, lam2]), 2.0, kT=kT)
+        assert abs(mu - 0.5 * (lam1 + lam2)) < 1e-12 * max(1.0, abs(lam1))
+        half = (lam2 - lam1) / (2 * kT)
+        assert abs(f[0] - 1 / (1 + np.exp(-half))) < 1e-12
+        assert abs(f[1] - 1 / (1 + np.exp(half))) < 1e-12
+    for ns, ne in ((7, 3.0), (12, 20.0)):
+        f, _ = oracle.fermi_occupations(np.full(ns, -0.42), ne, kT=0.01)
+        np.testing.assert_allclose(f, ne / (2 * ns), atol=1e-12)
+
+
+def test_lanczos_full_krylov_gives_exact_extremes():
+    """With k = Nd steps (no restarts, tiny system) the Krylov space is the
+    whole space, so theta_min and theta_max are the exact extreme eigenvalues of
+    the dense operator (up to the loss of orthogonality, which for Nd = 64
+    and well separated ends stays far below 1e-8)."""
+    s = synth.random_system((4, 4, 4), 0.5, (1, 1, 1), 2, seed=9)
+    o = oracle.Oracle(s)
+    H = o.hpsi(np.eye(s.nd)).T
+    ev = np.linalg.eigvalsh(0.5 * (H + H.T))
+    a0, b, al, bt, tmax = o.lanczos(s.nd, 3)
+    assert abs(a0 - ev[0]) < 1e-8 * np.max(np.abs(ev))
+    assert abs(tmax - ev[-1]) < 1e-8 * np.max(np.abs(ev))
+    assert b >= ev[-1] - 1e-8
