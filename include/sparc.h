@@ -25,11 +25,14 @@
  *    call says "device or host", a host pointer is copied through a library
  *    buffer inside the call.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
- *    enqueued on it; calls return without waiting unless stated.  Kernels that
- *    wait on barriers bound every wait; if one runs out the kernel stops and
- *    records SPARC_ERR_TIMEOUT, which the next synchronous call on the handle
- *    (sparc_chefsi_step, sparc_subspace_eig, mixed-precision sparc_project /
- *    sparc_rotate) returns.
+ *    enqueued on it; calls return without waiting unless stated.  The calls
+ *    that wait for the stream before returning are sparc_spectrum_bounds,
+ *    sparc_chefsi_step, sparc_subspace_eig, sparc_batch_chefsi_step, the
+ *    calls given a host block, and sparc_project / sparc_rotate whenever they
+ *    run the tensor-core form (every mixed handle, and FP64 handles without
+ *    options flag bit 1).  Kernels that wait on barriers bound every wait; if
+ *    one runs out the kernel stops and records SPARC_ERR_TIMEOUT, which the
+ *    next of those waiting calls on the handle returns.
  *  - All inputs given at create time are copied; the caller may free them.
  *  - The library owns its workspace (two Nd x ns_max blocks of the working
  *    precision plus the Ns x Ns subspace buffers), sized at create time.
@@ -175,7 +178,9 @@ int sparc_cheb_filter(sparc_handle h, void* X, int ns, int64_t ld, int dtype, in
 /*
  * sparc_project — Hs = Xt^T Yt and Ms = Xt^T Xt (Algorithm 1, projection).
  * Xt, Yt: device blocks (dtype, ld).  Hs, Ms: device ns x ns FP64 column-major
- * outputs.  Both are symmetrised from their upper triangles.  Asynchronous.
+ * outputs.  Both are symmetrised from their upper triangles.  Asynchronous on
+ * the FP64 SIMT form; the tensor-core form waits for the stream and returns
+ * TIMEOUT if one of its bounded waits ran out.
  */
 int sparc_project(sparc_handle h, const void* Xt, const void* Yt, int ns, int64_t ld,
                   int dtype, double* Hs, double* Ms, void* stream);
@@ -195,7 +200,8 @@ int sparc_subspace_eig(sparc_handle h, const double* Hs, const double* Ms, int n
 /*
  * sparc_rotate — Xout = Xt Z (Algorithm 1, rotation).  Xt, Xout: device
  * blocks (dtype, ld), not overlapping.  Z: device ns x ns FP64 column-major.
- * Asynchronous.
+ * Asynchronous on the FP64 SIMT form; the tensor-core form waits for the
+ * stream, as sparc_project does.
  */
 int sparc_rotate(sparc_handle h, const void* Xt, void* Xout, const double* Z, int ns, int64_t ld,
                  int dtype, void* stream);
@@ -207,9 +213,11 @@ int sparc_rotate(sparc_handle h, const void* Xt, void* Xout, const double* Z, in
  * 32-step Lanczos run (seed 0) made on the first such call, and a is the
  * largest Ritz value of the previous step on this handle (first step:
  * a0 + 0.1 (b - a0)).  eig: ns Ritz values, ascending, written to host memory
- * if eig_on_host is nonzero (the call then waits for the stream), else to
- * device memory (may be NULL).  X: device or host block.
- * Errors: INVALID_ARG, NOT_SPD, NUMERIC, CUDA, OOM.
+ * if eig_on_host is nonzero, else to device memory (may be NULL).  X: device
+ * or host block.  Synchronous: the call waits for the stream at its end, to
+ * read the status word of the step's kernels and the largest Ritz value (the
+ * next step's cut-off).  Errors: INVALID_ARG, NOT_SPD, NUMERIC, TIMEOUT, CUDA,
+ * OOM.
  */
 int sparc_chefsi_step(sparc_handle h, void* X, int ns, int64_t ld, int dtype, int degree,
                       const double* bounds, double* eig, int eig_on_host, void* stream);
@@ -326,8 +334,12 @@ int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step);
  * library holds until the process exits.  ns may be at most 1448 (two ns x ns
  * partials must fit); larger ns returns INVALID_ARG without launching work.
  * The first call on a device looks up that array's device address (once per
- * device, with that device current); make that first call before any CUDA
- * stream capture.  All calls share the array and it keeps the last call's
+ * device, with that device current) and keeps it for the life of the process;
+ * make that first call before any CUDA stream capture.  A cudaDeviceReset
+ * invalidates the kept address: do not call this entry point on a device
+ * after resetting it.  Xt, Yt, Hs and Ms must be memory of the current
+ * device (or managed memory); a pointer to another GPU's memory returns
+ * INVALID_ARG.  All calls share the array and it keeps the last call's
  * contents; every value a call reads from it is written earlier by the same
  * call, so nothing needs clearing, but calls that overlap on the GPU (for
  * example on two streams at once) race on it and must be serialised by the

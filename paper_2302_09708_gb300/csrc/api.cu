@@ -35,6 +35,38 @@ thread_local std::string g_create_err;
 void sparc::set_global_error(const std::string& msg) { g_create_err = msg; }
 
 namespace {
+constexpr int kMaxDev = 64;
+std::atomic<int> g_sms[kMaxDev];
+}  // namespace
+
+int sparc::sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+  int v = g_sms[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  g_sms[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+cudaError_t sparc::smem_limit_once(unsigned long long* bits, const void* func, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev)
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const unsigned long long bit = 1ull << dev;
+  auto* word = reinterpret_cast<std::atomic<unsigned long long>*>(bits);
+  if (word->load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) word->fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
+namespace {
 
 // 12th-order central second-derivative weights (Fornberg 1988, radius 6):
 // w0 = -5369/1800, w1..w6 = 12/7, -15/56, 10/189, -1/112, 2/1925, -1/16632.
@@ -74,10 +106,13 @@ int cuda_status(cudaError_t e) {
 
 size_t elem_size(int dtype) { return dtype == SPARC_F32 ? 4 : 8; }
 
+// Device or managed memory.  A failed attribute query (an unregistered host
+// pointer) clears only the error it raised, never one left pending before it.
 bool is_device_ptr(const void* p) {
+  const cudaError_t pending = cudaPeekAtLastError();
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
+    if (pending == cudaSuccess) cudaGetLastError();
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
@@ -705,11 +740,15 @@ int sparc_project(sparc_handle c, const void* Xt, const void* Yt, int ns, int64_
   ARG(c, Yt && Hs && Ms, "null argument");
   CK(c, cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
+  // the tensor-core form's bounded waits report through the status word, which
+  // this call then reads (synchronously); the FP64 SIMT form has no waits
+  if (c->tc_gemm) CK(c, cudaMemsetAsync(c->eig.status, 0, 3 * sizeof(int), st));
   if (dtype == SPARC_F64)
-    return do_project<double>(c, (const double*)Xt, ld, (const double*)Yt, ld, ns, Hs, Ms, st);
-  CK(c, cudaMemsetAsync(c->eig.status, 0, 3 * sizeof(int), st));
-  rc = do_project<float>(c, (const float*)Xt, ld, (const float*)Yt, ld, ns, Hs, Ms, st);
-  return rc ? rc : read_status(c, st);
+    rc = do_project<double>(c, (const double*)Xt, ld, (const double*)Yt, ld, ns, Hs, Ms, st);
+  else
+    rc = do_project<float>(c, (const float*)Xt, ld, (const float*)Yt, ld, ns, Hs, Ms, st);
+  if (rc) return rc;
+  return c->tc_gemm ? read_status(c, st) : SPARC_OK;
 }
 
 int sparc_subspace_eig(sparc_handle c, const double* Hs, const double* Ms, int ns, double* lam,
@@ -731,11 +770,13 @@ int sparc_rotate(sparc_handle c, const void* Xt, void* Xout, const double* Z, in
   ARG(c, Xout && Z && Xout != Xt, "Xout must be non-null and distinct from Xt");
   CK(c, cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->tc_gemm) CK(c, cudaMemsetAsync(c->eig.status, 0, 3 * sizeof(int), st));
   if (dtype == SPARC_F64)
-    return do_rotate<double>(c, (const double*)Xt, ld, ns, Z, (double*)Xout, ld, st);
-  CK(c, cudaMemsetAsync(c->eig.status, 0, 3 * sizeof(int), st));
-  rc = do_rotate<float>(c, (const float*)Xt, ld, ns, Z, (float*)Xout, ld, st);
-  return rc ? rc : read_status(c, st);
+    rc = do_rotate<double>(c, (const double*)Xt, ld, ns, Z, (double*)Xout, ld, st);
+  else
+    rc = do_rotate<float>(c, (const float*)Xt, ld, ns, Z, (float*)Xout, ld, st);
+  if (rc) return rc;
+  return c->tc_gemm ? read_status(c, st) : SPARC_OK;
 }
 
 int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, int degree,

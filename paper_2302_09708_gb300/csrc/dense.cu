@@ -172,7 +172,7 @@ int project_nsplit(int64_t nd, int ns) {
   // ~8 waves of the 3-CTA-per-SM residency so the last wave's tail is small
   int nb = (ns + kT - 1) / kT;
   int64_t tiles = (int64_t)nb * (nb + 1) / 2;
-  int64_t want = (8 * 3 * 152 + tiles - 1) / tiles;
+  int64_t want = (8 * 3 * sm_count() + tiles - 1) / tiles;
   int64_t maxk = (nd + 1023) / 1024;  // at least ~1024 K per split
   int64_t s = want < maxk ? want : maxk;
   if (s < 1) s = 1;
@@ -257,13 +257,20 @@ cudaError_t noalloc_scratch(double** out) {
   return cudaSuccess;
 }
 
+// True for memory the current device can address without peer access: device
+// memory of the current device, or managed memory.  A failed attribute query
+// clears only the error it raised itself, never one the caller left pending.
 bool device_pointer(const void* p) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  const cudaError_t pending = cudaPeekAtLastError();
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
+    if (pending == cudaSuccess) cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -287,7 +294,8 @@ extern "C" int sparc_project_noalloc(const double* Xt, const double* Yt, int ns,
   }
   if (!device_pointer(Xt) || !device_pointer(Yt) || !device_pointer(Hs) ||
       !device_pointer(Ms)) {
-    set_global_error("invalid argument: sparc_project_noalloc takes device pointers");
+    set_global_error("invalid argument: sparc_project_noalloc takes device pointers of the "
+                     "current device");
     return SPARC_ERR_INVALID_ARG;
   }
   double* work = nullptr;

@@ -158,7 +158,7 @@ cudaError_t launch_density(const T* X, int64_t ld, int64_t nd, int ns, const dou
   const unsigned bx = (unsigned)((threads + 255) / 256);
   // enough orbital splits to give every SM about 1024 threads, bounded by the
   // orbitals (at least 8 per split) and by the scratch
-  int nsplit = (int)std::max<int64_t>(1, (int64_t)152 * 1024 / std::max<int64_t>(threads, 1));
+  int nsplit = (int)std::max<int64_t>(1, (int64_t)sm_count() * 1024 / std::max<int64_t>(threads, 1));
   nsplit = std::min(nsplit, std::max(1, ns / 8));
   nsplit = (int)std::min<int64_t>(nsplit, std::max<int64_t>(1, work_elems / std::max<int64_t>(nd, 1)));
   nsplit = std::min(nsplit, 64);

@@ -749,6 +749,20 @@ void eig_free(EigWork& w) {
   w = EigWork{};
 }
 
+// Checked enqueue: return the first failing runtime call's error at once.
+#define EK(expr)                      \
+  do {                                \
+    const cudaError_t e_ = (expr);    \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+// Kernel launch followed by the launch check.
+#define EL(...)                   \
+  do {                            \
+    note_launch();                \
+    __VA_ARGS__;                  \
+    EK(cudaGetLastError());       \
+  } while (0)
+
 cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, double* lam, double* Z,
                     cudaStream_t st) {
   // Buffers (n x n unless noted): L (Cholesky factor of Ms, kept to the end),
@@ -759,46 +773,48 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
   const dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
   int* st0 = w.status;
   int* st1 = w.status + 1;
-  cudaMemsetAsync(w.status, 0, 2 * sizeof(int), st);  // words 2, 3: GEMM / stencil waits
+  EK(cudaMemsetAsync(w.status, 0, 2 * sizeof(int), st));  // words 2, 3: GEMM / stencil waits
   // 1. Ms = L L^T
-  cudaMemcpyAsync(w.W, Ms, nn * 8, cudaMemcpyDeviceToDevice, st);
-  cholesky(w.W, n, st0, st);
-  note_launch(), k_tril_copy<<<nb, 256, 0, st>>>(w.W, w.L, n);
-  note_launch(), k_transpose<<<tg, tb, 0, st>>>(w.L, w.V, n);  // V = L row-major (forward solves)
+  EK(cudaMemcpyAsync(w.W, Ms, nn * 8, cudaMemcpyDeviceToDevice, st));
+  EK(cholesky(w.W, n, st0, st));
+  EL(k_tril_copy<<<nb, 256, 0, st>>>(w.W, w.L, n));
+  EL(k_transpose<<<tg, tb, 0, st>>>(w.L, w.V, n));  // V = L row-major (forward solves)
   // 2. A = sym(L^-1 (L^-1 Hs)^T)
-  trsm<true>(w.V, Hs, w.W, n, st0, st);          // W = L^-1 Hs
-  note_launch(), k_transpose<<<tg, tb, 0, st>>>(w.W, w.A, n);  // A = W^T
-  trsm<true>(w.V, w.A, w.W, n, st0, st);         // W = L^-1 W^T
-  note_launch(), k_symmetrize<<<nb, 256, 0, st>>>(w.W, w.A, n);
+  EK(trsm<true>(w.V, Hs, w.W, n, st0, st));          // W = L^-1 Hs
+  EL(k_transpose<<<tg, tb, 0, st>>>(w.W, w.A, n));  // A = W^T
+  EK(trsm<true>(w.V, w.A, w.W, n, st0, st));         // W = L^-1 W^T
+  EL(k_symmetrize<<<nb, 256, 0, st>>>(w.W, w.A, n));
   // 3. Householder tridiagonalisation; reflectors in the rows of Hv = lu[0, nn)
   double* Hv = w.lu;
   double* p = w.tau;
   bool coop_done = false;
   if (n >= 64) {
-    int dev = 0, sms = 0, per_sm = 0, coop = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int dev = 0, per_sm = 0, coop = 0;
+    EK(cudaGetDevice(&dev));
+    EK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    const int sms = sm_count();
     const size_t vbytes = (size_t)n * sizeof(double);
     if (vbytes > 48 * 1024)
-      cudaFuncSetAttribute(k_house_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)std::min<size_t>(vbytes, 200 * 1024));
+      EK(cudaFuncSetAttribute(k_house_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)std::min<size_t>(vbytes, 200 * 1024)));
     if (vbytes <= 200 * 1024)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_house_persistent, 256, vbytes);
+      EK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_house_persistent, 256, vbytes));
     else
       per_sm = 0;  // the reflector would not fit in shared memory: per-step kernels
     if (coop && sms > 0 && per_sm > 0) {
       int blocks = sms * std::min(per_sm, 2);
       GridBar gb{reinterpret_cast<unsigned*>(w.status + 8), reinterpret_cast<unsigned*>(w.status + 9),
                  w.status + 4};
-      cudaMemsetAsync(w.status + 4, 0, sizeof(int), st);
-      cudaMemsetAsync(w.status + 8, 0, 2 * sizeof(int), st);
+      EK(cudaMemsetAsync(w.status + 4, 0, sizeof(int), st));
+      EK(cudaMemsetAsync(w.status + 8, 0, 2 * sizeof(int), st));
       double* Ap = w.A;
       double* dp = w.d;
       double* ep = w.e;
       int nn_ = n;
       void* args[] = {&Ap, &Hv, &dp, &ep, &p, &nn_, &gb};
       note_launch();
+      // a refused cooperative launch (e.g. not enough co-resident blocks)
+      // falls back to the per-step kernels below
       if (cudaLaunchCooperativeKernel((void*)k_house_persistent, dim3(blocks), dim3(256), args,
                                       vbytes, st) == cudaSuccess)
         coop_done = true;
@@ -807,50 +823,52 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
     }
   }
   for (int k = 0; !coop_done && k + 2 < n; ++k) {
-    note_launch(), k_house_vec<<<1, 256, 0, st>>>(w.A, Hv, w.d, w.e, n, k);
+    EL(k_house_vec<<<1, 256, 0, st>>>(w.A, Hv, w.d, w.e, n, k));
     int m = n - k - 1;
-    note_launch(), k_house_matvec<<<(m + 7) / 8, 256, 0, st>>>(w.A, Hv, p, n, k);
+    EL(k_house_matvec<<<(m + 7) / 8, 256, 0, st>>>(w.A, Hv, p, n, k));
     int ub = (int)std::min<int64_t>(((int64_t)m * m + 255) / 256, 1024);
-    note_launch(), k_house_update<<<ub, 256, 0, st>>>(w.A, Hv, p, n, k);
+    EL(k_house_update<<<ub, 256, 0, st>>>(w.A, Hv, p, n, k));
   }
-  note_launch(), k_house_tail<<<1, 32, 0, st>>>(w.A, Hv, w.d, w.e, n);
-  cudaMemcpyAsync(w.A, Hv, nn * 8, cudaMemcpyDeviceToDevice, st);  // reflectors -> A
+  EL(k_house_tail<<<1, 32, 0, st>>>(w.A, Hv, w.d, w.e, n));
+  EK(cudaMemcpyAsync(w.A, Hv, nn * 8, cudaMemcpyDeviceToDevice, st));  // reflectors -> A
   // 4. eigenvalues of T (ascending)
   double* e2 = w.tau + n;
-  note_launch(), k_gersh<<<1, 1024, 0, st>>>(w.d, w.e, n, e2, w.scal);
-  note_launch(), k_bisect<<<(n * kMsLanes + 127) / 128, 128, 0, st>>>(w.d, e2, n, w.scal, lam);
+  EL(k_gersh<<<1, 1024, 0, st>>>(w.d, w.e, n, e2, w.scal));
+  EL(k_bisect<<<(n * kMsLanes + 127) / 128, 128, 0, st>>>(w.d, e2, n, w.scal, lam));
   // 5. eigenvectors of T into W (column-major); factors in lu (4 n x n)
-  note_launch(), k_clusters<<<1, 32, 0, st>>>(lam, n, w.scal, w.clus);
+  EL(k_clusters<<<1, 32, 0, st>>>(lam, n, w.scal, w.clus));
   double* VT = w.W;
-  note_launch(), k_inviter_single<<<(n + 31) / 32, 32, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv,
-                                                 VT);
-  note_launch(), k_inviter_cluster<<<n, 256, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv, VT);
+  EL(k_inviter_single<<<(n + 31) / 32, 32, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu,
+                                                    w.piv, VT));
+  EL(k_inviter_cluster<<<n, 256, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv, VT));
   //    Cholesky-QR pass: G = VT^T VT = R R^T, Q = VT R^-T  (Q^T = R^-1 VT^T)
   {
     double* G1 = w.lu;           // unused copy (projection writes two outputs)
     double* G = w.lu + nn;
     double* work = w.lu + 2 * nn;  // 2 nn doubles for one split
-    project_simt<double>(VT, VT, n, n, n, G1, G, work, 1, st);
-    cholesky(G, n, st1, st);
-    note_launch(), k_tril_copy<<<nb, 256, 0, st>>>(G, w.V, n);            // V = R (column-major)
-    note_launch(), k_transpose<<<tg, tb, 0, st>>>(w.V, w.lu, n);          // lu0 = R row-major
-    note_launch(), k_transpose<<<tg, tb, 0, st>>>(VT, w.lu + 2 * nn, n);  // lu2 = VT^T column-major
-    trsm<true>(w.lu, w.lu + 2 * nn, w.lu + nn, n, st1, st);  // lu1 = Q^T
-    note_launch(), k_transpose<<<tg, tb, 0, st>>>(w.lu + nn, VT, n);      // VT = Q
+    EK(project_simt<double>(VT, VT, n, n, n, G1, G, work, 1, st));
+    EK(cholesky(G, n, st1, st));
+    EL(k_tril_copy<<<nb, 256, 0, st>>>(G, w.V, n));            // V = R (column-major)
+    EL(k_transpose<<<tg, tb, 0, st>>>(w.V, w.lu, n));          // lu0 = R row-major
+    EL(k_transpose<<<tg, tb, 0, st>>>(VT, w.lu + 2 * nn, n));  // lu2 = VT^T column-major
+    EK(trsm<true>(w.lu, w.lu + 2 * nn, w.lu + nn, n, st1, st));  // lu1 = Q^T
+    EL(k_transpose<<<tg, tb, 0, st>>>(w.lu + nn, VT, n));      // VT = Q
   }
   // 6. V = Q_house VT (all reflectors, warp per column)
   {
     int wpb = col_warps(n);
     size_t smem = (size_t)wpb * n * sizeof(double);
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-    note_launch(), k_backtransform<<<(n + wpb - 1) / wpb, wpb * 32, smem, st>>>(w.A, VT, n);
+      EK(cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem));
+    EL(k_backtransform<<<(n + wpb - 1) / wpb, wpb * 32, smem, st>>>(w.A, VT, n));
   }
   // 7. Z = L^-T V; sign convention; NaN check
-  trsm<false>(w.L, VT, Z, n, st0, st);
-  note_launch(), k_fix_signs<<<(n * 32 + 255) / 256, 256, 0, st>>>(Z, n, lam, st0);
-  return cudaGetLastError();
+  EK(trsm<false>(w.L, VT, Z, n, st0, st));
+  EL(k_fix_signs<<<(n * 32 + 255) / 256, 256, 0, st>>>(Z, n, lam, st0));
+  return cudaSuccess;
 }
+#undef EL
+#undef EK
 
 }  // namespace sparc

@@ -20,6 +20,13 @@ long long launch_count();
 // Message returned by sparc_last_error(NULL) (calls made without a handle).
 void set_global_error(const std::string& msg);
 
+// Number of SMs of the current device (queried once per device; 1 if the query
+// fails, so grid sizing stays valid).
+int sm_count();
+// Sets a kernel's dynamic shared-memory limit on the current device, once per
+// device per `bits` word (one word per kernel instantiation).
+cudaError_t smem_limit_once(unsigned long long* bits, const void* func, int bytes);
+
 constexpr int kRadius = 6;  // 12th-order central FD Laplacian (radius 6)
 
 struct Grid {

@@ -283,7 +283,7 @@ cudaError_t apply_h(const Grid& g, const LapCoef& lc, const T* veff, const Nonlo
   int tiles_y = (g.ny + C::BY - 1) / C::BY;
   int64_t xy_ctas = (int64_t)a.tiles_x * tiles_y * ns;
   // split z so that the grid covers the SMs several times over
-  int nzc = (int)((4 * 152 + xy_ctas - 1) / xy_ctas);
+  int nzc = (int)((4 * sm_count() + xy_ctas - 1) / xy_ctas);
   nzc = max(1, min(nzc, max(1, g.nz / 8)));
   a.bz = (g.nz + nzc - 1) / nzc;
   nzc = (g.nz + a.bz - 1) / a.bz;

@@ -493,17 +493,15 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
   a.status = status;
   // z split: enough CTAs to cover the SMs a few times
   const int64_t xy = (int64_t)a.nslab * ns;
-  int nzc = (int)std::max<int64_t>(1, (2 * 152 + xy - 1) / xy);
+  int nzc = (int)std::max<int64_t>(1, (2 * sm_count() + xy - 1) / xy);
   nzc = std::min(nzc, std::max(1, g.nz / 16));
   a.bz = (g.nz + nzc - 1) / nzc;
   nzc = (g.nz + a.bz - 1) / a.bz;
   a.d_off = (uint32_t)slots * slot_bytes;
   const size_t smem = (size_t)slots * slot_bytes + (size_t)nl.kp * sizeof(T) + 128;
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(k_apply_h_ring<T, VX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         210 * 1024);
-  });
+  static unsigned long long attr_bits = 0;
+  cudaError_t ae = smem_limit_once(&attr_bits, (const void*)k_apply_h_ring<T, VX>, 210 * 1024);
+  if (ae != cudaSuccess) return ae;
   dim3 grid((unsigned)(a.nslab * ns), (unsigned)nzc);
   note_launch(), k_apply_h_ring<T, VX><<<grid, threads, smem, st>>>(mmid, mhalo, a);
   *used = true;

@@ -1006,7 +1006,7 @@ int tc_project_nsplit(int ns) {
       if (bi * kBM <= bj * kBN + kBN - 1) ++tiles;
   tiles *= 2;  // Hs and Ms
   // enough (tile, split) items for the persistent CTAs to balance: ~4 per SM
-  int s = (4 * 152 + tiles - 1) / tiles;
+  int s = (4 * sm_count() + tiles - 1) / tiles;
   return std::max(1, std::min(s, 64));
 }
 

@@ -242,7 +242,14 @@ WORKLOADS = {
                    degree=20, steps=3),
     "slab64x64x160": dict(name="64x64x160 slab (periodic xy, Dirichlet z), h=0.35, 600 atoms, "
                                "Ns=4800, m=24", seed_offset=4000, shape=(64, 64, 160), h=0.35,
-                          bc=(PERIODIC, PERIODIC, DIRICHLET), ns=4800, degree=24, steps=1),
+                          bc=(PERIODIC, PERIODIC, DIRICHLET), ns=4800, degree=24, steps=1,
+                          lattice=(10, 10, 6)),
+    # the same slab recipe at half the lateral size and half the depth: the
+    # reduced slab the oracle can step in seconds
+    "slab32x32x80": dict(name="32x32x80 slab (periodic xy, Dirichlet z), h=0.35, 75 atoms, "
+                              "Ns=600, m=24", seed_offset=4100, shape=(32, 32, 80), h=0.35,
+                         bc=(PERIODIC, PERIODIC, DIRICHLET), ns=600, degree=24, steps=1,
+                         lattice=(5, 5, 3)),
 }
 BATCH_SEED_OFFSET = 5000  # the 64 uneven systems of the batched form
 
@@ -253,8 +260,9 @@ def workload_seed(workload: str, index: int = 0) -> int:
 
 def make_workload_system(workload: str) -> System:
     """The synthetic system of a named workload: the 24^3 bulk with 8 random
-    atoms, the 96^3 bulk with 216 atoms on a jittered simple-cubic lattice, or
-    the 64 x 64 x 160 slab with 600 atoms in the central 60 % of z."""
+    atoms, the 96^3 bulk with 216 atoms on a jittered simple-cubic lattice, the
+    64 x 64 x 160 slab with 600 atoms in the central 60 % of z, or the reduced
+    32 x 32 x 80 slab (75 atoms) built the same way."""
     c = WORKLOADS[workload]
     seed = workload_seed(workload)
     shape, h, bc = c["shape"], c["h"], c["bc"]
@@ -263,11 +271,12 @@ def make_workload_system(workload: str) -> System:
     rng = np.random.default_rng(seed + 500)
     if workload == "bulk96":
         pos = jittered_lattice((6, 6, 6), 6.4, (3.2, 3.2, 3.2), 0.5, rng)
-    else:  # slab: 10 x 10 x 6 lattice in x, y and z in [0.2, 0.8] Lz
+    else:  # slab: cx x cy x cz lattice in x, y and z in [0.2, 0.8] Lz
+        cx, cy, cz = c["lattice"]
         lx, lz = shape[0] * h, (shape[2] - 1) * h
-        zs = np.linspace(0.2 * lz, 0.8 * lz, 6)
-        sx = lx / 10.0
-        base = jittered_lattice((10, 10, 1), (sx, sx, 1.0), (sx / 2, sx / 2, 0.0), 0.0, rng)
+        zs = np.linspace(0.2 * lz, 0.8 * lz, cz)
+        sx = lx / cx
+        base = jittered_lattice((cx, cy, 1), (sx, sx, 1.0), (sx / 2, sx / 2, 0.0), 0.0, rng)
         pos = np.concatenate([base + np.array([0.0, 0.0, z]) for z in zs])
         pos += rng.uniform(-0.5, 0.5, size=pos.shape)
     return random_system(shape, h, bc, pos.shape[0], seed, positions=pos, name=c["name"])

@@ -1,6 +1,9 @@
 """Batched form: several independent systems of uneven size stepped by one
 batched call (one launch per Chebyshev degree for all members, CUDA graph),
-against the oracle per member and against per-member single steps."""
+against the oracle per member and against per-member single steps.  FP64
+members meet the FP64 targets (Ritz values within 1e-8 Ha); mixed members meet
+the mixed ones against the FP64 oracle (occupied Ritz values within 1e-6 Ha,
+density L1 within 1e-6 per electron)."""
 import numpy as np
 import pytest
 
@@ -47,13 +50,25 @@ def test_batch_step_vs_oracle_and_single(precision):
     degrees = [m["degree"] for m in MEMBERS]
     for step in range(2):  # second call replays the captured graph
         lam_b = batch.chefsi_step(Xb, degrees, bounds=bounds)
+        if step == 0:
+            for i, ((s, o), m) in enumerate(zip(systems, MEMBERS)):
+                rX, rlam = o.chefsi_step(X0[i], m["degree"], *bounds[i])
+                if precision == "fp64":
+                    assert np.max(np.abs(lam_b[i] - rlam)) < 1e-8
+                    continue
+                ne = synth.electrons_for(m["ns"])
+                rf, _ = oracle.fermi_occupations(rlam, ne, 0.01)
+                occ = rf > 1e-6
+                assert np.max(np.abs(lam_b[i] - rlam)[occ]) < 1e-6, (i, lam_b[i] - rlam)
+                f, _ = handles[i].occupations(torch.from_numpy(lam_b[i]).to(DEV), ne, 0.01)
+                rho = handles[i].density(Xb[i], f).cpu().numpy()
+                rrho = oracle.density(rX, rf, s.nd, s.h)
+                l1 = s.h ** 3 * np.sum(np.abs(rho - rrho)) / ne
+                assert l1 < 1e-6, (i, l1)
         for i, ((s, o), m) in enumerate(zip(systems, MEMBERS)):
             Xs = torch.from_numpy(X0[i]).to(DEV, dt)
             lam_s = handles[i].chefsi_step(Xs, m["degree"], bounds=bounds[i])
             assert np.max(np.abs(lam_b[i] - lam_s)) < (1e-10 if precision == "fp64" else 1e-5)
-            if precision == "fp64" and step == 0:
-                _, rlam = o.chefsi_step(X0[i], m["degree"], *bounds[i])
-                assert np.max(np.abs(lam_b[i] - rlam)) < 1e-8
             X0[i] = Xs.double().cpu().numpy()
             Xb[i].copy_(Xs)
         assert batch.launches() > 0

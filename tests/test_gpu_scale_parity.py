@@ -1,0 +1,177 @@
+"""GPU parity at the sizes the benchmarks run: the subspace eigensolver at
+n = 257, 1300 and 4800 (the persistent Householder, multisection and clustered
+inverse-iteration paths) against the oracle and a library reduction, and one
+CheFSI step of the reduced slab (32 x 32 x 80, periodic x and y, Dirichlet z,
+h = 0.35, 75 atoms with projectors overlapping about ten deep, Ns = 600,
+degree 24) against the oracle in both precisions.
+
+Tolerances: the eigensolver's backward error is a few eps |H| cond(M), so the
+eigenvalue and residual bounds scale with cond(M) / 1e4 as in the small-size
+tests; degenerate levels are compared through their spectral projectors
+Z_c Z_c^T, which are unique.  The slab step uses the stated targets: Ritz
+values within 1e-8 Ha and subspace distance 1e-7 (FP64), occupied Ritz values
+within 1e-6 Ha and density L1 within 1e-6 per electron (mixed)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_09708_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2302_09708_gb300 import sparc  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def to_dev(X, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(X)).to(DEV, dtype)
+
+
+def subspace_distance(A, B):
+    """|(I - Qa Qa^T) Qb|_F for orthonormal bases of span(A^T), span(B^T)."""
+    Qa, _ = np.linalg.qr(A.T)
+    Qb, _ = np.linalg.qr(B.T)
+    return float(np.linalg.norm(Qb - Qa @ (Qa.T @ Qb)))
+
+
+def _spd_pair(n, cond, rng, levels=None):
+    """H, M with M SPD of condition number `cond` and H = L (P diag(ev) P^T) L^T
+    (L the Cholesky factor of M), so that H z = lambda M z has eigenvalues ev.
+    `levels`: list of (first index, multiplicity) made exactly degenerate."""
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    M = (Q * np.logspace(0, -np.log10(cond), n)) @ Q.T
+    M = 0.5 * (M + M.T)
+    ev = np.sort(rng.uniform(-3, 40, n))
+    for i0, mult in levels or ():
+        ev[i0:i0 + mult] = ev[i0]
+    ev = np.sort(ev)
+    P, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    L = np.linalg.cholesky(M)
+    H = L @ ((P * ev) @ P.T) @ L.T
+    return 0.5 * (H + H.T), M, ev
+
+
+@pytest.fixture(scope="module")
+def free_handle():
+    s = synth.free_system((16, 16, 16), 0.5, (0, 0, 0), v0=0.3)
+    h = sparc.Handle(s, "fp64", ns_max=4800)
+    yield h
+    h.close()
+
+
+@pytest.mark.parametrize("n,cond", [(257, 1e8), (1300, 1e6)])
+def test_subspace_eig_large_vs_oracle(free_handle, n, cond):
+    rng = np.random.default_rng(n)
+    H, M, ev = _spd_pair(n, cond, rng)
+    lam, Z = free_handle.subspace_eig(to_dev(H), to_dev(M))
+    lam, Z = lam.cpu().numpy(), Z.cpu().numpy()
+    rlam, rZ = oracle.gen_eig(H, M)
+    scale = max(1.0, cond / 1e4)
+    amax = np.max(np.abs(rlam))
+    assert np.max(np.abs(lam - rlam)) < 1e-9 * scale * amax
+    assert np.max(np.abs(lam - ev)) < 1e-9 * scale * amax  # the constructed spectrum
+    assert np.max(np.abs(Z.T @ M @ Z - np.eye(n))) < 1e-9 * scale
+    assert np.max(np.abs(H @ Z - M @ Z * lam)) < 1e-9 * scale * np.max(np.abs(H))
+    # eigenvalues here are simple (random): each vector spans the same line as
+    # the oracle's, up to rounding amplified by 1 / gap (columns with a clear
+    # gap; the M-inner product of two M-normalised vectors is then +-1)
+    gaps = np.minimum(np.abs(np.diff(rlam, prepend=-np.inf)), np.abs(np.diff(rlam, append=np.inf)))
+    ok = gaps > 1e-3 * amax
+    ov = np.abs(np.sum(Z[:, ok] * (M @ rZ[:, ok]), axis=0))
+    assert np.max(np.abs(ov - 1.0)) < 1e-6 * scale
+    cols = np.argmax(np.abs(Z), axis=0)
+    assert np.all(Z[cols, np.arange(n)] > 0)
+
+
+def test_subspace_eig_clustered_levels(free_handle):
+    """n = 300 with a 48-fold and a 12-fold exactly degenerate level (the sizes
+    of free-electron shells): eigenvalues, M-orthonormality, residual, and the
+    spectral projector of each degenerate level against the oracle's."""
+    n = 300
+    rng = np.random.default_rng(4848)
+    H, M, ev = _spd_pair(n, 1e2, rng, levels=[(20, 48), (150, 12)])
+    lam, Z = free_handle.subspace_eig(to_dev(H), to_dev(M))
+    lam, Z = lam.cpu().numpy(), Z.cpu().numpy()
+    rlam, rZ = oracle.gen_eig(H, M)
+    amax = np.max(np.abs(rlam))
+    assert np.max(np.abs(lam - rlam)) < 1e-10 * amax
+    assert np.max(np.abs(Z.T @ M @ Z - np.eye(n))) < 1e-10
+    assert np.max(np.abs(H @ Z - M @ Z * lam)) < 1e-10 * np.max(np.abs(H))
+    for level in (ev[20], ev[150]):
+        c = np.abs(rlam - level) < 1e-8 * amax
+        assert c.sum() in (48, 12)
+        P, rP = Z[:, c] @ Z[:, c].T, rZ[:, c] @ rZ[:, c].T
+        assert np.max(np.abs(P - rP)) < 1e-9 * np.max(np.abs(rP))
+
+
+def test_subspace_eig_n4800_eigenvalues(free_handle):
+    """The slab's subspace size, eigenvalues only: against scipy's generalised
+    symmetric solver (LAPACK sygvd-style reduction) and the constructed
+    spectrum, plus M-orthonormality and the residual on sampled columns."""
+    sl = pytest.importorskip("scipy.linalg")
+    n = 4800
+    rng = np.random.default_rng(4800)
+    H, M, ev = _spd_pair(n, 1e4, rng)
+    lam, Z = free_handle.subspace_eig(to_dev(H), to_dev(M))
+    lam = lam.cpu().numpy()
+    rlam = sl.eigh(H, M, eigvals_only=True)
+    amax = np.max(np.abs(rlam))
+    assert np.max(np.abs(lam - rlam)) < 1e-9 * amax
+    assert np.max(np.abs(lam - ev)) < 1e-9 * amax
+    cols = np.linspace(0, n - 1, 24).astype(int)
+    Zc = Z[:, torch.as_tensor(cols, device=Z.device)].cpu().numpy()
+    MZ = M @ Zc
+    assert np.max(np.abs(Zc.T @ MZ - np.eye(len(cols)))) < 1e-9
+    assert np.max(np.abs(H @ Zc - MZ * lam[cols])) < 1e-9 * np.max(np.abs(H))
+
+
+# ---------------------------------------------------------------------------
+# Reduced slab: one CheFSI step against the oracle in both precisions.
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def slab():
+    s = synth.make_workload_system("slab32x32x80")
+    c = synth.WORKLOADS["slab32x32x80"]
+    o = oracle.Oracle(s)
+    a0, b, *_ = o.lanczos(32, 0)
+    a = a0 + 0.1 * (b - a0)
+    X0 = synth.random_orbitals(s.nd, c["ns"], seed=synth.workload_seed("slab32x32x80"))
+    rX, rlam = o.chefsi_step(X0, c["degree"], a, b, a0)
+    return dict(s=s, o=o, bounds=(a, b, a0), X0=X0, rX=rX, rlam=rlam, ns=c["ns"],
+                m=c["degree"])
+
+
+def test_slab_step_fp64_vs_oracle(slab):
+    s, ns, m = slab["s"], slab["ns"], slab["m"]
+    h = sparc.Handle(s, "fp64", ns_max=ns)
+    Xd = to_dev(slab["X0"])
+    lam = h.chefsi_step(Xd, m, bounds=slab["bounds"])
+    X1 = Xd.cpu().numpy()
+    assert np.max(np.abs(lam - slab["rlam"])) < 1e-8, np.max(np.abs(lam - slab["rlam"]))
+    assert subspace_distance(X1, slab["rX"]) < 1e-7
+    assert np.max(np.abs(X1 @ X1.T - np.eye(ns))) < 1e-9
+    h.close()
+
+
+def test_slab_step_mixed_vs_oracle(slab):
+    s, ns, m = slab["s"], slab["ns"], slab["m"]
+    h = sparc.Handle(s, "mixed", ns_max=ns)
+    Xd = to_dev(slab["X0"], torch.float32)
+    lam = h.chefsi_step(Xd, m, bounds=slab["bounds"])
+    ne = synth.electrons_for(ns)
+    rf, _ = oracle.fermi_occupations(slab["rlam"], ne, 0.01)
+    occ = rf > 1e-6
+    err = np.max(np.abs(lam - slab["rlam"])[occ])
+    assert err < 1e-6, err
+    # density of the occupied states (invariant under rotations within levels)
+    rrho = oracle.density(slab["rX"], rf, s.nd, s.h)
+    f, _ = h.occupations(to_dev(lam), ne, 0.01)
+    rho = h.density(Xd, f).cpu().numpy()
+    l1 = s.h ** 3 * np.sum(np.abs(rho - rrho)) / ne
+    assert l1 < 1e-6, l1
+    h.close()

@@ -2,13 +2,16 @@
 device memory (their memory belongs to another allocator, or a cudaMalloc would
 stall a latency-critical loop).  It keeps its split-K scratch in a static device
 array, so this file checks it through the C ABI against sparc_project on a
-handle, on consecutive calls that reuse the same scratch.  The file sorts last
-so that a run stopping at the first failure has already run every other test."""
+handle and against the oracle's projection, on consecutive calls that reuse the
+same scratch, including the largest size the scratch holds right after a call
+that used more splits.  The file sorts last so that a run stopping at the first
+failure has already run every other test."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2302_09708_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -51,6 +54,42 @@ def test_project_noalloc_matches_handle_projection_on_consecutive_calls():
         assert torch.isfinite(Hs).all() and torch.isfinite(Ms).all()
         assert float((Hs - rH).abs().max()) < TOL
         assert float((Ms - rM).abs().max()) < TOL
+        # the oracle (symmetric outputs: the column-major C result equals the
+        # row-major view)
+        oH, oM = oracle.project(X[:, :nd].cpu().numpy(), Y[:, :nd].cpu().numpy(), nd)
+        iu = np.triu_indices(ns)
+        assert np.max(np.abs(Hs.cpu().numpy().T[iu] - oH[iu])) < TOL
+        assert np.max(np.abs(Ms.cpu().numpy() - oM)) < TOL
+    h.close()
+
+
+def test_project_noalloc_largest_size_after_a_call_with_more_splits():
+    """ns = 1448 fills the static scratch with a single split (2 ns^2 of its
+    4194304 doubles), so the split count the size would otherwise get is
+    clamped to 1.  It runs right after a call that spread its partials over many
+    splits, whose stale values must not be read, and matches the oracle and the
+    handle projection."""
+    L = sparc.load()
+    rng = np.random.default_rng(1448)
+    nd0, ns0 = 200000, 40  # many splits: partials spread over the scratch
+    X0 = torch.from_numpy(rng.standard_normal((ns0, nd0))).to(DEV)
+    _noalloc(L, X0, X0, ns0, nd0, nd0)
+    ns, nd = 1448, 4096
+    X = torch.from_numpy(rng.standard_normal((ns, nd))).to(DEV)
+    Y = torch.from_numpy(rng.standard_normal((ns, nd))).to(DEV)
+    for _ in range(2):
+        Hs, Ms = _noalloc(L, X, Y, ns, nd, nd)
+        oH, oM = oracle.project(X.cpu().numpy(), Y.cpu().numpy(), nd)
+        iu = np.triu_indices(ns)
+        assert np.max(np.abs(Hs.cpu().numpy().T[iu] - oH[iu])) < TOL
+        assert np.max(np.abs(Ms.cpu().numpy() - oM)) < TOL
+        _noalloc(L, X0, X0, ns0, nd0, nd0)
+    s = synth.free_system((16, 16, 16), 0.5, (0, 0, 0))
+    h = sparc.Handle(s, "fp64", ns_max=ns, options_flags=2)
+    rH, rM = h.project(torch.nn.functional.pad(X, (0, s.nd - nd)),
+                       torch.nn.functional.pad(Y, (0, s.nd - nd)))
+    torch.cuda.synchronize()
+    assert float((Hs - rH).abs().max()) < TOL and float((Ms - rM).abs().max()) < TOL
     h.close()
 
 
