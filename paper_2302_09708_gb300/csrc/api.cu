@@ -141,16 +141,37 @@ int check_block(sparc_context* c, const void* X, int ns, int64_t ld, int dtype) 
   return SPARC_OK;
 }
 
-// Nonlocal coefficients of x followed by y = s_h (H - shift) x + s_p prev.
+template <typename T>
+const NlTiles<T>& tiles_of(const sparc_context* c);
+template <>
+const NlTiles<double>& tiles_of<double>(const sparc_context* c) { return c->tiles64; }
+template <>
+const NlTiles<float>& tiles_of<float>(const sparc_context* c) { return c->tiles32; }
+// The support-point tables exist for the handle's working precision only (FP64
+// handles: double, mixed handles: float).
+template <typename T>
+bool tiles_usable(const sparc_context* c) {
+  const bool mixed = c->precision == SPARC_PREC_MIXED;
+  return c->tiles_ok && (std::is_same<T, float>::value == mixed);
+}
+
+// y = s_h (H - shift) x + s_p prev.  The nonlocal coefficients D of x are in
+// c->D when `d_ready`, else they are gathered first (k_nl_coef).  On the ring
+// path the local stencil runs first and the nonlocal term follows by support-
+// point tiles; with `want_next` that pass also leaves the coefficients of y in
+// c->D (the next recurrence step's D) and sets *next_done.
 template <typename T>
 int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
-          int64_t ldp, int ns, double shift, double s_h, double s_p, cudaStream_t st) {
+          int64_t ldp, int ns, double shift, double s_h, double s_p, cudaStream_t st,
+          bool d_ready = false, bool want_next = false, bool* next_done = nullptr) {
   const Nonlocal<T>& nl = std::is_same<T, double>::value
                               ? reinterpret_cast<const Nonlocal<T>&>(c->nl64)
                               : reinterpret_cast<const Nonlocal<T>&>(c->nl32);
   const T* veff = std::is_same<T, double>::value ? (const T*)c->veff64 : (const T*)c->veff32;
   T* D = (T*)c->D;
-  CK(c, nl_coefficients<T>(nl, c->h * c->h * c->h, x, ldx, ns, D, st));
+  const double h3 = c->h * c->h * c->h;
+  if (next_done) *next_done = false;
+  if (!d_ready) CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st));
   if (std::is_same<T, double>::value && c->ring_enabled && c->df_stencil) {
     bool used = false;
     CK(c, apply_h_ring_df(c->grid, c->lap, c->veff_df, c->nl64, (const double*)D,
@@ -158,16 +179,36 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
                           shift, s_h, s_p, c->eig.status + 3, st, &used));
     if (used) return SPARC_OK;
   }
+  if (c->ring_enabled && (nl.natoms == 0 || nl.kp == 0 || tiles_usable<T>(c))) {
+    bool used = false;
+    CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
+                          c->wait_cycles, c->eig.status + 3, st, &used));
+    if (used) {
+      if (nl.natoms > 0 && nl.kp > 0) {
+        const NlTiles<T>& t = tiles_of<T>(c);
+        T* part = want_next ? (T*)c->part : nullptr;
+        CK(c, nl_apply<T>(t, D, nl.kp, y, ldy, ns, s_h, part, st));
+        if (want_next) {
+          CK(c, nl_reduce<T>(t, part, ns, nl.kp, nl.gamma, h3, D, st));
+          if (next_done) *next_done = true;
+        }
+      }
+      return SPARC_OK;
+    }
+  }
   CK(c, apply_h<T>(c->grid, c->lap, veff, nl, D, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
-                   c->ring_enabled ? c->eig.status + 3 : nullptr, st));
+                   st));
   return SPARC_OK;
 }
 
 // Chebyshev filter (Algorithm 1, scaled three-term recurrence).  Y_0 = X (ldx);
-// Y_i goes to outs[i] (X, W1 or W2).  Returns the buffer holding Y_m.
+// Y_i goes to outs[i] (X, W1 or W2).  Returns the buffer holding Y_m; with
+// `result_d`, *result_d tells whether c->D holds the nonlocal coefficients of
+// Y_m on return (the ring path computes them from the last degree's values).
 template <typename T>
 int run_filter(sparc_context* c, T* X, int64_t ldx, int ns, int m, double a, double b, double a0,
-               bool land_in_workspace, T** result, int64_t* ldr, cudaStream_t st) {
+               bool land_in_workspace, T** result, int64_t* ldr, cudaStream_t st,
+               bool* result_d = nullptr) {
   const double e = (b - a) / 2.0, cc = (b + a) / 2.0;
   double sigma = e / (a0 - cc);
   const double sigma1 = sigma, tau = 2.0 / sigma1;
@@ -190,20 +231,26 @@ int run_filter(sparc_context* c, T* X, int64_t ldx, int ns, int m, double a, dou
     buf[i] = out;
     lds[i] = out == X ? ldx : c->ld;
   }
+  bool d_ready = false;
   for (int i = 1; i <= m; ++i) {
     int rc;
+    const bool want_next = i < m || result_d != nullptr;
+    bool next = false;
     if (i == 1) {
-      rc = hstep<T>(c, buf[0], lds[0], buf[1], lds[1], nullptr, 0, ns, cc, sigma1 / e, 0.0, st);
+      rc = hstep<T>(c, buf[0], lds[0], buf[1], lds[1], nullptr, 0, ns, cc, sigma1 / e, 0.0, st,
+                    d_ready, want_next, &next);
     } else {
       double sigma_new = 1.0 / (tau - sigma);
       rc = hstep<T>(c, buf[i - 1], lds[i - 1], buf[i], lds[i], buf[i - 2], lds[i - 2], ns, cc,
-                    2.0 * sigma_new / e, -sigma * sigma_new, st);
+                    2.0 * sigma_new / e, -sigma * sigma_new, st, d_ready, want_next, &next);
       sigma = sigma_new;
     }
     if (rc) return rc;
+    d_ready = next;
   }
   *result = buf[m];
   *ldr = lds[m];
+  if (result_d) *result_d = d_ready;
   return SPARC_OK;
 }
 
@@ -223,7 +270,7 @@ int lanczos(sparc_context* c, int iters, uint64_t seed, double* a0, double* b, c
     CK(c, nl_coefficients<double>(nl, c->h * c->h * c->h, v, nd, 1, c->lz + 3 * nd + 1024 + 384,
                                   st));
     CK(c, apply_h<double>(c->grid, c->lap, c->veff64, nl, c->lz + 3 * nd + 1024 + 384, v, nd, w,
-                          nd, nullptr, 0, 1, 0.0, 1.0, 0.0, nullptr, st));
+                          nd, nullptr, 0, 1, 0.0, 1.0, 0.0, st));
     CK(c, lanczos_update(w, v, vp, ab, j, nd, st));
     CK(c, lanczos_normalize(v, w, vp, ab, j, nd, partial, st));
   }
@@ -318,14 +365,18 @@ int do_step(sparc_context* c, T* X, int64_t ldx, int ns, int m, double a, double
   CK(c, cudaEventRecord(c->ev[1], st));
   T* Xt;
   int64_t ldt;
-  int rc = run_filter<T>(c, X, ldx, ns, m, a, b, a0, true, &Xt, &ldt, st);
+  // FP64: the last filter degree also leaves the nonlocal coefficients of Xt
+  // for Yt = H Xt; mixed precision evaluates Yt in FP64 from its own gather
+  const bool f64 = std::is_same<T, double>::value;
+  bool xt_d = false;
+  int rc = run_filter<T>(c, X, ldx, ns, m, a, b, a0, true, &Xt, &ldt, st, f64 ? &xt_d : nullptr);
   if (rc) return rc;
   CK(c, cudaEventRecord(c->ev[2], st));
-  if (std::is_same<T, float>::value) {
+  if (!f64) {
     rc = mixed_yt_project(c, (const float*)Xt, ldt, ns, c->ev[3], st);
   } else {
     T* Yt = Xt == (T*)c->W1 ? (T*)c->W2 : (T*)c->W1;
-    rc = hstep<T>(c, Xt, ldt, Yt, c->ld, nullptr, 0, ns, 0.0, 1.0, 0.0, st);
+    rc = hstep<T>(c, Xt, ldt, Yt, c->ld, nullptr, 0, ns, 0.0, 1.0, 0.0, st, xt_d);
     if (rc) return rc;
     CK(c, cudaEventRecord(c->ev[3], st));
     rc = do_project<T>(c, Xt, ldt, Yt, c->ld, ns, c->Hs, c->Ms, st);
@@ -383,6 +434,7 @@ void destroy_ctx(sparc_context* c) {
   cudaFree(c->veff64); cudaFree(c->veff32); cudaFree(c->veff_df);
   cudaFree(c->W1); cudaFree(c->W2); cudaFree(c->Wstage); cudaFree(c->D);
   cudaFree(c->S1); cudaFree(c->S2); cudaFree(c->SZ); cudaFree(c->esc); cudaFree(c->Y64);
+  cudaFree(c->part);
   cudaFree(c->Hs); cudaFree(c->Ms); cudaFree(c->Z); cudaFree(c->lam); cudaFree(c->proj_work);
   cudaFree(c->lz);
   eig_free(c->eig);
@@ -594,6 +646,43 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
       n32.grp_k = dgk;
       n32.grp_chi = dgc;
     }
+    // support-point tiles of the working precision (nonlocal pass of the
+    // ring stencil path)
+    NlTilesHost th;
+    nl_tiles_build(nd, pull_ptr.data(), pull_k.data(), pull_chi.data(), kp, th);
+    const bool mixed = c->precision == SPARC_PREC_MIXED;
+    auto put_tiles = [&](auto& t, auto tag) -> int {
+      using TT = decltype(tag);
+      int r;
+      int *tp_, *pt_, *ep_, *ksp, *ksk, *kep, *kpp, *kpr;
+      uint16_t *ekl, *kpt;
+      TT *ech, *kch;
+      std::vector<TT> ec(th.ent_chi.begin(), th.ent_chi.end());
+      std::vector<TT> kc(th.kent_chi.begin(), th.kent_chi.end());
+      if ((r = upload<int>(c, th.tile_ptr.data(), th.tile_ptr.size(), &tp_))) return r;
+      if ((r = upload<int>(c, th.pts.data(), th.pts.size(), &pt_))) return r;
+      if ((r = upload<int>(c, th.ent_ptr.data(), th.ent_ptr.size(), &ep_))) return r;
+      if ((r = upload<uint16_t>(c, th.ent_kl.data(), th.ent_kl.size(), &ekl))) return r;
+      if ((r = upload<TT>(c, ec.data(), ec.size(), &ech))) return r;
+      if ((r = upload<int>(c, th.kset_ptr.data(), th.kset_ptr.size(), &ksp))) return r;
+      if ((r = upload<int>(c, th.kset_k.data(), th.kset_k.size(), &ksk))) return r;
+      if ((r = upload<int>(c, th.kent_ptr.data(), th.kent_ptr.size(), &kep))) return r;
+      if ((r = upload<uint16_t>(c, th.kent_pt.data(), th.kent_pt.size(), &kpt))) return r;
+      if ((r = upload<TT>(c, kc.data(), kc.size(), &kch))) return r;
+      if ((r = upload<int>(c, th.kpair_ptr.data(), th.kpair_ptr.size(), &kpp))) return r;
+      if ((r = upload<int>(c, th.kpair.data(), th.kpair.size(), &kpr))) return r;
+      t.ntiles = (int)th.tile_ptr.size() - 1;
+      t.npairs = (int)th.kset_k.size();
+      t.kt_max = th.kt_max;
+      t.tile_ptr = tp_; t.pts = pt_; t.ent_ptr = ep_; t.ent_kl = ekl; t.ent_chi = ech;
+      t.kset_ptr = ksp; t.kset_k = ksk; t.kent_ptr = kep; t.kent_pt = kpt; t.kent_chi = kch;
+      t.kpair_ptr = kpp; t.kpair = kpr;
+      c->tiles_ok = nl_apply_smem(t) <= 227 * 1024;
+      if (c->tiles_ok)
+        CK(c, cudaMalloc(&c->part, (size_t)std::max(t.npairs, 1) * c->ns_max * sizeof(TT)));
+      return SPARC_OK;
+    };
+    if ((rc = mixed ? put_tiles(c->tiles32, 0.0f) : put_tiles(c->tiles64, 0.0))) return rc;
   }
 
   // --- workspace ----------------------------------------------------------

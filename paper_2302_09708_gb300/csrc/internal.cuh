@@ -80,20 +80,22 @@ struct Nonlocal {
 };
 
 // Launchers (stencil.cu) -------------------------------------------------
-// y = s_h * ((H - shift) x) + s_p * prev   (prev may be null: s_p ignored)
-// with D the nonlocal coefficients of x (computed by nl_coefficients).
-// `status` (device int, may be null): receives SPARC_ERR_TIMEOUT if a bounded
-// wait of the TMA-ring form runs out; with a null status the generic form runs.
+// Generic form: y = s_h * ((H - shift) x) + s_p * prev   (prev may be null: s_p
+// ignored) with D the nonlocal coefficients of x (computed by nl_coefficients),
+// the nonlocal pull-add fused in.
 template <typename T>
 cudaError_t apply_h(const Grid& g, const LapCoef& lc, const T* veff, const Nonlocal<T>& nl,
                     const T* D, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
-                    int64_t ldp, int ns, double shift, double s_h, double s_p, int* status,
-                    cudaStream_t st);
-// TMA plane-ring form (stencil_tma.cu); *used = false when it does not apply.
+                    int64_t ldp, int ns, double shift, double s_h, double s_p, cudaStream_t st);
+// TMA plane-ring form (stencil_tma.cu) of the local part only:
+// y = s_h ((-1/2 Lap + Veff - shift) x) + s_p prev; the nonlocal term follows
+// with nl_apply.  *used = false when the grid or the buffers do not fit it.
+// `status` (device int) receives SPARC_ERR_TIMEOUT if a bounded wait (of
+// `wait_cycles` SM clock cycles) runs out.
 template <typename T>
-cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const Nonlocal<T>& nl,
-                         const T* D, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
-                         int64_t ldp, int ns, double shift, double s_h, double s_p, int* status,
+cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const T* x, int64_t ldx,
+                         T* y, int64_t ldy, const T* prev, int64_t ldp, int ns, double shift,
+                         double s_h, double s_p, long long wait_cycles, int* status,
                          cudaStream_t st, bool* used);
 // Ring plan (stencil_tma.cu): slab rows, ring slots, slot bytes and threads for
 // a grid and element type, or false when the generic kernel must run.
@@ -106,6 +108,47 @@ cudaError_t apply_h_ring_df(const Grid& g, const LapCoef& lc, const float2* veff
                             int64_t ldx, double* y, int64_t ldy, const double* prev, int64_t ldp,
                             int ns, double shift, double s_h, double s_p, int* status,
                             cudaStream_t st, bool* used);
+
+// Nonlocal term by tiles of support points (nonlocal.cu) -----------------
+constexpr int kTilePts = 256;  // support points per tile (= threads per CTA)
+template <typename T>
+struct NlTiles {
+  int ntiles = 0, npairs = 0, kt_max = 0;
+  const int* tile_ptr = nullptr;      // ntiles + 1: each tile's range in pts
+  const int* pts = nullptr;           // support points (grid indices), ascending
+  const int* ent_ptr = nullptr;       // per support point: range of its entries
+  const uint16_t* ent_kl = nullptr;   // entry's tile-local projector index
+  const T* ent_chi = nullptr;         // entry's chi_k(i)
+  const int* kset_ptr = nullptr;      // ntiles + 1: each tile's (tile, k) pairs
+  const int* kset_k = nullptr;        // global projector index of each pair
+  const int* kent_ptr = nullptr;      // npairs + 1: entries of each pair
+  const uint16_t* kent_pt = nullptr;  // tile-local point index (ascending)
+  const T* kent_chi = nullptr;
+  const int* kpair_ptr = nullptr;     // kp + 1: pairs of each projector
+  const int* kpair = nullptr;         // pair indices, ascending (tile order)
+};
+struct NlTilesHost {
+  int tp = 0, kt_max = 0;
+  std::vector<int> tile_ptr, pts, ent_ptr, kset_ptr, kset_k, kent_ptr, kpair_ptr, kpair;
+  std::vector<uint16_t> ent_kl, kent_pt;
+  std::vector<double> ent_chi, kent_chi;
+};
+// Tiles of the support points of the pull table (per grid point: entries
+// pull_ptr[i] .. pull_ptr[i + 1] - 1 of (pull_k, pull_chi)).
+void nl_tiles_build(int64_t nd, const int* pull_ptr, const int* pull_k, const double* pull_chi,
+                    int kp, NlTilesHost& out);
+template <typename T>
+size_t nl_apply_smem(const NlTiles<T>& t);
+// y_i += s_h sum_k chi_k(i) D[n kp + k] at the support points of all ns
+// orbitals; with `part` (npairs x ns) also the per-tile partial sums of
+// chi_k^T y for nl_reduce.
+template <typename T>
+cudaError_t nl_apply(const NlTiles<T>& t, const T* D, int kp, T* y, int64_t ldy, int ns,
+                     double s_h, T* part, cudaStream_t st);
+// D[n kp + k] = gamma_k h3 sum over the tiles of k of part (tile order)
+template <typename T>
+cudaError_t nl_reduce(const NlTiles<T>& t, const T* part, int ns, int kp, const double* gamma,
+                      double h3, T* D, cudaStream_t st);
 
 // D[n * kp + k] = gamma_k h^3 sum_s chi[s][k] x[idx_s + n ldx]
 template <typename T>
@@ -255,7 +298,7 @@ struct sparc_context {
   // nonlocal tables
   sparc::Nonlocal<double> nl64;
   sparc::Nonlocal<float> nl32;
-  void* nl_mem[32] = {};
+  void* nl_mem[64] = {};
   int nl_nmem = 0;
   // workspaces
   void* W1 = nullptr;
@@ -288,6 +331,13 @@ struct sparc_context {
   long long step_launches = 0;
   bool ring_enabled = true;  // TMA-ring stencil (options.reserved[0] bit 0 turns it off)
   bool tc_gemm = true;       // tensor-core projection/rotation (FP64: reserved[0] bit 1 off)
+  // nonlocal term by support-point tiles (ring stencil path); tables of the
+  // handle's working precision, partial sums npairs x ns_max
+  sparc::NlTiles<double> tiles64;
+  sparc::NlTiles<float> tiles32;
+  bool tiles_ok = false;  // the tables of the working precision are built and fit
+  void* part = nullptr;
+  long long wait_cycles = 4000000000LL;  // bound of every device wait (SM clock cycles)
   double* Y64 = nullptr;     // mixed handles: FP64 Yt = H Xt of a step (ld x ns_max)
   float2* veff_df = nullptr; // Veff as (hi, lo) FP32 pairs for the double-FP32 stencil
   bool df_stencil = false;   // FP64 H x in double-FP32 arithmetic (mixed Yt; reserved[0] bit 2)

@@ -1,0 +1,206 @@
+// Nonlocal projector term of H (paper Sec. II A: per atom, a dense projector
+// block applied to the components of X on the atom's support) for blocks of
+// orbitals, after the local stencil (stencil_tma.cu):
+//
+//   nl_apply:  y_i += s_h sum_k chi_k(i) D[k]            (i a support point)
+//              and, from the same updated values, the partial sums
+//              C_t[k] = sum_{i in tile t} chi_k(i) y_i    (next degree's D)
+//   nl_reduce: D[k] = gamma_k h^3 sum_t C_t[k]           (fixed tile order)
+//
+// The support points (grid points inside at least one atom's cut-off sphere)
+// are cut into tiles of kTilePts consecutive points.  A CTA takes one tile and
+// NB orbitals: each thread owns one support point, loads its (k, chi) entries
+// once and applies them to all NB orbitals, with the tile's projector
+// coefficients D for those orbitals staged in shared memory.  The projector
+// tables therefore stream once per NB orbitals instead of once per orbital, and
+// every orbital's values move in coalesced rows.  The partial sums C_t are
+// taken per (tile, projector) pair in point order by one thread each, and the
+// reduction adds the tiles of a projector in tile order: no floating-point
+// atomics, so results are bit-reproducible.
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace sparc {
+
+void nl_tiles_build(int64_t nd, const int* pull_ptr, const int* pull_k, const double* pull_chi,
+                    int kp, NlTilesHost& o) {
+  o = NlTilesHost{};
+  o.tp = kTilePts;
+  // support points and their entries (pull order: atom, then projector)
+  for (int64_t i = 0; i < nd; ++i)
+    if (pull_ptr[i + 1] > pull_ptr[i]) o.pts.push_back((int)i);
+  const int npts = (int)o.pts.size();
+  const int ntiles = (npts + o.tp - 1) / o.tp;
+  o.tile_ptr.resize(ntiles + 1);
+  for (int t = 0; t <= ntiles; ++t) o.tile_ptr[t] = std::min(t * o.tp, npts);
+  o.ent_ptr.assign(npts + 1, 0);
+  o.kset_ptr.assign(ntiles + 1, 0);
+  std::vector<int> local(kp, -1);
+  std::vector<std::vector<std::pair<int, double>>> bykl;  // per tile-local k: (point, chi)
+  for (int t = 0; t < ntiles; ++t) {
+    std::vector<int> ks;
+    bykl.clear();
+    for (int pl = o.tile_ptr[t]; pl < o.tile_ptr[t + 1]; ++pl) {
+      const int i = o.pts[pl];
+      for (int e = pull_ptr[i]; e < pull_ptr[i + 1]; ++e) {
+        const int k = pull_k[e];
+        if (local[k] < 0) {
+          local[k] = (int)ks.size();
+          ks.push_back(k);
+          bykl.emplace_back();
+        }
+        o.ent_kl.push_back((uint16_t)local[k]);
+        o.ent_chi.push_back(pull_chi[e]);
+        bykl[local[k]].emplace_back(pl - o.tile_ptr[t], pull_chi[e]);
+      }
+      o.ent_ptr[pl + 1] = (int)o.ent_kl.size();
+    }
+    o.kt_max = std::max(o.kt_max, (int)ks.size());
+    for (size_t kl = 0; kl < ks.size(); ++kl) {
+      o.kset_k.push_back(ks[kl]);
+      for (const auto& pc : bykl[kl]) {
+        o.kent_pt.push_back((uint16_t)pc.first);
+        o.kent_chi.push_back(pc.second);
+      }
+      o.kent_ptr.push_back((int)o.kent_pt.size());
+      local[ks[kl]] = -1;
+    }
+    o.kset_ptr[t + 1] = (int)o.kset_k.size();
+  }
+  o.kent_ptr.insert(o.kent_ptr.begin(), 0);
+  // pairs of each projector, in tile order
+  o.kpair_ptr.assign(kp + 1, 0);
+  for (int k : o.kset_k) ++o.kpair_ptr[k + 1];
+  for (int k = 0; k < kp; ++k) o.kpair_ptr[k + 1] += o.kpair_ptr[k];
+  o.kpair.resize(o.kset_k.size());
+  std::vector<int> fill(o.kpair_ptr.begin(), o.kpair_ptr.end() - 1);
+  for (int pr = 0; pr < (int)o.kset_k.size(); ++pr) o.kpair[fill[o.kset_k[pr]]++] = pr;
+}
+
+namespace {
+
+template <typename T>
+struct NbOf;
+template <>
+struct NbOf<float> { static constexpr int v = 32; };
+template <>
+struct NbOf<double> { static constexpr int v = 16; };
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(kTilePts)
+    k_nl_apply(const NlTiles<T> t, const T* __restrict__ D, int kp, T* __restrict__ Y,
+               int64_t ldy, int ns, T s_h, T* __restrict__ part) {
+  extern __shared__ __align__(16) uint8_t nl_smem[];
+  const int tile = blockIdx.x;
+  const int nb0 = blockIdx.y * NB;
+  const int nb = min(NB, ns - nb0);
+  const int p0 = t.tile_ptr[tile], np = t.tile_ptr[tile + 1] - p0;
+  const int k0 = t.kset_ptr[tile], nk = t.kset_ptr[tile + 1] - k0;
+  const int KS = nk + 1;        // padded row of Dsh (bank spread)
+  const int YS = kTilePts + 1;  // padded row of ysh
+  T* const Dsh = reinterpret_cast<T*>(nl_smem);  // [NB][KS]
+  T* const ysh = Dsh + NB * KS;                   // [NB][YS]
+  for (int idx = threadIdx.x; idx < NB * nk; idx += blockDim.x) {
+    const int j = idx / nk, kl = idx - j * nk;
+    Dsh[j * KS + kl] = j < nb ? D[(int64_t)(nb0 + j) * kp + t.kset_k[k0 + kl]] : T(0);
+  }
+  __syncthreads();
+  const int pl = threadIdx.x;
+  if (pl < np) {
+    const int64_t i = t.pts[p0 + pl];
+    T y[NB], acc[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      y[j] = j < nb ? Y[(int64_t)(nb0 + j) * ldy + i] : T(0);
+      acc[j] = T(0);
+    }
+    const int e1 = t.ent_ptr[p0 + pl + 1];
+    for (int e = t.ent_ptr[p0 + pl]; e < e1; ++e) {
+      const int kl = t.ent_kl[e];
+      const T c = t.ent_chi[e];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) acc[j] += c * Dsh[j * KS + kl];
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      y[j] += s_h * acc[j];
+      if (j < nb) Y[(int64_t)(nb0 + j) * ldy + i] = y[j];
+      ysh[j * YS + pl] = y[j];
+    }
+  }
+  if (!part) return;
+  __syncthreads();
+  // C_t[k] for this tile's projectors, each (k, orbital) by one thread in point order
+  for (int idx = threadIdx.x; idx < nk * NB; idx += blockDim.x) {
+    const int kl = idx / NB, j = idx - kl * NB;
+    if (j >= nb) continue;
+    const int e1 = t.kent_ptr[k0 + kl + 1];
+    T s = T(0);
+    for (int e = t.kent_ptr[k0 + kl]; e < e1; ++e) s += t.kent_chi[e] * ysh[j * YS + t.kent_pt[e]];
+    part[(int64_t)(k0 + kl) * ns + nb0 + j] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_nl_reduce(const int* __restrict__ kpair_ptr, const int* __restrict__ kpair,
+                            const T* __restrict__ part, int ns, int kp,
+                            const double* __restrict__ gamma, double h3, T* __restrict__ D) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)kp * ns) return;
+  const int k = (int)(idx / ns), n = (int)(idx - (int64_t)k * ns);
+  T s = T(0);
+  for (int p = kpair_ptr[k]; p < kpair_ptr[k + 1]; ++p) s += part[(int64_t)kpair[p] * ns + n];
+  D[(int64_t)n * kp + k] = T(s * (gamma[k] * h3));
+}
+
+}  // namespace
+
+template <typename T>
+size_t nl_apply_smem(const NlTiles<T>& t) {
+  constexpr int NB = NbOf<T>::v;
+  return (size_t)NB * ((size_t)(t.kt_max + 1) + kTilePts + 1) * sizeof(T);
+}
+
+template <typename T>
+cudaError_t nl_apply(const NlTiles<T>& t, const T* D, int kp, T* y, int64_t ldy, int ns,
+                     double s_h, T* part, cudaStream_t st) {
+  if (t.ntiles == 0 || ns < 1) return cudaSuccess;
+  constexpr int NB = NbOf<T>::v;
+  const size_t smem = nl_apply_smem(t);
+  static unsigned long long attr_bits = 0;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = smem_limit_once(&attr_bits, (const void*)k_nl_apply<T, NB>,
+                                          (int)std::min<size_t>(smem, 227 * 1024));
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 grid((unsigned)t.ntiles, (unsigned)((ns + NB - 1) / NB));
+  note_launch(), k_nl_apply<T, NB><<<grid, kTilePts, smem, st>>>(t, D, kp, y, ldy, ns, T(s_h), part);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t nl_reduce(const NlTiles<T>& t, const T* part, int ns, int kp, const double* gamma,
+                      double h3, T* D, cudaStream_t st) {
+  if (t.ntiles == 0 || ns < 1 || kp < 1) return cudaSuccess;
+  const int64_t total = (int64_t)kp * ns;
+  note_launch(), k_nl_reduce<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      t.kpair_ptr, t.kpair, part, ns, kp, gamma, h3, D);
+  return cudaGetLastError();
+}
+
+template size_t nl_apply_smem<float>(const NlTiles<float>&);
+template size_t nl_apply_smem<double>(const NlTiles<double>&);
+template cudaError_t nl_apply<float>(const NlTiles<float>&, const float*, int, float*, int64_t, int,
+                                     double, float*, cudaStream_t);
+template cudaError_t nl_apply<double>(const NlTiles<double>&, const double*, int, double*, int64_t,
+                                      int, double, double*, cudaStream_t);
+template cudaError_t nl_reduce<float>(const NlTiles<float>&, const float*, int, int, const double*,
+                                      double, float*, cudaStream_t);
+template cudaError_t nl_reduce<double>(const NlTiles<double>&, const double*, int, int,
+                                       const double*, double, double*, cudaStream_t);
+
+}  // namespace sparc

@@ -260,14 +260,7 @@ struct TileCfg<double> { static constexpr int VX = 2, BX = 32, BY = 16; };
 template <typename T>
 cudaError_t apply_h(const Grid& g, const LapCoef& lc, const T* veff, const Nonlocal<T>& nl,
                     const T* D, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
-                    int64_t ldp, int ns, double shift, double s_h, double s_p, int* status,
-                    cudaStream_t st) {
-  if (status) {
-    bool used = false;
-    cudaError_t e = apply_h_ring<T>(g, lc, veff, nl, D, x, ldx, y, ldy, prev, ldp, ns, shift,
-                                    s_h, s_p, status, st, &used);
-    if (e != cudaSuccess || used) return e;
-  }
+                    int64_t ldp, int ns, double shift, double s_h, double s_p, cudaStream_t st) {
   using C = TileCfg<T>;
   HArgs<T> a;
   a.x = x; a.ldx = ldx; a.y = y; a.ldy = ldy; a.prev = prev; a.ldp = ldp; a.veff = veff;
@@ -305,11 +298,11 @@ cudaError_t apply_h(const Grid& g, const LapCoef& lc, const T* veff, const Nonlo
 template cudaError_t apply_h<double>(const Grid&, const LapCoef&, const double*,
                                      const Nonlocal<double>&, const double*, const double*,
                                      int64_t, double*, int64_t, const double*, int64_t, int,
-                                     double, double, double, int*, cudaStream_t);
+                                     double, double, double, cudaStream_t);
 template cudaError_t apply_h<float>(const Grid&, const LapCoef&, const float*,
                                     const Nonlocal<float>&, const float*, const float*, int64_t,
                                     float*, int64_t, const float*, int64_t, int, double, double,
-                                    double, int*, cudaStream_t);
+                                    double, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // K2: nonlocal coefficients D[n][k] = gamma_k h^3 sum_t chi_k(t) x_n(t).  One

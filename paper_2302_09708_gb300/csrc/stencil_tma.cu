@@ -1,17 +1,15 @@
-// Hamiltonian application (paper Sec. II A) with a TMA plane ring — the fast
-// form of K1 used when the grid rows are TMA-friendly.
+// Hamiltonian application (paper Sec. II A) with a TMA plane ring: the local
+// part of H (the radius-6 finite-difference Laplacian and Veff) fused with the
+// Chebyshev recurrence axpy, for grids whose rows are TMA-friendly.  The
+// nonlocal projector term is applied afterwards by nl_apply (nonlocal.cu).
 //
 // One CTA owns one orbital and one y-slab of BY rows spanning the full x
 // extent, and marches along z.  For every z-plane a single thread issues TMA
 // loads of the slab plus its 6-row y halos (wrapped for periodic y, zero-filled
 // outside the grid for Dirichlet y; zero-filled planes for Dirichlet z) into a
 // ring of S shared-memory slots, up to S - 7 planes ahead of use, with one
-// full/empty mbarrier pair per slot.  Each thread computes VY = 2 rows x VX
-// consecutive x points: x and y neighbours come from the slot of the current
-// plane (vector shared-memory loads), z neighbours from a 13-deep register
-// queue fed from the ring.  Veff, the nonlocal pull-add and the Chebyshev
-// recurrence axpy are fused as in the generic kernel.  Every mbarrier wait is
-// bounded; on expiry the CTA records SPARC_ERR_TIMEOUT and leaves its loop.
+// full/empty mbarrier pair per slot.  Every mbarrier wait is bounded; on expiry
+// the CTA records SPARC_ERR_TIMEOUT and leaves its loop.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
@@ -27,7 +25,6 @@ namespace {
 
 constexpr int R = kRadius;
 constexpr int VY = 2;
-constexpr long long kWait = 4000000000LL;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -44,12 +41,13 @@ __device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity) {
 }
 // Bounded wait.  Gives up when its own budget runs out (recording the timeout)
 // or as soon as any CTA of the launch has recorded one in the status word.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int* status) {
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int* status,
+                                         long long budget) {
   if (bar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (!bar_test(bar, parity)) {
     if (*(volatile int*)status != 0) return false;
-    if (clock64() - t0 > kWait) {
+    if (clock64() - t0 > budget) {
       atomicCAS(status, 0, SPARC_ERR_TIMEOUT);
       return false;
     }
@@ -86,16 +84,6 @@ __device__ __forceinline__ void ldg(T (&d)[V], const T* p) {
 #pragma unroll
   for (int i = 0; i < V; ++i) d[i] = s[i];
 }
-template <int V>
-__device__ __forceinline__ void ldg_idx(int (&d)[V], const int* p) {
-  if constexpr (V == 4) {
-    const int4 v = __ldg(reinterpret_cast<const int4*>(p));
-    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
-  } else {
-    const int2 v = __ldg(reinterpret_cast<const int2*>(p));
-    d[0] = v.x; d[1] = v.y;
-  }
-}
 template <typename T, int V>
 __device__ __forceinline__ void stg(T* p, const T (&d)[V]) {
   typename Vec<T, V>::t v;
@@ -105,6 +93,36 @@ __device__ __forceinline__ void stg(T* p, const T (&d)[V]) {
   *reinterpret_cast<typename Vec<T, V>::t*>(p) = v;
 }
 
+// Two-lane arithmetic on pairs of neighbouring x points: FP32 pairs run as
+// packed f32x2 instructions (one instruction per two points), FP64 pairs as
+// two scalar operations.
+template <typename T>
+struct Two;
+template <>
+struct Two<float> {
+  using t = float2;
+  static __device__ __forceinline__ t add(t a, t b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ t mul(t a, t b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ t fma(t a, t b, t c) { return __ffma2_rn(a, b, c); }
+  static __device__ __forceinline__ t make(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ t zero() { return make_float2(0.f, 0.f); }
+};
+template <>
+struct Two<double> {
+  using t = double2;
+  static __device__ __forceinline__ t add(t a, t b) {
+    return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+  }
+  static __device__ __forceinline__ t mul(t a, t b) {
+    return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+  }
+  static __device__ __forceinline__ t fma(t a, t b, t c) {
+    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+  }
+  static __device__ __forceinline__ t make(double a, double b) { return make_double2(a, b); }
+  static __device__ __forceinline__ t zero() { return make_double2(0.0, 0.0); }
+};
+
 template <typename T>
 struct RingArgs {
   T* y;
@@ -112,37 +130,50 @@ struct RingArgs {
   const T* prev;
   int64_t ldp;
   const T* veff;
-  const int* grp_ptr;  // grouped nonlocal slots, VX points per group
-  const int* grp_k;
-  const T* grp_chi;
-  const T* D;
-  int kp;
-  uint32_t d_off;  // byte offset of the orbital's D column in dynamic shared memory
   int nx, ny, nz, bcx, bcy, bcz;
   int by;        // slab rows
   int nslab;     // ny / by (rounded up)
   int bz;        // z planes per CTA
   int slots;     // ring depth S
   uint32_t slot_bytes;
-  T diag_minus_shift;
-  T off[R + 1];
-  T s_h, s_p;
+  // coefficients duplicated into both lanes of a pair (kernel-argument
+  // operands of the pair instructions, so they take no registers)
+  typename Two<T>::t dms2;      // (-1/2 Laplacian diagonal) - shift
+  typename Two<T>::t off2[R + 1];  // -1/2 w_p / h^2
+  typename Two<T>::t sh2, sp2;
+  long long wait_cycles;  // bound of every mbarrier wait (SM clock cycles)
   int* status;
 };
 
+// Local part of y = s_h (H - shift) x + s_p prev: the radius-6 Laplacian, Veff
+// and the Chebyshev recurrence axpy.  The nonlocal term is added afterwards by
+// nl_apply (nonlocal.cu), which reads the support points of all orbitals of a
+// block at once.  One CTA owns one orbital and one y-slab (BY rows x full x) and
+// marches along z; TMA loads every plane of the slab with its y halos into a
+// ring of S shared-memory slots.  Each thread computes VY = 2 rows x VX points:
+// y neighbours and the x window come from the current plane's slot, z
+// neighbours from a 13-deep register queue.  The x window is five (FP32) or
+// seven (FP64) aligned vector loads at offsets wrapped once per thread (zero
+// chunks for Dirichlet x), so no thread takes a per-element path.  prev and
+// Veff of plane z + 1 are loaded while plane z is computed.
 template <typename T, int VX>
 __global__ void __launch_bounds__(384, 1)
     k_apply_h_ring(const __grid_constant__ CUtensorMap mid, const __grid_constant__ CUtensorMap halo,
                    const RingArgs<T> a) {
+  using TW = Two<T>;
+  using P = typename TW::t;
+  constexpr int NP = VX / 2;                   // point pairs per row
+  constexpr int WL = (R + VX - 1) / VX * VX;   // window start x - WL (multiple of VX, >= R)
+  constexpr int NC = (2 * WL + VX) / VX;       // window chunks of VX elements
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[16], empty[16];
   __shared__ int abort_sh;
   __shared__ int issued_hi;  // one past the last issued plane
 
   const int nwarps = (blockDim.x + 31) >> 5;
-  const int qpr = a.nx / VX;  // x quads per row
+  const int nq = a.nx / VX;  // x chunks per row
   const int tid = threadIdx.x;
-  const int ry = tid / qpr, qx = tid % qpr;
+  const int ry = tid / nq, qx = tid % nq;
   const int x = qx * VX;
   const int yy = ry * VY;  // first of the thread's two rows within the slab
   const int n = blockIdx.x / a.nslab;
@@ -157,6 +188,7 @@ __global__ void __launch_bounds__(384, 1)
   T* const ring = reinterpret_cast<T*>(smem_raw + (base - su32(smem_raw)));
   const int64_t nxy = (int64_t)a.nx * a.ny;
   const int slab_rows = a.by + 2 * R;
+  const long long wmax = a.wait_cycles;
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -167,9 +199,6 @@ __global__ void __launch_bounds__(384, 1)
     abort_sh = 0;
     issued_hi = z0 - R;
   }
-  // this CTA's orbital column of the nonlocal coefficients D, kept on chip
-  T* const dsh = reinterpret_cast<T*>(smem_raw + (base - su32(smem_raw)) + a.d_off);
-  for (int k = tid; k < a.kp; k += blockDim.x) dsh[k] = __ldg(a.D + (int64_t)n * a.kp + k);
   __syncthreads();
   volatile int* abort = &abort_sh;
   const unsigned full_mask = 0xffffffffu;
@@ -202,13 +231,12 @@ __global__ void __launch_bounds__(384, 1)
   // bounded wait; any timeout aborts the whole CTA
   auto wait = [&](uint32_t bar, uint32_t parity) {
     if (*abort) return false;
-    if (!bar_wait(bar, parity, a.status)) {
+    if (!bar_wait(bar, parity, a.status, wmax)) {
       *abort = 1;
       return false;
     }
     return true;
   };
-  // slot, phase of plane p
   auto slot_of = [&](int p) { return (p - pbase) % S; };
   auto round_of = [&](int p) { return (uint32_t)((p - pbase) / S); };
 
@@ -216,11 +244,34 @@ __global__ void __launch_bounds__(384, 1)
   if (tid == 0)
     for (int p = pbase; p < min(plast, pbase + S); ++p) issue(p);
 
-  T q[2 * R + 1][VY][VX];
+  // x window: chunk c covers x - WL + c VX .. + VX - 1; its row offset wrapped
+  // once here (periodic x), or marked for zero fill (Dirichlet x)
+  int coff[NC];
+  unsigned cvalid = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    int qi = qx - WL / VX + c;
+    bool ok = true;
+    if (qi < 0 || qi >= nq) {
+      ok = a.bcx == SPARC_PERIODIC;
+      qi = ((qi % nq) + nq) % nq;
+    }
+    coff[c] = qi * VX;
+    if (ok) cvalid |= 1u << c;
+  }
+  const bool xdir = a.bcx == SPARC_DIRICHLET;
+
+  auto load_pairs = [&](P (&d)[NP], const T* p) {
+    T t[VX];
+    lds<T, VX>(t, p);
+#pragma unroll
+    for (int u = 0; u < NP; ++u) d[u] = TW::make(t[2 * u], t[2 * u + 1]);
+  };
+
+  P q[2 * R + 1][VY][NP];
   // initial queue: planes z0-R .. z0+R-1.  The first R of them (before z0) serve
   // only the queue, so each is released as soon as it is read and its slot is
-  // refilled at once: the ring then needs only 2R - R + 1 = R + 1 < S slots of
-  // look-ahead here instead of all 2R planes at the same time.
+  // refilled at once.
 #pragma unroll
   for (int j = 0; j < 2 * R; ++j) {
     const int p = pbase + j;
@@ -228,7 +279,7 @@ __global__ void __launch_bounds__(384, 1)
     wait(su32(&full[s]), round_of(p) & 1);
     const T* row = ring + (size_t)s * (a.slot_bytes / sizeof(T));
 #pragma unroll
-    for (int r = 0; r < VY; ++r) lds<T, VX>(q[j][r], row + (R + yy + r) * rowe + x);
+    for (int r = 0; r < VY; ++r) load_pairs(q[j][r], row + (R + yy + r) * rowe + x);
     if (j < R) {
       __syncwarp();
       if ((tid & 31) == 0)
@@ -243,27 +294,36 @@ __global__ void __launch_bounds__(384, 1)
   T* __restrict__ yn = a.y + (int64_t)n * a.ldy;
   const T* __restrict__ pn = a.prev ? a.prev + (int64_t)n * a.ldp : nullptr;
   const int gy0 = y0 + yy;
+  bool rowok[VY];
+#pragma unroll
+  for (int r = 0; r < VY; ++r) rowok[r] = gy0 + r < a.ny;
 
-  for (int z = z0; z < z1; ++z) {
-    if (__shfl_sync(full_mask, *abort, 0)) break;
-    // Veff, prev and the nonlocal slot range of this plane (used after the
-    // stencil sums, which cover their latency)
-    const int64_t g0 = z * nxy + (int64_t)gy0 * a.nx + x;
-    T vf[VY][VX], pv[VY][VX];
-    int gs[VY], ge[VY];
+  // Veff and prev of plane zz at the thread's points
+  auto load_vp = [&](int zz, P (&vf)[VY][NP], P (&pv)[VY][NP]) {
+    const int64_t g0 = zz * nxy + (int64_t)gy0 * a.nx + x;
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
-      gs[r] = ge[r] = 0;
-      if (gy0 + r < a.ny) {
-        ldg<T, VX>(vf[r], a.veff + g0 + r * a.nx);
-        if (pn) ldg<T, VX>(pv[r], pn + g0 + r * a.nx);
-        if (a.kp > 0) {
-          const int64_t q = (g0 + r * a.nx) / VX;
-          gs[r] = __ldg(a.grp_ptr + q);
-          ge[r] = __ldg(a.grp_ptr + q + 1);
-        }
+      T t[VX], u[VX];
+#pragma unroll
+      for (int v = 0; v < VX; ++v) t[v] = u[v] = T(0);
+      if (rowok[r]) {
+        ldg<T, VX>(t, a.veff + g0 + r * a.nx);
+        if (pn) ldg<T, VX>(u, pn + g0 + r * a.nx);
+      }
+#pragma unroll
+      for (int w = 0; w < NP; ++w) {
+        vf[r][w] = TW::make(t[2 * w], t[2 * w + 1]);
+        pv[r][w] = TW::make(u[2 * w], u[2 * w + 1]);
       }
     }
+  };
+
+  // Veff and prev of the current plane; reloaded for the next plane right
+  // after the store, so their latency is covered by one plane of work
+  P vc[VY][NP], pc[VY][NP];
+  load_vp(z0, vc, pc);
+  for (int z = z0; z < z1; ++z) {
+    if (__shfl_sync(full_mask, *abort, 0)) break;
     // push plane z + R into the queue
     {
       const int p = z + R;
@@ -272,66 +332,43 @@ __global__ void __launch_bounds__(384, 1)
       if (!__all_sync(full_mask, got)) break;
       const T* row = ring + (size_t)s * (a.slot_bytes / sizeof(T));
 #pragma unroll
-      for (int r = 0; r < VY; ++r) lds<T, VX>(q[2 * R][r], row + (R + yy + r) * rowe + x);
+      for (int r = 0; r < VY; ++r) load_pairs(q[2 * R][r], row + (R + yy + r) * rowe + x);
     }
     const int sz = slot_of(z);
     const T* pl = ring + (size_t)sz * (a.slot_bytes / sizeof(T));
-    T acc[VY][VX];
-#pragma unroll
-    for (int r = 0; r < VY; ++r)
-#pragma unroll
-      for (int v = 0; v < VX; ++v) acc[r][v] = a.diag_minus_shift * q[R][r][v];
-    // y and z neighbours
-#pragma unroll
-    for (int p = 1; p <= R; ++p) {
-      T up[VY][VX], dn[VY][VX];
-#pragma unroll
-      for (int r = 0; r < VY; ++r) {
-        lds<T, VX>(up[r], pl + (R + yy + r + p) * rowe + x);
-        lds<T, VX>(dn[r], pl + (R + yy + r - p) * rowe + x);
-      }
-#pragma unroll
-      for (int r = 0; r < VY; ++r)
-#pragma unroll
-        for (int v = 0; v < VX; ++v)
-          acc[r][v] += a.off[p] * ((up[r][v] + dn[r][v]) + (q[R + p][r][v] + q[R - p][r][v]));
-    }
-    // x neighbours
+    P acc[VY][NP];
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
       const T* rowp = pl + (R + yy + r) * rowe;
-      // window x - R .. x + VX - 1 + R; interior threads read it with aligned
-      // vector loads starting at x - WL (bank-conflict free), edge threads wrap
-      T w[VX + 2 * R];
-      constexpr int WL = (R + VX - 1) / VX * VX;  // >= R, multiple of VX
-      constexpr int NV = (2 * WL + VX) / VX;
-      if (x >= WL && x + VX + WL <= a.nx) {
-        T buf[NV * VX];
+      // x window of this row
+      T b[NC * VX];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-          T t4[VX];
-          lds<T, VX>(t4, rowp + x - WL + k * VX);
+      for (int c = 0; c < NC; ++c) {
+        T t[VX];
+        lds<T, VX>(t, rowp + coff[c]);
+        if (xdir && !((cvalid >> c) & 1u)) {
 #pragma unroll
-          for (int v = 0; v < VX; ++v) buf[k * VX + v] = t4[v];
+          for (int v = 0; v < VX; ++v) t[v] = T(0);
         }
 #pragma unroll
-        for (int i = 0; i < VX + 2 * R; ++i) w[i] = buf[i + WL - R];
-      } else {
-#pragma unroll
-        for (int i = 0; i < VX + 2 * R; ++i) {
-          int xx = x - R + i;
-          bool inside = true;
-          if (xx < 0 || xx >= a.nx) {
-            if (a.bcx == SPARC_DIRICHLET) inside = false;
-            else xx = xx < 0 ? xx + a.nx : xx - a.nx;
-          }
-          w[i] = inside ? rowp[xx] : T(0);
-        }
+        for (int v = 0; v < VX; ++v) b[c * VX + v] = t[v];
       }
 #pragma unroll
-      for (int p = 1; p <= R; ++p)
+      for (int u = 0; u < NP; ++u) acc[r][u] = TW::mul(TW::add(a.dms2, vc[r][u]), q[R][r][u]);
 #pragma unroll
-        for (int v = 0; v < VX; ++v) acc[r][v] += a.off[p] * (w[R + v + p] + w[R + v - p]);
+      for (int p = 1; p <= R; ++p) {
+        P up[NP], dn[NP];
+        load_pairs(up, pl + (R + yy + r + p) * rowe + x);
+        load_pairs(dn, pl + (R + yy + r - p) * rowe + x);
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
+          const int o = WL + 2 * u;
+          const P xs = TW::add(TW::make(b[o + p], b[o + 1 + p]), TW::make(b[o - p], b[o + 1 - p]));
+          const P ys = TW::add(up[u], dn[u]);
+          const P zs = TW::add(q[R + p][r][u], q[R - p][r][u]);
+          acc[r][u] = TW::fma(a.off2[p], TW::add(TW::add(ys, zs), xs), acc[r][u]);
+        }
+      }
     }
     // release the slot of plane z (all warps), refill it with plane z + S
     __syncwarp();
@@ -341,56 +378,35 @@ __global__ void __launch_bounds__(384, 1)
       if (wait(su32(&empty[sz]), round_of(z) & 1)) issue(z + S);
     }
     __syncwarp();
-    // Veff, nonlocal pull-add (one slot = VX (k, chi) pairs), recurrence, store
+    // recurrence and store
+    const int64_t g0 = z * nxy + (int64_t)gy0 * a.nx + x;
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
-      if (gy0 + r >= a.ny) continue;
-      const int64_t g = g0 + r * a.nx;
-      T h[VX];
-#pragma unroll
-      for (int v = 0; v < VX; ++v) h[v] = acc[r][v] + vf[r][v] * q[R][r][v];
-      // up to four slots' loads in flight before their FMAs (the loads are L2
-      // round trips; one at a time they would serialise)
-      for (int sl = gs[r]; sl < ge[r]; sl += 4) {
-        int kk[4][VX];
-        T ch[4][VX];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (sl + u < ge[r]) {
-            ldg_idx<VX>(kk[u], a.grp_k + (int64_t)(sl + u) * VX);
-            ldg<T, VX>(ch[u], a.grp_chi + (int64_t)(sl + u) * VX);
-          } else {
-#pragma unroll
-            for (int v = 0; v < VX; ++v) {
-              kk[u][v] = 0;
-              ch[u][v] = T(0);
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < VX; ++v) h[v] += ch[u][v] * dsh[kk[u][v]];
-      }
+      if (!rowok[r]) continue;
       T out[VX];
 #pragma unroll
-      for (int v = 0; v < VX; ++v) out[v] = pn ? a.s_h * h[v] + a.s_p * pv[r][v] : a.s_h * h[v];
-      stg<T, VX>(yn + g, out);
+      for (int u = 0; u < NP; ++u) {
+        const P o2 = pn ? TW::fma(a.sh2, acc[r][u], TW::mul(a.sp2, pc[r][u]))
+                        : TW::mul(a.sh2, acc[r][u]);
+        out[2 * u] = o2.x;
+        out[2 * u + 1] = o2.y;
+      }
+      stg<T, VX>(yn + g0 + r * a.nx, out);
     }
-
+    if (z + 1 < z1) load_vp(z + 1, vc, pc);
 #pragma unroll
     for (int j = 0; j < 2 * R; ++j)
 #pragma unroll
       for (int r = 0; r < VY; ++r)
 #pragma unroll
-        for (int v = 0; v < VX; ++v) q[j][r][v] = q[j + 1][r][v];
+        for (int u = 0; u < NP; ++u) q[j][r][u] = q[j + 1][r][u];
   }
   // drain: every issued load must have landed before the CTA exits
   if (tid == 0) {
     const int hi = issued_hi;
     for (int p = max(pbase, hi - S); p < hi; ++p) {
       const long long t0 = clock64();
-      while (!bar_test(su32(&full[slot_of(p)]), round_of(p) & 1) && clock64() - t0 < kWait) {
+      while (!bar_test(su32(&full[slot_of(p)]), round_of(p) & 1) && clock64() - t0 < wmax) {
       }
     }
   }
@@ -461,16 +477,15 @@ bool ring_plan(const Grid& g, int kp, int& by, int& slots, uint32_t& slot_bytes,
 }
 
 template <typename T>
-cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const Nonlocal<T>& nl,
-                         const T* D, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
-                         int64_t ldp, int ns, double shift, double s_h, double s_p, int* status,
+cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const T* x, int64_t ldx,
+                         T* y, int64_t ldy, const T* prev, int64_t ldp, int ns, double shift,
+                         double s_h, double s_p, long long wait_cycles, int* status,
                          cudaStream_t st, bool* used) {
   *used = false;
   constexpr int VX = sizeof(T) == 4 ? 4 : 2;
   int by, slots, threads;
   uint32_t slot_bytes;
-  if (!ring_plan<T>(g, nl.kp, by, slots, slot_bytes, threads)) return cudaSuccess;
-  if (nl.kp > 0 && (!nl.grp_ptr || nl.grp != VX)) return cudaSuccess;
+  if (!ring_plan<T>(g, 0, by, slots, slot_bytes, threads)) return cudaSuccess;
   const int va = 16 / sizeof(T);
   if (ldx % va || ldy % va || (prev && ldp % va) || ((uintptr_t)x % 16) || ((uintptr_t)y % 16) ||
       (prev && ((uintptr_t)prev % 16)) || ((uintptr_t)veff % 16))
@@ -480,16 +495,17 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
     return cudaSuccess;
   RingArgs<T> a;
   a.y = y; a.ldy = ldy; a.prev = prev; a.ldp = ldp; a.veff = veff;
-  a.grp_ptr = nl.grp_ptr; a.grp_k = nl.grp_k; a.grp_chi = nl.grp_chi; a.D = D; a.kp = nl.kp;
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.bcx = g.bc[0]; a.bcy = g.bc[1]; a.bcz = g.bc[2];
   a.by = by;
   a.nslab = (g.ny + by - 1) / by;
   a.slots = slots;
   a.slot_bytes = slot_bytes;
-  a.diag_minus_shift = T(lc.diag - shift);
-  for (int p = 0; p <= R; ++p) a.off[p] = T(lc.off[p]);
-  a.s_h = T(s_h);
-  a.s_p = T(s_p);
+  const T dms = T(lc.diag - shift);
+  a.dms2 = {dms, dms};
+  for (int p = 0; p <= R; ++p) a.off2[p] = {T(lc.off[p]), T(lc.off[p])};
+  a.sh2 = {T(s_h), T(s_h)};
+  a.sp2 = {T(s_p), T(s_p)};
+  a.wait_cycles = wait_cycles;
   a.status = status;
   // z split: enough CTAs to cover the SMs a few times
   const int64_t xy = (int64_t)a.nslab * ns;
@@ -497,8 +513,7 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
   nzc = std::min(nzc, std::max(1, g.nz / 16));
   a.bz = (g.nz + nzc - 1) / nzc;
   nzc = (g.nz + a.bz - 1) / a.bz;
-  a.d_off = (uint32_t)slots * slot_bytes;
-  const size_t smem = (size_t)slots * slot_bytes + (size_t)nl.kp * sizeof(T) + 128;
+  const size_t smem = (size_t)slots * slot_bytes + 128;
   static unsigned long long attr_bits = 0;
   cudaError_t ae = smem_limit_once(&attr_bits, (const void*)k_apply_h_ring<T, VX>, 210 * 1024);
   if (ae != cudaSuccess) return ae;
@@ -510,13 +525,13 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
 
 template bool ring_plan<float>(const Grid&, int, int&, int&, uint32_t&, int&);
 template bool ring_plan<double>(const Grid&, int, int&, int&, uint32_t&, int&);
-template cudaError_t apply_h_ring<float>(const Grid&, const LapCoef&, const float*,
-                                         const Nonlocal<float>&, const float*, const float*,
+template cudaError_t apply_h_ring<float>(const Grid&, const LapCoef&, const float*, const float*,
                                          int64_t, float*, int64_t, const float*, int64_t, int,
-                                         double, double, double, int*, cudaStream_t, bool*);
+                                         double, double, double, long long, int*, cudaStream_t,
+                                         bool*);
 template cudaError_t apply_h_ring<double>(const Grid&, const LapCoef&, const double*,
-                                          const Nonlocal<double>&, const double*, const double*,
-                                          int64_t, double*, int64_t, const double*, int64_t, int,
-                                          double, double, double, int*, cudaStream_t, bool*);
+                                          const double*, int64_t, double*, int64_t, const double*,
+                                          int64_t, int, double, double, double, long long, int*,
+                                          cudaStream_t, bool*);
 
 }  // namespace sparc
