@@ -24,7 +24,6 @@ namespace sparc {
 namespace {
 
 constexpr int R = kRadius;
-constexpr int VY = 2;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -147,16 +146,17 @@ struct RingArgs {
 
 // Local part of y = s_h (H - shift) x + s_p prev: the radius-6 Laplacian, Veff
 // and the Chebyshev recurrence axpy.  The nonlocal term is added afterwards by
-// nl_apply (nonlocal.cu), which reads the support points of all orbitals of a
-// block at once.  One CTA owns one orbital and one y-slab (BY rows x full x) and
-// marches along z; TMA loads every plane of the slab with its y halos into a
-// ring of S shared-memory slots.  Each thread computes VY = 2 rows x VX points:
-// y neighbours and the x window come from the current plane's slot, z
-// neighbours from a 13-deep register queue.  The x window is five (FP32) or
-// seven (FP64) aligned vector loads at offsets wrapped once per thread (zero
-// chunks for Dirichlet x), so no thread takes a per-element path.  prev and
-// Veff of plane z + 1 are loaded while plane z is computed.
-template <typename T, int VX>
+// nl_apply (nonlocal.cu), which reads the support points of a block of
+// orbitals at once.  One CTA owns one orbital and one y-slab (BY rows x full x)
+// and marches along z; TMA loads every plane of the slab with its y halos into
+// a ring of S shared-memory slots.  Each thread computes VY rows x VX points per
+// plane and U planes per step: y neighbours and the x window come from the
+// plane's slot, z neighbours from a register queue of 2R + U planes that moves
+// by U planes per step.  The x window is NC aligned vector loads at offsets
+// wrapped once per thread (zero chunks for Dirichlet x), so no thread takes a
+// per-element path.  Even x distances are summed as pairs, odd ones (whose
+// pairs straddle two vector registers) as two scalar adds.
+template <typename T, int VX, int VY, int U, bool XDIR>
 __global__ void __launch_bounds__(384, 1)
     k_apply_h_ring(const __grid_constant__ CUtensorMap mid, const __grid_constant__ CUtensorMap halo,
                    const RingArgs<T> a) {
@@ -165,8 +165,10 @@ __global__ void __launch_bounds__(384, 1)
   constexpr int NP = VX / 2;                   // point pairs per row
   constexpr int WL = (R + VX - 1) / VX * VX;   // window start x - WL (multiple of VX, >= R)
   constexpr int NC = (2 * WL + VX) / VX;       // window chunks of VX elements
+  constexpr int Q = 2 * R + U;                 // queue depth (planes)
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[16], empty[16];
+  __shared__ int released[16];  // warps that have released each slot this round
   __shared__ int abort_sh;
   __shared__ int issued_hi;  // one past the last issued plane
 
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(384, 1)
   const int tid = threadIdx.x;
   const int ry = tid / nq, qx = tid % nq;
   const int x = qx * VX;
-  const int yy = ry * VY;  // first of the thread's two rows within the slab
+  const int yy = ry * VY;  // first of the thread's rows within the slab
   const int n = blockIdx.x / a.nslab;
   const int slab = blockIdx.x % a.nslab;
   const int y0 = slab * a.by;
@@ -184,6 +186,7 @@ __global__ void __launch_bounds__(384, 1)
   const int pbase = z0 - R;
   const int S = a.slots;
   const int rowe = a.nx;  // elements per shared row
+  const int slot_elems = (int)(a.slot_bytes / sizeof(T));
   const uint32_t base = (su32(smem_raw) + 127u) & ~127u;
   T* const ring = reinterpret_cast<T*>(smem_raw + (base - su32(smem_raw)));
   const int64_t nxy = (int64_t)a.nx * a.ny;
@@ -194,6 +197,7 @@ __global__ void __launch_bounds__(384, 1)
     for (int s = 0; s < S; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[s])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&empty[s])), "r"(nwarps));
+      released[s] = 0;
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_sh = 0;
@@ -203,10 +207,8 @@ __global__ void __launch_bounds__(384, 1)
   volatile int* abort = &abort_sh;
   const unsigned full_mask = 0xffffffffu;
 
-  // issue plane p into its slot (thread 0 only)
-  auto issue = [&](int p) {
-    const int k = p - pbase;
-    const int s = k % S;
+  // plane p (in slot s) to the ring
+  auto issue = [&](int p, int s) {
     const uint32_t fb = su32(&full[s]);
     const uint32_t dst = base + (uint32_t)s * a.slot_bytes;
     int zc = p;
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(384, 1)
     tma4(dst, &halo, 0, yt, zc, n, fb);
     tma4(dst + R * rb, &mid, 0, y0, zc, n, fb);
     tma4(dst + (R + a.by) * rb, &halo, 0, yb, zc, n, fb);
-    issued_hi = p + 1;
+    atomicMax(&issued_hi, p + 1);
   };
   // bounded wait; any timeout aborts the whole CTA
   auto wait = [&](uint32_t bar, uint32_t parity) {
@@ -237,12 +239,31 @@ __global__ void __launch_bounds__(384, 1)
     }
     return true;
   };
-  auto slot_of = [&](int p) { return (p - pbase) % S; };
-  auto round_of = [&](int p) { return (uint32_t)((p - pbase) / S); };
+  // slot and round of a plane, advanced one plane at a time (no division)
+  struct Pos {
+    int s, r;
+  };
+  auto advance = [&](Pos& q) {
+    if (++q.s == S) {
+      q.s = 0;
+      ++q.r;
+    }
+  };
 
   const int plast = z1 + R;  // planes [pbase, plast) are needed
   if (tid == 0)
-    for (int p = pbase; p < min(plast, pbase + S); ++p) issue(p);
+    for (int p = pbase; p < min(plast, pbase + S); ++p) issue(p, p - pbase);
+  // Release plane p's slot (lane 0 of every warp, after the warp's reads).  The
+  // last warp to release it refills it with plane p + S, once the slot's empty
+  // barrier has completed (bounded wait; it completes with that last arrival),
+  // so no warp waits for the others and the ring stays S - 7 planes ahead.
+  auto release = [&](int p, Pos ps) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&empty[ps.s])) : "memory");
+    if (atomicAdd(&released[ps.s], 1) == nwarps - 1) {
+      released[ps.s] = 0;
+      if (p + S < plast && wait(su32(&empty[ps.s]), ps.r & 1)) issue(p + S, ps.s);
+    }
+  };
 
   // x window: chunk c covers x - WL + c VX .. + VX - 1; its row offset wrapped
   // once here (periodic x), or marked for zero fill (Dirichlet x)
@@ -253,13 +274,12 @@ __global__ void __launch_bounds__(384, 1)
     int qi = qx - WL / VX + c;
     bool ok = true;
     if (qi < 0 || qi >= nq) {
-      ok = a.bcx == SPARC_PERIODIC;
+      ok = !XDIR;
       qi = ((qi % nq) + nq) % nq;
     }
     coff[c] = qi * VX;
     if (ok) cvalid |= 1u << c;
   }
-  const bool xdir = a.bcx == SPARC_DIRICHLET;
 
   auto load_pairs = [&](P (&d)[NP], const T* p) {
     T t[VX];
@@ -268,26 +288,25 @@ __global__ void __launch_bounds__(384, 1)
     for (int u = 0; u < NP; ++u) d[u] = TW::make(t[2 * u], t[2 * u + 1]);
   };
 
-  P q[2 * R + 1][VY][NP];
+  P q[Q][VY][NP];
   // initial queue: planes z0-R .. z0+R-1.  The first R of them (before z0) serve
   // only the queue, so each is released as soon as it is read and its slot is
   // refilled at once.
+  {
+    Pos ps{0, 0};
 #pragma unroll
-  for (int j = 0; j < 2 * R; ++j) {
-    const int p = pbase + j;
-    const int s = slot_of(p);
-    wait(su32(&full[s]), round_of(p) & 1);
-    const T* row = ring + (size_t)s * (a.slot_bytes / sizeof(T));
+    for (int j = 0; j < 2 * R; ++j) {
+      const int p = pbase + j;
+      wait(su32(&full[ps.s]), ps.r & 1);
+      const T* row = ring + (size_t)ps.s * slot_elems;
 #pragma unroll
-    for (int r = 0; r < VY; ++r) load_pairs(q[j][r], row + (R + yy + r) * rowe + x);
-    if (j < R) {
-      __syncwarp();
-      if ((tid & 31) == 0)
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&empty[s]))
-                     : "memory");
-      if (tid == 0 && p + S < plast)
-        if (wait(su32(&empty[s]), round_of(p) & 1)) issue(p + S);
-      __syncwarp();
+      for (int r = 0; r < VY; ++r) load_pairs(q[j][r], row + (R + yy + r) * rowe + x);
+      if (j < R) {
+        __syncwarp();
+        if ((tid & 31) == 0) release(p, ps);
+        __syncwarp();
+      }
+      advance(ps);
     }
   }
 
@@ -298,115 +317,129 @@ __global__ void __launch_bounds__(384, 1)
 #pragma unroll
   for (int r = 0; r < VY; ++r) rowok[r] = gy0 + r < a.ny;
 
-  // Veff and prev of plane zz at the thread's points
-  auto load_vp = [&](int zz, P (&vf)[VY][NP], P (&pv)[VY][NP]) {
-    const int64_t g0 = zz * nxy + (int64_t)gy0 * a.nx + x;
-#pragma unroll
-    for (int r = 0; r < VY; ++r) {
-      T t[VX], u[VX];
-#pragma unroll
-      for (int v = 0; v < VX; ++v) t[v] = u[v] = T(0);
-      if (rowok[r]) {
-        ldg<T, VX>(t, a.veff + g0 + r * a.nx);
-        if (pn) ldg<T, VX>(u, pn + g0 + r * a.nx);
-      }
-#pragma unroll
-      for (int w = 0; w < NP; ++w) {
-        vf[r][w] = TW::make(t[2 * w], t[2 * w + 1]);
-        pv[r][w] = TW::make(u[2 * w], u[2 * w + 1]);
-      }
-    }
-  };
-
-  // Veff and prev of the current plane; reloaded for the next plane right
-  // after the store, so their latency is covered by one plane of work
-  P vc[VY][NP], pc[VY][NP];
-  load_vp(z0, vc, pc);
-  for (int z = z0; z < z1; ++z) {
+  // slot/round of the next plane to push (z + R) and of the next plane to compute (z)
+  Pos push{(2 * R) % S, (2 * R) / S};
+  Pos cur{R % S, R / S};
+  for (int z = z0; z < z1; z += U) {
     if (__shfl_sync(full_mask, *abort, 0)) break;
-    // push plane z + R into the queue
-    {
-      const int p = z + R;
-      const int s = slot_of(p);
-      const bool got = wait(su32(&full[s]), round_of(p) & 1);
-      if (!__all_sync(full_mask, got)) break;
-      const T* row = ring + (size_t)s * (a.slot_bytes / sizeof(T));
+    const int nu = min(U, z1 - z);
+    // push planes z + R .. z + R + nu - 1 into the queue
+    bool got = true;
 #pragma unroll
-      for (int r = 0; r < VY; ++r) load_pairs(q[2 * R][r], row + (R + yy + r) * rowe + x);
+    for (int t = 0; t < U; ++t) {
+      if (t < nu) {
+        got = got && wait(su32(&full[push.s]), push.r & 1);
+        const T* row = ring + (size_t)push.s * slot_elems;
+#pragma unroll
+        for (int r = 0; r < VY; ++r) load_pairs(q[2 * R + t][r], row + (R + yy + r) * rowe + x);
+        advance(push);
+      }
     }
-    const int sz = slot_of(z);
-    const T* pl = ring + (size_t)sz * (a.slot_bytes / sizeof(T));
-    P acc[VY][NP];
+    if (!__all_sync(full_mask, got)) break;
 #pragma unroll
-    for (int r = 0; r < VY; ++r) {
-      const T* rowp = pl + (R + yy + r) * rowe;
-      // x window of this row
-      T b[NC * VX];
+    for (int t = 0; t < U; ++t) {
+      if (t >= nu) break;
+      const int zz = z + t;
+      // Veff and prev of this plane, used after the neighbour sums
+      const int64_t g0 = zz * nxy + (int64_t)gy0 * a.nx + x;
+      P vc[VY][NP], pc[VY][NP];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        T t[VX];
-        lds<T, VX>(t, rowp + coff[c]);
-        if (xdir && !((cvalid >> c) & 1u)) {
+      for (int r = 0; r < VY; ++r) {
+        T tv[VX], tp[VX];
 #pragma unroll
-          for (int v = 0; v < VX; ++v) t[v] = T(0);
+        for (int v = 0; v < VX; ++v) tv[v] = tp[v] = T(0);
+        if (rowok[r]) {
+          ldg<T, VX>(tv, a.veff + g0 + r * a.nx);
+          if (pn) ldg<T, VX>(tp, pn + g0 + r * a.nx);
         }
 #pragma unroll
-        for (int v = 0; v < VX; ++v) b[c * VX + v] = t[v];
+        for (int w = 0; w < NP; ++w) {
+          vc[r][w] = TW::make(tv[2 * w], tv[2 * w + 1]);
+          pc[r][w] = TW::make(tp[2 * w], tp[2 * w + 1]);
+        }
       }
+      const T* pl = ring + (size_t)cur.s * slot_elems;
+      // even and odd neighbour distances accumulate separately (two independent
+      // dependency chains)
+      P acc[VY][NP], acc1[VY][NP];
 #pragma unroll
-      for (int u = 0; u < NP; ++u) acc[r][u] = TW::mul(TW::add(a.dms2, vc[r][u]), q[R][r][u]);
+      for (int r = 0; r < VY; ++r) {
+        const T* rowp = pl + (R + yy + r) * rowe;
+        T b[NC * VX];
 #pragma unroll
-      for (int p = 1; p <= R; ++p) {
-        P up[NP], dn[NP];
-        load_pairs(up, pl + (R + yy + r + p) * rowe + x);
-        load_pairs(dn, pl + (R + yy + r - p) * rowe + x);
+        for (int c = 0; c < NC; ++c) {
+          T tt[VX];
+          lds<T, VX>(tt, rowp + coff[c]);
+          if (XDIR && !((cvalid >> c) & 1u)) {
+#pragma unroll
+            for (int v = 0; v < VX; ++v) tt[v] = T(0);
+          }
+#pragma unroll
+          for (int v = 0; v < VX; ++v) b[c * VX + v] = tt[v];
+        }
 #pragma unroll
         for (int u = 0; u < NP; ++u) {
-          const int o = WL + 2 * u;
-          const P xs = TW::add(TW::make(b[o + p], b[o + 1 + p]), TW::make(b[o - p], b[o + 1 - p]));
-          const P ys = TW::add(up[u], dn[u]);
-          const P zs = TW::add(q[R + p][r][u], q[R - p][r][u]);
-          acc[r][u] = TW::fma(a.off2[p], TW::add(TW::add(ys, zs), xs), acc[r][u]);
+          acc[r][u] = TW::mul(a.dms2, q[R + t][r][u]);
+          acc1[r][u] = TW::zero();
+        }
+#pragma unroll
+        for (int p = 1; p <= R; ++p) {
+          P up[NP], dn[NP];
+          load_pairs(up, pl + (R + yy + r + p) * rowe + x);
+          load_pairs(dn, pl + (R + yy + r - p) * rowe + x);
+#pragma unroll
+          for (int u = 0; u < NP; ++u) {
+            const int o = WL + 2 * u;
+            P xs;
+            if (p & 1)  // b[o + p] starts a pair only for even p
+              xs = TW::make(b[o + p] + b[o - p], b[o + 1 + p] + b[o + 1 - p]);
+            else
+              xs = TW::add(TW::make(b[o + p], b[o + 1 + p]), TW::make(b[o - p], b[o + 1 - p]));
+            const P ys = TW::add(up[u], dn[u]);
+            const P zs = TW::add(q[R + t + p][r][u], q[R + t - p][r][u]);
+            const P sum = TW::add(TW::add(ys, zs), xs);
+            if (p & 1)
+              acc1[r][u] = TW::fma(a.off2[p], sum, acc1[r][u]);
+            else
+              acc[r][u] = TW::fma(a.off2[p], sum, acc[r][u]);
+          }
         }
       }
-    }
-    // release the slot of plane z (all warps), refill it with plane z + S
-    __syncwarp();
-    if ((tid & 31) == 0)
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&empty[sz])) : "memory");
-    if (tid == 0 && z + S < plast) {
-      if (wait(su32(&empty[sz]), round_of(z) & 1)) issue(z + S);
-    }
-    __syncwarp();
-    // recurrence and store
-    const int64_t g0 = z * nxy + (int64_t)gy0 * a.nx + x;
+      // release the slot of plane zz (the last warp refills it)
+      __syncwarp();
+      if ((tid & 31) == 0) release(zz, cur);
+      __syncwarp();
+      advance(cur);
+      // Veff, recurrence and store
 #pragma unroll
-    for (int r = 0; r < VY; ++r) {
-      if (!rowok[r]) continue;
-      T out[VX];
+      for (int r = 0; r < VY; ++r) {
+        if (!rowok[r]) continue;
+        T out[VX];
 #pragma unroll
-      for (int u = 0; u < NP; ++u) {
-        const P o2 = pn ? TW::fma(a.sh2, acc[r][u], TW::mul(a.sp2, pc[r][u]))
-                        : TW::mul(a.sh2, acc[r][u]);
-        out[2 * u] = o2.x;
-        out[2 * u + 1] = o2.y;
+        for (int u = 0; u < NP; ++u) {
+          const P h = TW::fma(vc[r][u], q[R + t][r][u], TW::add(acc[r][u], acc1[r][u]));
+          const P o2 = pn ? TW::fma(a.sh2, h, TW::mul(a.sp2, pc[r][u])) : TW::mul(a.sh2, h);
+          out[2 * u] = o2.x;
+          out[2 * u + 1] = o2.y;
+        }
+        stg<T, VX>(yn + g0 + r * a.nx, out);
       }
-      stg<T, VX>(yn + g0 + r * a.nx, out);
     }
-    if (z + 1 < z1) load_vp(z + 1, vc, pc);
 #pragma unroll
     for (int j = 0; j < 2 * R; ++j)
 #pragma unroll
       for (int r = 0; r < VY; ++r)
 #pragma unroll
-        for (int u = 0; u < NP; ++u) q[j][r][u] = q[j + 1][r][u];
+        for (int u = 0; u < NP; ++u) q[j][r][u] = q[j + U][r][u];
   }
   // drain: every issued load must have landed before the CTA exits
+  __syncthreads();
   if (tid == 0) {
     const int hi = issued_hi;
     for (int p = max(pbase, hi - S); p < hi; ++p) {
+      const int k = p - pbase;
       const long long t0 = clock64();
-      while (!bar_test(su32(&full[slot_of(p)]), round_of(p) & 1) && clock64() - t0 < wmax) {
+      while (!bar_test(su32(&full[k % S]), (k / S) & 1) && clock64() - t0 < wmax) {
       }
     }
   }
@@ -446,7 +479,9 @@ bool block_map(CUtensorMap* m, const T* x, int64_t ldx, const Grid& g, int ns, i
 
 }  // namespace
 
-// Ring-kernel plan for a grid/dtype, or false if the generic kernel must be used.
+// Plan of the double-FP32 ring kernel (stencil_df.cu: two rows per thread, the
+// nonlocal coefficients D staged in shared memory), or false if the generic
+// kernel must be used.
 template <typename T>
 bool ring_plan(const Grid& g, int kp, int& by, int& slots, uint32_t& slot_bytes, int& threads) {
   constexpr int VX = sizeof(T) == 4 ? 4 : 2;
@@ -456,7 +491,7 @@ bool ring_plan(const Grid& g, int kp, int& by, int& slots, uint32_t& slot_bytes,
   by = 0;
   for (int c : cands) {
     if (g.ny % c == 0 || (g.bc[1] == SPARC_DIRICHLET && c <= g.ny)) {
-      if ((c / VY) * (g.nx / VX) <= 384) {
+      if ((c / 2) * (g.nx / VX) <= 384) {
         by = c;
         break;
       }
@@ -472,8 +507,59 @@ bool ring_plan(const Grid& g, int kp, int& by, int& slots, uint32_t& slot_bytes,
   const uint32_t budget = (uint32_t)(200 * 1024 - dbytes);
   slots = std::min<int>(13, (int)(budget / slot_bytes));
   if (slots < 8) return false;  // the march needs plane z + R resident S - 7 planes ahead
-  threads = (by / VY) * (g.nx / VX);
+  threads = (by / 2) * (g.nx / VX);
   return threads >= 32 && threads % 32 == 0;
+}
+
+// Plan of the local ring kernel for a grid, element type and thread shape
+// (vy rows per thread): slab rows, ring slots, slot bytes and threads, or
+// false when the grid does not fit the ring form.
+template <typename T>
+bool local_ring_plan(const Grid& g, int vy, int& by, int& slots, uint32_t& slot_bytes,
+                     int& threads) {
+  constexpr int VX = sizeof(T) == 4 ? 4 : 2;
+  const int es = sizeof(T);
+  if (g.nx % (sizeof(T) == 4 ? 16 : 8) != 0 || g.nx > 256) return false;
+  const int cands[4] = {64, 32, 16, 8};
+  by = 0;
+  for (int c : cands) {
+    if (c % vy) continue;
+    if (g.ny % c == 0 || (g.bc[1] == SPARC_DIRICHLET && c <= g.ny)) {
+      const int th = (c / vy) * (g.nx / VX);
+      if (th <= 384 && th % 32 == 0) {
+        by = c;
+        break;
+      }
+    }
+  }
+  if (by == 0) return false;
+  if (g.bc[1] == SPARC_PERIODIC && g.ny < by + 2 * R && g.ny != by) return false;
+  if (g.bc[1] == SPARC_PERIODIC && g.ny < 2 * R) return false;
+  slot_bytes = (uint32_t)((by + 2 * R) * g.nx * es);
+  slot_bytes = (slot_bytes + 127u) & ~127u;
+  slots = std::min<int>(16, (int)((200 * 1024) / slot_bytes));
+  if (slots < 8) return false;  // the march needs plane z + R resident S - 7 planes ahead
+  threads = (by / vy) * (g.nx / VX);
+  return threads >= 32 && threads % 32 == 0;
+}
+
+// Thread shape of the local ring kernel: rows per thread and planes per step.
+template <typename T>
+struct RingShape;
+template <>
+struct RingShape<float> { static constexpr int vy = 1, u = 4; };
+template <>
+struct RingShape<double> { static constexpr int vy = 1, u = 2; };
+
+template <typename T, int VX, int VY, int U, bool XD>
+cudaError_t launch_ring(dim3 grid, int threads, size_t smem, cudaStream_t st,
+                        const CUtensorMap& mmid, const CUtensorMap& mhalo, const RingArgs<T>& a) {
+  static unsigned long long attr_bits = 0;
+  cudaError_t ae =
+      smem_limit_once(&attr_bits, (const void*)k_apply_h_ring<T, VX, VY, U, XD>, 210 * 1024);
+  if (ae != cudaSuccess) return ae;
+  note_launch(), k_apply_h_ring<T, VX, VY, U, XD><<<grid, threads, smem, st>>>(mmid, mhalo, a);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -483,9 +569,10 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
                          cudaStream_t st, bool* used) {
   *used = false;
   constexpr int VX = sizeof(T) == 4 ? 4 : 2;
+  constexpr int VY = RingShape<T>::vy, U = RingShape<T>::u;
   int by, slots, threads;
   uint32_t slot_bytes;
-  if (!ring_plan<T>(g, 0, by, slots, slot_bytes, threads)) return cudaSuccess;
+  if (!local_ring_plan<T>(g, VY, by, slots, slot_bytes, threads)) return cudaSuccess;
   const int va = 16 / sizeof(T);
   if (ldx % va || ldy % va || (prev && ldp % va) || ((uintptr_t)x % 16) || ((uintptr_t)y % 16) ||
       (prev && ((uintptr_t)prev % 16)) || ((uintptr_t)veff % 16))
@@ -514,13 +601,12 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
   a.bz = (g.nz + nzc - 1) / nzc;
   nzc = (g.nz + a.bz - 1) / a.bz;
   const size_t smem = (size_t)slots * slot_bytes + 128;
-  static unsigned long long attr_bits = 0;
-  cudaError_t ae = smem_limit_once(&attr_bits, (const void*)k_apply_h_ring<T, VX>, 210 * 1024);
-  if (ae != cudaSuccess) return ae;
-  dim3 grid((unsigned)(a.nslab * ns), (unsigned)nzc);
-  note_launch(), k_apply_h_ring<T, VX><<<grid, threads, smem, st>>>(mmid, mhalo, a);
-  *used = true;
-  return cudaGetLastError();
+  const dim3 grid((unsigned)(a.nslab * ns), (unsigned)nzc);
+  cudaError_t e = g.bc[0] == SPARC_DIRICHLET
+                      ? launch_ring<T, VX, VY, U, true>(grid, threads, smem, st, mmid, mhalo, a)
+                      : launch_ring<T, VX, VY, U, false>(grid, threads, smem, st, mmid, mhalo, a);
+  if (e == cudaSuccess) *used = true;
+  return e;
 }
 
 template bool ring_plan<float>(const Grid&, int, int&, int&, uint32_t&, int&);
