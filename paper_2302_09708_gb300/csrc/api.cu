@@ -52,6 +52,16 @@ int sparc::sm_count() {
   return v;
 }
 
+int sparc::smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 48 * 1024;
+  }
+  return v;
+}
+
 cudaError_t sparc::smem_limit_once(unsigned long long* bits, const void* func, int bytes) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -677,7 +687,9 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
       t.tile_ptr = tp_; t.pts = pt_; t.ent_ptr = ep_; t.ent_kl = ekl; t.ent_chi = ech;
       t.kset_ptr = ksp; t.kset_k = ksk; t.kent_ptr = kep; t.kent_pt = kpt; t.kent_chi = kch;
       t.kpair_ptr = kpp; t.kpair = kpr;
-      c->tiles_ok = nl_apply_smem(t) <= 227 * 1024;
+      int optin = 0;
+      CK(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+      c->tiles_ok = nl_apply_smem(t) <= (size_t)optin;
       if (c->tiles_ok)
         CK(c, cudaMalloc(&c->part, (size_t)std::max(t.npairs, 1) * c->ns_max * sizeof(TT)));
       return SPARC_OK;

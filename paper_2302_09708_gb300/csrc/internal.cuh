@@ -23,6 +23,8 @@ void set_global_error(const std::string& msg);
 // Number of SMs of the current device (queried once per device; 1 if the query
 // fails, so grid sizing stays valid).
 int sm_count();
+// Largest dynamic shared memory a CTA may opt into on the current device.
+int smem_optin();
 // Sets a kernel's dynamic shared-memory limit on the current device, once per
 // device per `bits` word (one word per kernel instantiation).
 cudaError_t smem_limit_once(unsigned long long* bits, const void* func, int bytes);

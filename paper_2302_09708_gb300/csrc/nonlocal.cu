@@ -86,7 +86,7 @@ namespace {
 template <typename T>
 struct NbOf;
 template <>
-struct NbOf<float> { static constexpr int v = 32; };
+struct NbOf<float> { static constexpr int v = 16; };
 template <>
 struct NbOf<double> { static constexpr int v = 16; };
 
@@ -111,15 +111,16 @@ __global__ void __launch_bounds__(kTilePts)
   __syncthreads();
   const int pl = threadIdx.x;
   if (pl < np) {
+    // the point's entry range is in flight together with its NB orbital values
     const int64_t i = t.pts[p0 + pl];
+    const int e0 = t.ent_ptr[p0 + pl], e1 = t.ent_ptr[p0 + pl + 1];
     T y[NB], acc[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       y[j] = j < nb ? Y[(int64_t)(nb0 + j) * ldy + i] : T(0);
       acc[j] = T(0);
     }
-    const int e1 = t.ent_ptr[p0 + pl + 1];
-    for (int e = t.ent_ptr[p0 + pl]; e < e1; ++e) {
+    for (int e = e0; e < e1; ++e) {
       const int kl = t.ent_kl[e];
       const T c = t.ent_chi[e];
 #pragma unroll
@@ -173,8 +174,9 @@ cudaError_t nl_apply(const NlTiles<T>& t, const T* D, int kp, T* y, int64_t ldy,
   const size_t smem = nl_apply_smem(t);
   static unsigned long long attr_bits = 0;
   if (smem > 48 * 1024) {
-    const cudaError_t e = smem_limit_once(&attr_bits, (const void*)k_nl_apply<T, NB>,
-                                          (int)std::min<size_t>(smem, 227 * 1024));
+    // the device's whole opt-in limit, so that handles with larger tiles later
+    // need no second setting
+    const cudaError_t e = smem_limit_once(&attr_bits, (const void*)k_nl_apply<T, NB>, smem_optin());
     if (e != cudaSuccess) return e;
   }
   const dim3 grid((unsigned)t.ntiles, (unsigned)((ns + NB - 1) / NB));
