@@ -99,19 +99,40 @@ typedef struct {
                     projection/rotation, FP64 bounds/Cholesky/eigensolve.      */
   int ns_max;    /* largest Ns passed to any call on this handle (>= 1)        */
   int device;    /* CUDA device ordinal                                        */
-  int reserved[5]; /* reserved[0] bit 0: use the generic stencil kernel instead
-                      of the TMA plane-ring form (for cross-checking).
-                      reserved[0] bit 1 (FP64 handles): projection and rotation
-                      on the FP64 SIMT pipe instead of the FP64-accurate
-                      six-digit tensor-core split (about 2^-45 relative to
-                      sum |x_k y_k|).
-                      reserved[0] bit 2 (FP64 handles): H x of FP64 blocks in
-                      double-FP32 arithmetic (48-bit pairs on the FP32 pipe,
-                      ~5x faster, ~1e-13 relative; Ritz values stay within
-                      1e-8 Ha, the subspace of nearly degenerate top states
-                      may move by ~1e-7).  Mixed handles always evaluate their
-                      FP64 Yt this way.  Other bits and entries 0.          */
+  int flags;     /* bit 0: use the generic stencil kernel instead of the TMA
+                    plane-ring form (for cross-checking).
+                    bit 1 (FP64 handles): projection and rotation on the FP64
+                    SIMT pipe instead of the FP64-accurate six-digit
+                    tensor-core split (about 2^-45 relative to sum |x_k y_k|).
+                    bit 2 (FP64 handles): H x of FP64 blocks in double-FP32
+                    arithmetic (48-bit pairs on the FP32 pipe, ~5x faster,
+                    ~1e-13 relative; Ritz values stay within 1e-8 Ha, the
+                    subspace of nearly degenerate top states may move by
+                    ~1e-7).  Mixed handles always evaluate their FP64 Yt this
+                    way.  Other bits 0.                                        */
+  int stencil_shape; /* thread shape of the ring stencil: 0 = chosen by timing
+                    the shapes that fit the grid on the first filter or H x call
+                    with a given ns (that call waits for its stream); k >= 1 =
+                    shape k - 1 always (see sparc_get_tuning).  The shapes give
+                    bit-identical results.                                     */
+  int reserved;  /* must be 0                                                  */
+  int64_t timeout_cycles; /* bound of every device-side wait, in SM clock cycles
+                    (0 = 4e9, about two seconds); a wait that runs out stops its
+                    kernel and the next waiting call returns SPARC_ERR_TIMEOUT */
 } sparc_options;
+
+/* Thread shape of the ring stencil in use on a handle and the timings that
+ * chose it (sparc_get_tuning).  shape = -1: no ring-form stencil has run. */
+typedef struct {
+  int shape;            /* index of the shape in use                          */
+  int rows_per_thread;  /* grid rows a thread computes per plane              */
+  int planes_per_step;  /* planes per move of the thread's z register queue   */
+  int slab_rows;        /* y rows of the slab one CTA owns                    */
+  int threads;          /* threads per CTA                                    */
+  int ns;               /* orbital count of the timed launches                */
+  int candidates;       /* number of shapes                                   */
+  float candidate_ms[8];/* one stencil launch per shape (0: did not fit)      */
+} sparc_tuning;
 
 /* Stage times (ms) of the last sparc_chefsi_step on the handle (CUDA events)
  * and the number of library kernels it launched.  bounds_ms includes the
@@ -231,6 +252,14 @@ int sparc_chefsi_step(sparc_handle h, void* X, int ns, int64_t ld, int dtype, in
 int sparc_get_timings(sparc_handle h, sparc_timings* t);
 
 /*
+ * sparc_get_tuning — the thread shape the handle's ring stencil uses for the
+ * most recent ns it tuned (or was given), with the per-shape times measured on
+ * the handle's workspace blocks (stencil_shape 0), into *t.  Errors:
+ * INVALID_ARG (null arguments).
+ */
+int sparc_get_tuning(sparc_handle h, sparc_tuning* t);
+
+/*
  * sparc_occupations — Fermi-Dirac occupations of the Ritz values (the smeared
  * occupation a self-consistent cycle applies after each CheFSI step, Sec. 2.1):
  * f_n = 1 / (1 + exp((lam_n - mu) / kT)), with the Fermi level mu found by
@@ -316,7 +345,7 @@ int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step);
 /*
  * sparc_project_noalloc — the FP64 projection of sparc_project (Hs = Xt^T Yt,
  * Ms = Xt^T Xt) on the FP64 SIMT pipe (the form FP64 handles use when created
- * with sparc_options.reserved[0] bit 1), without a handle and without
+ * with sparc_options.flags bit 1), without a handle and without
  * allocating any device memory.
  * The paper has no counterpart; this entry point exists for callers that may
  * not call cudaMalloc: code whose device memory is owned by another allocator

@@ -52,6 +52,12 @@ int sparc::sm_count() {
   return v;
 }
 
+namespace {
+thread_local long long g_wait_cycles = 4000000000LL;
+}  // namespace
+long long sparc::wait_cycles() { return g_wait_cycles; }
+void sparc::set_wait_cycles(long long cycles) { g_wait_cycles = cycles; }
+
 int sparc::smem_optin() {
   int dev = 0, v = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -165,6 +171,71 @@ bool tiles_usable(const sparc_context* c) {
   return c->tiles_ok && (std::is_same<T, float>::value == mixed);
 }
 
+// Thread shape of the ring stencil for ns orbitals of type T: the fixed one,
+// one tuned before for this ns, or the fastest of the shapes that fit the grid
+// timed now (one warm-up and two timed launches each, x = W1, y = prev = W2 as
+// in the filter's recurrence; the contents of W1/W2 are scratch here).  The
+// shapes give bit-identical results.  Tuning waits for the stream; during a
+// stream capture the first shape is used untimed.
+template <typename T>
+int ring_shape(sparc_context* c, int ns, cudaStream_t st, int* shape) {
+  *shape = 0;
+  const int nsh = ring_num_shapes<T>();
+  if (c->shape_fixed >= 0) {
+    *shape = std::min(c->shape_fixed, nsh - 1);
+    return SPARC_OK;
+  }
+  for (const auto& e : c->shape_by_ns)
+    if (e.first == ns) {
+      *shape = e.second;
+      return SPARC_OK;
+    }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(c, cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return SPARC_OK;
+  const T* veff = std::is_same<T, double>::value ? (const T*)c->veff64 : (const T*)c->veff32;
+  T* x = (T*)c->W1;
+  T* y = (T*)c->W2;
+  sparc_tuning tu{};
+  tu.candidates = std::min(nsh, 8);
+  tu.ns = ns;
+  float best = 0.f;
+  int best_s = -1;
+  for (int s_ = 0; s_ < tu.candidates; ++s_) {
+    int vy, u, by, th;
+    if (!ring_shape_info<T>(c->grid, s_, &vy, &u, &by, &th)) continue;
+    float t = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      bool used = false;
+      CK(c, cudaEventRecord(c->ev[0], st));
+      CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, c->ld, y, c->ld, y, c->ld, ns, 0.0, 1.0,
+                            0.0, c->wait_cycles, c->eig.status + 3, st, s_, &used));
+      CK(c, cudaEventRecord(c->ev[1], st));
+      CK(c, cudaEventSynchronize(c->ev[1]));
+      if (!used) break;
+      float ms = 0.f;
+      CK(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+      if (rep == 1 || (rep == 2 && ms < t)) t = ms;  // rep 0 warms up
+    }
+    tu.candidate_ms[s_] = t;
+    if (t > 0.f && (best_s < 0 || t < best)) {
+      best = t;
+      best_s = s_;
+    }
+  }
+  *shape = best_s < 0 ? 0 : best_s;
+  c->shape_by_ns.emplace_back(ns, *shape);
+  int vy = 0, u = 0, by = 0, th = 0;
+  ring_shape_info<T>(c->grid, *shape, &vy, &u, &by, &th);
+  tu.shape = *shape;
+  tu.rows_per_thread = vy;
+  tu.planes_per_step = u;
+  tu.slab_rows = by;
+  tu.threads = th;
+  c->tuning = tu;
+  return SPARC_OK;
+}
+
 // y = s_h (H - shift) x + s_p prev.  The nonlocal coefficients D of x are in
 // c->D when `d_ready`, else they are gathered first (k_nl_coef).  On the ring
 // path the local stencil runs first and the nonlocal term follows by support-
@@ -191,8 +262,16 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
   }
   if (c->ring_enabled && (nl.natoms == 0 || nl.kp == 0 || tiles_usable<T>(c))) {
     bool used = false;
+    int shape = 0;
+    int rc = ring_shape<T>(c, ns, st, &shape);
+    if (rc) return rc;
     CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
-                          c->wait_cycles, c->eig.status + 3, st, &used));
+                          c->wait_cycles, c->eig.status + 3, st, shape, &used));
+    if (used && c->shape_fixed >= 0 && c->tuning.shape != shape) {
+      int vy = 0, u = 0, by = 0, th = 0;
+      ring_shape_info<T>(c->grid, shape, &vy, &u, &by, &th);
+      c->tuning = sparc_tuning{shape, vy, u, by, th, ns, ring_num_shapes<T>(), {}};
+    }
     if (used) {
       if (nl.natoms > 0 && nl.kp > 0) {
         const NlTiles<T>& t = tiles_of<T>(c);
@@ -464,9 +543,19 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
     ARG(c, g->bc[d] == SPARC_PERIODIC || g->bc[d] == SPARC_DIRICHLET, "bad boundary condition");
   const int64_t nd = (int64_t)g->nx * g->ny * g->nz;
   ARG(c, nd < (int64_t)1 << 31, "grid too large (Nd must fit in int32)");
-  sparc_options o = opt ? *opt : sparc_options{SPARC_PREC_FP64, 1, 0, {0, 0, 0, 0, 0}};
+  sparc_options o = opt ? *opt : sparc_options{SPARC_PREC_FP64, 1, 0, 0, 0, 0, 0};
   ARG(c, o.precision == SPARC_PREC_FP64 || o.precision == SPARC_PREC_MIXED, "bad precision");
   ARG(c, o.ns_max >= 1 && o.ns_max <= 65535, "ns_max must be in [1, 65535]");
+  ARG(c, (o.flags & ~7) == 0 && o.reserved == 0, "unknown option flags or nonzero reserved");
+  ARG(c, o.timeout_cycles >= 0, "timeout_cycles must be >= 0");
+  {
+    const int nsh = o.precision == SPARC_PREC_MIXED ? ring_num_shapes<float>()
+                                                    : ring_num_shapes<double>();
+    ARG(c, o.stencil_shape >= 0 && o.stencil_shape <= nsh, "stencil_shape out of range");
+  }
+  c->shape_fixed = o.stencil_shape - 1;
+  if (o.timeout_cycles > 0) c->wait_cycles = o.timeout_cycles;
+  c->tuning.shape = -1;
   CK(c, cudaSetDevice(o.device));
   c->device = o.device;
   c->grid.nx = g->nx; c->grid.ny = g->ny; c->grid.nz = g->nz;
@@ -698,12 +787,12 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
   }
 
   // --- workspace ----------------------------------------------------------
-  c->ring_enabled = !(opt && (opt->reserved[0] & 1));
+  c->ring_enabled = !(opt && (opt->flags & 1));
   // double-FP32 stencil: always for the mixed form's FP64 Yt, opt-in (bit 2)
   // for FP64 handles, whose subspace target needs the full 53 bits
-  c->df_stencil = c->precision == SPARC_PREC_MIXED || (opt && (opt->reserved[0] & 4));
+  c->df_stencil = c->precision == SPARC_PREC_MIXED || (opt && (opt->flags & 4));
   // mixed handles always take the tensor-core GEMMs; FP64 handles unless bit 1
-  c->tc_gemm = c->precision == SPARC_PREC_MIXED || !(opt && (opt->reserved[0] & 2));
+  c->tc_gemm = c->precision == SPARC_PREC_MIXED || !(opt && (opt->flags & 2));
   const size_t es = c->precision == SPARC_PREC_MIXED ? 4 : 8;
   const size_t blk = (size_t)c->ld * c->ns_max * es;
   CK(c, cudaMalloc(&c->W1, blk));
@@ -782,6 +871,7 @@ int sparc_hpsi(sparc_handle c, const void* X, void* Y, int ns, int64_t ld, int d
   ARG(c, Y != nullptr && X != Y, "Y must be non-null and distinct from X");
   ARG(c, is_device_ptr(X) && is_device_ptr(Y), "hpsi takes device blocks");
   CK(c, cudaSetDevice(c->device));
+  set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
   // a stencil wait that runs out is reported by the next call that reads status
   CK(c, cudaMemsetAsync(c->eig.status + 3, 0, sizeof(int), st));
@@ -796,6 +886,7 @@ int sparc_spectrum_bounds(sparc_handle c, int iters, uint64_t seed, double* a0, 
   ARG(c, iters >= 2 && iters <= 512, "iters must be in [2, 512]");
   ARG(c, a0 && b, "null output");
   CK(c, cudaSetDevice(c->device));
+  set_wait_cycles(c->wait_cycles);
   return lanczos(c, iters, seed, a0, b, (cudaStream_t)stream);
 }
 
@@ -808,6 +899,7 @@ int sparc_cheb_filter(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   ARG(c, std::isfinite(a) && std::isfinite(b) && std::isfinite(a0) && a0 < a && a < b,
       "bounds must satisfy a0 < a < b");
   CK(c, cudaSetDevice(c->device));
+  set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
   const bool host = !is_device_ptr(X);
   void* Xd = X;
@@ -840,6 +932,7 @@ int sparc_project(sparc_handle c, const void* Xt, const void* Yt, int ns, int64_
   if (rc) return rc;
   ARG(c, Yt && Hs && Ms, "null argument");
   CK(c, cudaSetDevice(c->device));
+  set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
   // the tensor-core form's bounded waits report through the status word, which
   // this call then reads (synchronously); the FP64 SIMT form has no waits
@@ -858,6 +951,7 @@ int sparc_subspace_eig(sparc_handle c, const double* Hs, const double* Ms, int n
   ARG(c, Hs && Ms && lam && Z, "null argument");
   ARG(c, ns >= 1 && ns <= c->ns_max, "ns must be in [1, ns_max]");
   CK(c, cudaSetDevice(c->device));
+  set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
   CK(c, gen_eig(c->eig, Hs, Ms, ns, lam, Z, st));
   return read_status(c, st);
@@ -870,6 +964,7 @@ int sparc_rotate(sparc_handle c, const void* Xt, void* Xout, const double* Z, in
   if (rc) return rc;
   ARG(c, Xout && Z && Xout != Xt, "Xout must be non-null and distinct from Xt");
   CK(c, cudaSetDevice(c->device));
+  set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
   if (c->tc_gemm) CK(c, cudaMemsetAsync(c->eig.status, 0, 3 * sizeof(int), st));
   if (dtype == SPARC_F64)
@@ -887,6 +982,7 @@ int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   if (rc) return rc;
   ARG(c, degree >= 1 && degree <= 1000, "degree must be in [1, 1000]");
   CK(c, cudaSetDevice(c->device));
+  set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
   const auto wall0 = std::chrono::steady_clock::now();
   c->staged = false;
@@ -928,6 +1024,13 @@ int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   return SPARC_OK;
 }
 
+int sparc_get_tuning(sparc_handle c, sparc_tuning* t) {
+  if (!c) return SPARC_ERR_INVALID_ARG;
+  ARG(c, t != nullptr, "null output");
+  *t = c->tuning;
+  return SPARC_OK;
+}
+
 int sparc_occupations(sparc_handle c, const double* lam, int ns, double ne, double kT,
                       double* occ, double* mu, void* stream) {
   if (!c) return SPARC_ERR_INVALID_ARG;
@@ -938,6 +1041,7 @@ int sparc_occupations(sparc_handle c, const double* lam, int ns, double ne, doub
   ARG(c, is_device_ptr(lam) && is_device_ptr(occ) && is_device_ptr(mu),
       "occupations take device arrays");
   CK(c, cudaSetDevice(c->device));
+  set_wait_cycles(c->wait_cycles);
   CK(c, fermi_occupations(lam, ns, ne, kT, occ, mu, (cudaStream_t)stream));
   return SPARC_OK;
 }
@@ -953,6 +1057,7 @@ int sparc_density(sparc_handle c, const void* X, int ns, int64_t ld, int dtype, 
   ARG(c, ns == 0 || (X && occ && is_device_ptr(X) && is_device_ptr(occ)),
       "X and occ must be device arrays");
   CK(c, cudaSetDevice(c->device));
+  set_wait_cycles(c->wait_cycles);
   // scratch: the W1 filter buffer (ld x ns_max elements of the handle's type)
   const int64_t work_elems = c->ld * (int64_t)c->ns_max * (int64_t)elem_size(want) / 8;
   CK(c, density(X, ld, c->nd, ns, dtype == SPARC_F32, occ, c->h, rho, (double*)c->W1, work_elems,
@@ -976,6 +1081,7 @@ int sparc_nonlocal_forces(sparc_handle c, const void* X, int ns, int64_t ld, int
   const int64_t work_doubles = c->ld * (int64_t)c->ns_max * (int64_t)elem_size(want) / 8;
   ARG(c, (int64_t)natoms * 3 * ns <= work_doubles, "too many atoms for the handle's workspace");
   CK(c, cudaSetDevice(c->device));
+  set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == SPARC_F64)
     CK(c, nonlocal_forces<double>(c->grid, c->h, c->nl64, (const double*)X, ld, ns, occ, F,
@@ -1348,6 +1454,8 @@ int sparc_batch_chefsi_step(sparc_batch b, void* const* X, const int* ns, const 
   const int want = b->precision == SPARC_PREC_MIXED ? SPARC_F32 : SPARC_F64;
   ARG(b, dtype == want, "dtype does not match the handles' precision");
   CK(b, cudaSetDevice(b->device));
+  // the members' kernels wait as long as the first member's handle allows
+  set_wait_cycles(b->hs.empty() ? 4000000000LL : b->hs[0]->wait_cycles);
   if (dtype == SPARC_F64)
     return batch_step_impl<double>(b, X, ns, ld, degree, bounds, eig, (cudaStream_t)stream);
   return batch_step_impl<float>(b, X, ns, ld, degree, bounds, eig, (cudaStream_t)stream);

@@ -283,12 +283,11 @@ __global__ void k_house_tail(const double* A, double* Hv, double* d, double* e, 
 // launches per step.  The barrier waits are bounded: on expiry the kernel
 // records SPARC_ERR_TIMEOUT in status[4] and every block leaves the loop.
 // ---------------------------------------------------------------------------
-constexpr long long kBarrierCycles = 4000000000LL;
-
 struct GridBar {
   unsigned* count;
   unsigned* gen;
   int* status;
+  long long cycles;  // bound of each barrier wait (SM clock cycles)
 };
 
 // Returns false if the barrier timed out (in any block).
@@ -305,7 +304,7 @@ __device__ bool grid_barrier(const GridBar& gb, unsigned nblocks, int* abort_sh)
     } else {
       const long long t0 = clock64();
       while (*vgen == g) {
-        if (*(volatile int*)gb.status != 0 || clock64() - t0 > kBarrierCycles) {
+        if (*(volatile int*)gb.status != 0 || clock64() - t0 > gb.cycles) {
           atomicCAS(gb.status, 0, SPARC_ERR_TIMEOUT);
           *abort_sh = 1;
           break;
@@ -804,7 +803,7 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
     if (coop && sms > 0 && per_sm > 0) {
       int blocks = sms * std::min(per_sm, 2);
       GridBar gb{reinterpret_cast<unsigned*>(w.status + 8), reinterpret_cast<unsigned*>(w.status + 9),
-                 w.status + 4};
+                 w.status + 4, wait_cycles()};
       EK(cudaMemsetAsync(w.status + 4, 0, sizeof(int), st));
       EK(cudaMemsetAsync(w.status + 8, 0, 2 * sizeof(int), st));
       double* Ap = w.A;

@@ -23,6 +23,15 @@ void set_global_error(const std::string& msg);
 // Number of SMs of the current device (queried once per device; 1 if the query
 // fails, so grid sizing stays valid).
 int sm_count();
+// Bound of every device-side wait (SM clock cycles) for the kernels the calling
+// host thread launches next; set by each C entry point from its handle.
+long long wait_cycles();
+void set_wait_cycles(long long cycles);
+// Lower bound of the waits with which a stopping kernel lets its own copies
+// and tensor-core operations in flight land before it exits (about 0.1 s),
+// whatever the wait bound above: those complete on their own.
+constexpr long long kDrainCycles = 200000000LL;
+
 // Largest dynamic shared memory a CTA may opt into on the current device.
 int smem_optin();
 // Sets a kernel's dynamic shared-memory limit on the current device, once per
@@ -94,11 +103,19 @@ cudaError_t apply_h(const Grid& g, const LapCoef& lc, const T* veff, const Nonlo
 // with nl_apply.  *used = false when the grid or the buffers do not fit it.
 // `status` (device int) receives SPARC_ERR_TIMEOUT if a bounded wait (of
 // `wait_cycles` SM clock cycles) runs out.
+// `shape` selects one of ring_num_shapes<T>() thread shapes (rows per thread,
+// planes per step, CTA size); all give bit-identical results.
 template <typename T>
 cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const T* x, int64_t ldx,
                          T* y, int64_t ldy, const T* prev, int64_t ldp, int ns, double shift,
                          double s_h, double s_p, long long wait_cycles, int* status,
-                         cudaStream_t st, bool* used);
+                         cudaStream_t st, int shape, bool* used);
+template <typename T>
+int ring_num_shapes();
+// rows per thread, planes per step, slab rows and threads of a shape on a grid
+// (false if that shape does not fit the grid)
+template <typename T>
+bool ring_shape_info(const Grid& g, int shape, int* vy, int* u, int* by, int* threads);
 // Ring plan (stencil_tma.cu): slab rows, ring slots, slot bytes and threads for
 // a grid and element type, or false when the generic kernel must run.
 template <typename T>
@@ -340,6 +357,10 @@ struct sparc_context {
   bool tiles_ok = false;  // the tables of the working precision are built and fit
   void* part = nullptr;
   long long wait_cycles = 4000000000LL;  // bound of every device wait (SM clock cycles)
+  // ring stencil thread shape: fixed (>= 0) or tuned per ns (-1)
+  int shape_fixed = -1;
+  std::vector<std::pair<int, int>> shape_by_ns;  // (ns, shape) tuned so far
+  sparc_tuning tuning{};
   double* Y64 = nullptr;     // mixed handles: FP64 Yt = H Xt of a step (ld x ns_max)
   float2* veff_df = nullptr; // Veff as (hi, lo) FP32 pairs for the double-FP32 stencil
   bool df_stencil = false;   // FP64 H x in double-FP32 arithmetic (mixed Yt; reserved[0] bit 2)

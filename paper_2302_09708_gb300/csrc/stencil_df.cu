@@ -29,7 +29,6 @@ namespace {
 constexpr int R = kRadius;
 constexpr int VX = 2;  // points per thread along x (one 16-byte load of two pairs)
 constexpr int VY = 2;  // rows per thread
-constexpr long long kWait = 4000000000LL;
 
 struct df {
   float h, l;
@@ -145,12 +144,13 @@ __device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity) {
 }
 // Bounded wait: false on its own timeout (recorded) or once any CTA of the
 // launch has recorded a status.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int* status) {
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int* status,
+                                         long long budget) {
   if (bar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (!bar_test(bar, parity)) {
     if (*(volatile int*)status != 0) return false;
-    if (clock64() - t0 > kWait) {
+    if (clock64() - t0 > budget) {
       atomicCAS(status, 0, SPARC_ERR_TIMEOUT);
       return false;
     }
@@ -192,6 +192,7 @@ struct RingArgsDF {
   df off[R + 1];
   df s_h, s_p;
   int* status;
+  long long wait;  // bound of every mbarrier wait (SM clock cycles)
 };
 
 __global__ void __launch_bounds__(384, 1)
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(384, 1)
   // wait gave up.
   auto arrive_convert = [&](int p) {
     const int s = slot_of(p);
-    const bool got = bar_wait(su32(&full[s]), round_of(p) & 1, a.status);
+    const bool got = bar_wait(su32(&full[s]), round_of(p) & 1, a.status, a.wait);
     if (got) {
       df* sl = slot_ptr(s);
       const double* sd = reinterpret_cast<const double*>(sl);
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(384, 1)
     if ((tid & 31) == 0)
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&empty[s])) : "memory");
     if (tid == 0 && p + S < z1 + R)
-      if (bar_wait(su32(&empty[s]), round_of(p) & 1, a.status)) issue(p + S);
+      if (bar_wait(su32(&empty[s]), round_of(p) & 1, a.status, a.wait)) issue(p + S);
     __syncwarp();
   };
 
@@ -431,7 +432,8 @@ __global__ void __launch_bounds__(384, 1)
     const int hi = issued_hi;
     for (int p = max(pbase, hi - S); p < hi; ++p) {
       const long long t0 = clock64();
-      while (!bar_test(su32(&full[slot_of(p)]), round_of(p) & 1) && clock64() - t0 < kWait) {
+      while (!bar_test(su32(&full[slot_of(p)]), round_of(p) & 1) &&
+             clock64() - t0 < max(a.wait, kDrainCycles)) {
       }
     }
   }
@@ -503,6 +505,7 @@ cudaError_t apply_h_ring_df(const Grid& g, const LapCoef& lc, const float2* veff
   a.s_h = host_df(s_h);
   a.s_p = host_df(s_p);
   a.status = status;
+  a.wait = wait_cycles();
   const int64_t xy = (int64_t)a.nslab * ns;
   int nzc = (int)std::max<int64_t>(1, (2 * sm_count() + xy - 1) / xy);
   nzc = std::min(nzc, std::max(1, g.nz / 16));

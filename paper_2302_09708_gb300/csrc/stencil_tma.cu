@@ -156,8 +156,8 @@ struct RingArgs {
 // wrapped once per thread (zero chunks for Dirichlet x), so no thread takes a
 // per-element path.  Even x distances are summed as pairs, odd ones (whose
 // pairs straddle two vector registers) as two scalar adds.
-template <typename T, int VX, int VY, int U, bool XDIR>
-__global__ void __launch_bounds__(384, 1)
+template <typename T, int VX, int VY, int U, int MAXT, bool XDIR>
+__global__ void __launch_bounds__(MAXT, 1)
     k_apply_h_ring(const __grid_constant__ CUtensorMap mid, const __grid_constant__ CUtensorMap halo,
                    const RingArgs<T> a) {
   using TW = Two<T>;
@@ -439,7 +439,8 @@ __global__ void __launch_bounds__(384, 1)
     for (int p = max(pbase, hi - S); p < hi; ++p) {
       const int k = p - pbase;
       const long long t0 = clock64();
-      while (!bar_test(su32(&full[k % S]), (k / S) & 1) && clock64() - t0 < wmax) {
+      while (!bar_test(su32(&full[k % S]), (k / S) & 1) &&
+             clock64() - t0 < max(wmax, kDrainCycles)) {
       }
     }
   }
@@ -512,21 +513,22 @@ bool ring_plan(const Grid& g, int kp, int& by, int& slots, uint32_t& slot_bytes,
 }
 
 // Plan of the local ring kernel for a grid, element type and thread shape
-// (vy rows per thread): slab rows, ring slots, slot bytes and threads, or
-// false when the grid does not fit the ring form.
+// (vy rows per thread, at most maxt threads): slab rows, ring slots, slot bytes
+// and threads, or false when the grid does not fit the ring form.
 template <typename T>
-bool local_ring_plan(const Grid& g, int vy, int& by, int& slots, uint32_t& slot_bytes,
-                     int& threads) {
+bool local_ring_plan(const Grid& g, int vy, int maxt, int& by, int& slots,
+                     uint32_t& slot_bytes, int& threads) {
   constexpr int VX = sizeof(T) == 4 ? 4 : 2;
   const int es = sizeof(T);
   if (g.nx % (sizeof(T) == 4 ? 16 : 8) != 0 || g.nx > 256) return false;
-  const int cands[4] = {64, 32, 16, 8};
+  const int cands[7] = {64, 48, 32, 24, 16, 12, 8};
   by = 0;
   for (int c : cands) {
     if (c % vy) continue;
     if (g.ny % c == 0 || (g.bc[1] == SPARC_DIRICHLET && c <= g.ny)) {
       const int th = (c / vy) * (g.nx / VX);
-      if (th <= 384 && th % 32 == 0) {
+      const uint32_t sb = ((uint32_t)((c + 2 * R) * g.nx * es) + 127u) & ~127u;
+      if (th <= maxt && th % 32 == 0 && (200 * 1024) / sb >= 8) {
         by = c;
         break;
       }
@@ -543,36 +545,71 @@ bool local_ring_plan(const Grid& g, int vy, int& by, int& slots, uint32_t& slot_
   return threads >= 32 && threads % 32 == 0;
 }
 
-// Thread shape of the local ring kernel: rows per thread and planes per step.
+// Thread shapes of the local ring kernel: rows per thread, planes per step and
+// the CTA's thread limit (which bounds the registers per thread).  Every shape
+// computes each point with the same operations in the same order, so the
+// results do not depend on the shape; the fastest one is picked by timing
+// (ring_tune).
+struct RingShapeDef {
+  int vy, u, maxt;
+};
+constexpr RingShapeDef kShapesF32[] = {{1, 4, 384}, {1, 1, 576}, {1, 2, 512}};
+constexpr RingShapeDef kShapesF64[] = {{1, 2, 384}, {1, 1, 576}};
 template <typename T>
-struct RingShape;
-template <>
-struct RingShape<float> { static constexpr int vy = 1, u = 4; };
-template <>
-struct RingShape<double> { static constexpr int vy = 1, u = 2; };
+constexpr int num_shapes() {
+  return sizeof(T) == 4 ? (int)(sizeof(kShapesF32) / sizeof(RingShapeDef))
+                        : (int)(sizeof(kShapesF64) / sizeof(RingShapeDef));
+}
+template <typename T>
+constexpr RingShapeDef shape_def(int i) {
+  return sizeof(T) == 4 ? kShapesF32[i] : kShapesF64[i];
+}
 
-template <typename T, int VX, int VY, int U, bool XD>
-cudaError_t launch_ring(dim3 grid, int threads, size_t smem, cudaStream_t st,
+template <typename T, int VX, int VY, int U, int MAXT>
+cudaError_t launch_ring(bool xdir, dim3 grid, int threads, size_t smem, cudaStream_t st,
                         const CUtensorMap& mmid, const CUtensorMap& mhalo, const RingArgs<T>& a) {
-  static unsigned long long attr_bits = 0;
-  cudaError_t ae =
-      smem_limit_once(&attr_bits, (const void*)k_apply_h_ring<T, VX, VY, U, XD>, 210 * 1024);
+  static unsigned long long bits[2] = {0, 0};
+  const void* fn = xdir ? (const void*)k_apply_h_ring<T, VX, VY, U, MAXT, true>
+                        : (const void*)k_apply_h_ring<T, VX, VY, U, MAXT, false>;
+  cudaError_t ae = smem_limit_once(&bits[xdir ? 1 : 0], fn, 210 * 1024);
   if (ae != cudaSuccess) return ae;
-  note_launch(), k_apply_h_ring<T, VX, VY, U, XD><<<grid, threads, smem, st>>>(mmid, mhalo, a);
+  note_launch();
+  if (xdir)
+    k_apply_h_ring<T, VX, VY, U, MAXT, true><<<grid, threads, smem, st>>>(mmid, mhalo, a);
+  else
+    k_apply_h_ring<T, VX, VY, U, MAXT, false><<<grid, threads, smem, st>>>(mmid, mhalo, a);
   return cudaGetLastError();
+}
+
+template <typename T>
+int ring_num_shapes() {
+  return num_shapes<T>();
+}
+
+template <typename T>
+bool ring_shape_info(const Grid& g, int shape, int* vy, int* u, int* by, int* threads) {
+  if (shape < 0 || shape >= num_shapes<T>()) return false;
+  const RingShapeDef d = shape_def<T>(shape);
+  int slots;
+  uint32_t sb;
+  if (!local_ring_plan<T>(g, d.vy, d.maxt, *by, slots, sb, *threads)) return false;
+  *vy = d.vy;
+  *u = d.u;
+  return true;
 }
 
 template <typename T>
 cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const T* x, int64_t ldx,
                          T* y, int64_t ldy, const T* prev, int64_t ldp, int ns, double shift,
                          double s_h, double s_p, long long wait_cycles, int* status,
-                         cudaStream_t st, bool* used) {
+                         cudaStream_t st, int shape, bool* used) {
   *used = false;
   constexpr int VX = sizeof(T) == 4 ? 4 : 2;
-  constexpr int VY = RingShape<T>::vy, U = RingShape<T>::u;
+  if (shape < 0 || shape >= num_shapes<T>()) shape = 0;
+  const RingShapeDef d = shape_def<T>(shape);
   int by, slots, threads;
   uint32_t slot_bytes;
-  if (!local_ring_plan<T>(g, VY, by, slots, slot_bytes, threads)) return cudaSuccess;
+  if (!local_ring_plan<T>(g, d.vy, d.maxt, by, slots, slot_bytes, threads)) return cudaSuccess;
   const int va = 16 / sizeof(T);
   if (ldx % va || ldy % va || (prev && ldp % va) || ((uintptr_t)x % 16) || ((uintptr_t)y % 16) ||
       (prev && ((uintptr_t)prev % 16)) || ((uintptr_t)veff % 16))
@@ -602,9 +639,20 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
   nzc = (g.nz + a.bz - 1) / a.bz;
   const size_t smem = (size_t)slots * slot_bytes + 128;
   const dim3 grid((unsigned)(a.nslab * ns), (unsigned)nzc);
-  cudaError_t e = g.bc[0] == SPARC_DIRICHLET
-                      ? launch_ring<T, VX, VY, U, true>(grid, threads, smem, st, mmid, mhalo, a)
-                      : launch_ring<T, VX, VY, U, false>(grid, threads, smem, st, mmid, mhalo, a);
+  const bool xd = g.bc[0] == SPARC_DIRICHLET;
+  cudaError_t e = cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    switch (shape) {
+      case 0: e = launch_ring<T, VX, 1, 4, 384>(xd, grid, threads, smem, st, mmid, mhalo, a); break;
+      case 1: e = launch_ring<T, VX, 1, 1, 576>(xd, grid, threads, smem, st, mmid, mhalo, a); break;
+      default: e = launch_ring<T, VX, 1, 2, 512>(xd, grid, threads, smem, st, mmid, mhalo, a); break;
+    }
+  } else {
+    switch (shape) {
+      case 0: e = launch_ring<T, VX, 1, 2, 384>(xd, grid, threads, smem, st, mmid, mhalo, a); break;
+      default: e = launch_ring<T, VX, 1, 1, 576>(xd, grid, threads, smem, st, mmid, mhalo, a); break;
+    }
+  }
   if (e == cudaSuccess) *used = true;
   return e;
 }
@@ -614,10 +662,14 @@ template bool ring_plan<double>(const Grid&, int, int&, int&, uint32_t&, int&);
 template cudaError_t apply_h_ring<float>(const Grid&, const LapCoef&, const float*, const float*,
                                          int64_t, float*, int64_t, const float*, int64_t, int,
                                          double, double, double, long long, int*, cudaStream_t,
-                                         bool*);
+                                         int, bool*);
 template cudaError_t apply_h_ring<double>(const Grid&, const LapCoef&, const double*,
                                           const double*, int64_t, double*, int64_t, const double*,
                                           int64_t, int, double, double, double, long long, int*,
-                                          cudaStream_t, bool*);
+                                          cudaStream_t, int, bool*);
+template int ring_num_shapes<float>();
+template int ring_num_shapes<double>();
+template bool ring_shape_info<float>(const Grid&, int, int*, int*, int*, int*);
+template bool ring_shape_info<double>(const Grid&, int, int*, int*, int*, int*);
 
 }  // namespace sparc

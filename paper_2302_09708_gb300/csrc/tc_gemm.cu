@@ -60,7 +60,6 @@ constexpr int kQ = 256;  // K values per exponent chunk
 constexpr uint32_t kTmemCols = 512;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // Compile-time plan of one accuracy form: D digits, levels 0..NL-1.
 template <int D, int NL>
@@ -127,13 +126,13 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 // Bounded wait; false on timeout (and then *abort is set).  Also gives up when
 // another CTA of the launch has already recorded a status.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
-                                          const int* status) {
+                                          const int* status, long long budget) {
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
     if (mbar_test(bar, parity)) return true;
     if (*abort) return false;
-    if (*(volatile const int*)status != 0 || clock64() - t0 > kWaitCycles) {
+    if (*(volatile const int*)status != 0 || clock64() - t0 > budget) {
       *abort = 1;
       return false;
     }
@@ -235,6 +234,7 @@ struct TcArgs {
   const int8_t* escB1;  // same for output 1
   int MP, NP;           // row strides of the exponent arrays (multiples of 128)
   int* status;
+  long long wait_cycles;  // bound of every wait (SM clock cycles)
 };
 
 template <int D, int NL>
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int it = 0; it < itm.nk; ++it, ++g) {
           const int s = g % kStages;
           const uint32_t round = (uint32_t)(g / kStages);
-          if (!mbar_wait(empty0 + 8 * s, (round & 1) ^ 1, abort, a.status)) {
+          if (!mbar_wait(empty0 + 8 * s, (round & 1) ^ 1, abort, a.status, a.wait_cycles)) {
             ok = false;
             break;
           }
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int it = max(0, g - kStages); it < g; ++it) {
           const long long t0 = clock64();
           while (!mbar_test(full0 + 8 * (it % kStages), (uint32_t)(it / kStages) & 1) &&
-                 clock64() - t0 < kWaitCycles) {
+                 clock64() - t0 < max(a.wait_cycles, kDrainCycles)) {
           }
         }
       }
@@ -370,13 +370,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int buf = gc % kBufs;
           const uint32_t use = (uint32_t)(gc / kBufs);
           if (in_chunk == 0) {
-            if (!mbar_wait(acce0 + 8 * buf, (use & 1) ^ 1, abort, a.status)) {
+            if (!mbar_wait(acce0 + 8 * buf, (use & 1) ^ 1, abort, a.status, a.wait_cycles)) {
               ok = false;
               break;
             }
             tc_fence_after();
           }
-          if (!mbar_wait(full0 + 8 * s, round & 1, abort, a.status)) {
+          if (!mbar_wait(full0 + 8 * s, round & 1, abort, a.status, a.wait_cycles)) {
             ok = false;
             break;
           }
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // all issued MMAs complete before tensor memory is released
       tc_commit(drain);
       const long long t0 = clock64();
-      while (!mbar_test(drain, 0) && clock64() - t0 < kWaitCycles) {
+      while (!mbar_test(drain, 0) && clock64() - t0 < max(a.wait_cycles, kDrainCycles)) {
       }
     }
   } else {
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int c = 0; c < nchunks && ok; ++c, ++gc) {
       const int buf = gc % kBufs;
       const uint32_t use = (uint32_t)(gc / kBufs);
-      if (!mbar_wait(accf0 + 8 * buf, use & 1, abort, a.status)) {
+      if (!mbar_wait(accf0 + 8 * buf, use & 1, abort, a.status, a.wait_cycles)) {
         ok = false;
         break;
       }
@@ -911,6 +911,7 @@ cudaError_t tc_project_t(const TX* Xt, int64_t ldx, const TY* Yt, int64_t ldy, i
   for (int bj = 0; bj < a.tiles_n; ++bj)
     a.ntiles_upper += std::min(a.tiles_m, (bj * kBN + kBN - 1) / kBM + 1);
   a.status = status;
+  a.wait_cycles = wait_cycles();
   const int nsp = (int)((lds + a.kchunk - 1) / a.kchunk);
   // out 0: Hs = X^T Y (B = Y slices), out 1: Ms = X^T X (B = X slices); tiles
   // entirely below the diagonal exit at once
@@ -973,6 +974,7 @@ cudaError_t tc_rotate_t(const T* Xt, int64_t ld, int64_t nd, int ns, const doubl
   a.NP = NP;
   a.nout = 1;
   a.status = status;
+  a.wait_cycles = wait_cycles();
   return launch_tc<P::kD, P::kNL>(mA, mZ, mZ, a, dim3(a.tiles_m * a.tiles_n, 1, 1), st);
 }
 

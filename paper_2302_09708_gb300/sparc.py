@@ -55,7 +55,14 @@ class sparc_nonlocal(ctypes.Structure):
 
 class sparc_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("ns_max", ctypes.c_int), ("device", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("flags", ctypes.c_int), ("stencil_shape", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("timeout_cycles", ctypes.c_int64)]
+
+
+class sparc_tuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in
+                ("shape", "rows_per_thread", "planes_per_step", "slab_rows", "threads", "ns",
+                 "candidates")] + [("candidate_ms", ctypes.c_float * 8)]
 
 
 class sparc_timings(ctypes.Structure):
@@ -70,7 +77,7 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_hpsi",
            "sparc_rotate", "sparc_chefsi_step", "sparc_get_timings", "sparc_project_noalloc",
            "sparc_occupations", "sparc_density", "sparc_nonlocal_forces",
            "sparc_batch_create", "sparc_batch_destroy", "sparc_batch_last_error",
-           "sparc_batch_chefsi_step", "sparc_batch_get_info"]
+           "sparc_batch_chefsi_step", "sparc_batch_get_info", "sparc_get_tuning"]
 
 _lib = None
 
@@ -103,6 +110,7 @@ def load(build: bool = True):
     L.sparc_rotate.argtypes = [vp, vp, vp, vp, i, i64, i, vp]
     L.sparc_chefsi_step.argtypes = [vp, vp, i, i64, i, i, vp, vp, i, vp]
     L.sparc_get_timings.argtypes = [vp, ctypes.POINTER(sparc_timings)]
+    L.sparc_get_tuning.argtypes = [vp, ctypes.POINTER(sparc_tuning)]
     L.sparc_project_noalloc.argtypes = [vp, vp, i, i64, i64, vp, vp, vp]
     L.sparc_occupations.argtypes = [vp, vp, i, d, d, vp, vp, vp]
     L.sparc_density.argtypes = [vp, vp, i, i64, i, vp, vp, vp]
@@ -160,9 +168,10 @@ def _arr(a, dtype):
 
 # -- C-named functions -------------------------------------------------------
 def sparc_create(system, precision: int = SPARC_PREC_FP64, ns_max: int = 1, device: int = 0,
-                 flags: int = 0):
+                 flags: int = 0, stencil_shape: int = 0, timeout_cycles: int = 0):
     """Create a handle for a `synth.System`-like object (grid, Veff, projectors).
-    flags (sparc_options.reserved[0]): bit 0 selects the generic stencil form."""
+    flags, stencil_shape and timeout_cycles are the sparc_options fields of the
+    same names (flags bit 0 selects the generic stencil form)."""
     L = load()
     g = sparc_grid(system.nx, system.ny, system.nz, system.h, (ctypes.c_int * 3)(*system.bc))
     keep = [_arr(system.veff, np.float64), _arr(system.supp_ptr, np.int64),
@@ -172,7 +181,7 @@ def sparc_create(system, precision: int = SPARC_PREC_FP64, ns_max: int = 1, devi
     veff, sp, si, npj, cp, chi, pp, gam = keep
     nl = sparc_nonlocal(int(system.natoms), sp.ctypes.data, si.ctypes.data, npj.ctypes.data,
                         cp.ctypes.data, chi.ctypes.data, pp.ctypes.data, gam.ctypes.data)
-    opt = sparc_options(precision, ns_max, device, (ctypes.c_int * 5)(flags, 0, 0, 0, 0))
+    opt = sparc_options(precision, ns_max, device, flags, stencil_shape, 0, timeout_cycles)
     out = ctypes.c_void_p()
     rc = L.sparc_create(ctypes.byref(g), veff.ctypes.data, ctypes.byref(nl), ctypes.byref(opt),
                         ctypes.byref(out))
@@ -276,15 +285,25 @@ def sparc_get_timings(h):
     return {n: getattr(t, n) for n, _ in sparc_timings._fields_}
 
 
+def sparc_get_tuning(h):
+    t = sparc_tuning()
+    _check(h, load().sparc_get_tuning(h, ctypes.byref(t)))
+    d = {n: getattr(t, n) for n, _ in sparc_tuning._fields_ if n != "candidate_ms"}
+    d["candidate_ms"] = list(t.candidate_ms)[: t.candidates]
+    return d
+
+
 class Handle:
     """Convenience wrapper owning one sparc_handle."""
 
-    def __init__(self, system, precision="fp64", ns_max=1, device=0, options_flags=0):
+    def __init__(self, system, precision="fp64", ns_max=1, device=0, options_flags=0,
+                 stencil_shape=0, timeout_cycles=0):
         prec = SPARC_PREC_MIXED if precision == "mixed" else SPARC_PREC_FP64
         self.system = system
         self.precision = precision
         self.ns_max = ns_max
-        self.h = sparc_create(system, prec, ns_max, device, options_flags)
+        self.h = sparc_create(system, prec, ns_max, device, options_flags, stencil_shape,
+                              timeout_cycles)
 
     @property
     def dtype(self):
@@ -363,6 +382,9 @@ class Handle:
 
     def timings(self):
         return sparc_get_timings(self.h)
+
+    def tuning(self):
+        return sparc_get_tuning(self.h)
 
 
 class Batch:

@@ -70,3 +70,28 @@ def test_every_declared_function_is_documented():
     assert not [n for n in undocumented
                 if n not in ("sparc_batch_destroy", "sparc_batch_last_error",
                              "sparc_batch_get_info")], undocumented
+
+
+def test_options_layout_and_validation_without_gpu():
+    """sparc_options is six ints and an int64 (32 bytes, timeout_cycles at byte
+    24); unknown flags, a nonzero reserved word, an out-of-range stencil shape
+    and a negative wait bound are rejected before any device work."""
+    assert ctypes.sizeof(sparc.sparc_options) == 32
+    assert sparc.sparc_options.timeout_cycles.offset == 24
+    assert ctypes.sizeof(sparc.sparc_tuning) == 7 * 4 + 8 * 4
+    L = sparc.load()
+    s = synth.free_system((13, 13, 13), 0.5, (0, 0, 0))
+    g = sparc.sparc_grid(13, 13, 13, 0.5, (ctypes.c_int * 3)(0, 0, 0))
+    veff = np.ascontiguousarray(s.veff)
+    out = ctypes.c_void_p()
+    for opt in (sparc.sparc_options(0, 4, 0, 8, 0, 0, 0),     # unknown flag bit
+                sparc.sparc_options(0, 4, 0, 0, 0, 1, 0),     # reserved != 0
+                sparc.sparc_options(0, 4, 0, 0, 99, 0, 0),    # no such stencil shape
+                sparc.sparc_options(0, 4, 0, 0, -1, 0, 0),
+                sparc.sparc_options(0, 4, 0, 0, 0, 0, -5)):   # negative wait bound
+        rc = L.sparc_create(ctypes.byref(g), veff.ctypes.data, None, ctypes.byref(opt),
+                            ctypes.byref(out))
+        assert rc == sparc.SPARC_ERR_INVALID_ARG
+        assert out.value is None
+    t = sparc.sparc_tuning()
+    assert L.sparc_get_tuning(None, ctypes.byref(t)) == sparc.SPARC_ERR_INVALID_ARG
