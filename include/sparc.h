@@ -109,7 +109,12 @@ typedef struct {
                     ~1e-13 relative; Ritz values stay within 1e-8 Ha, the
                     subspace of nearly degenerate top states may move by
                     ~1e-7).  Mixed handles always evaluate their FP64 Yt this
-                    way.  Other bits 0.                                        */
+                    way.
+                    bit 3 (test hook for the timeout path): every launch of the
+                    ring stencil first waits on a barrier that nothing
+                    completes, so that wait runs out after timeout_cycles, the
+                    kernel stops (its loads in flight land first) and the next
+                    waiting call returns SPARC_ERR_TIMEOUT.  Other bits 0.     */
   int stencil_shape; /* thread shape of the ring stencil: 0 = chosen by timing
                     the shapes that fit the grid on the first filter or H x call
                     with a given ns (that call waits for its stream); k >= 1 =

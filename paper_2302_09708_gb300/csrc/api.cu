@@ -209,7 +209,7 @@ int ring_shape(sparc_context* c, int ns, cudaStream_t st, int* shape) {
       bool used = false;
       CK(c, cudaEventRecord(c->ev[0], st));
       CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, c->ld, y, c->ld, y, c->ld, ns, 0.0, 1.0,
-                            0.0, c->wait_cycles, c->eig.status + 3, st, s_, &used));
+                            0.0, c->wait_cycles, c->eig.status + 3, st, s_, false, &used));
       CK(c, cudaEventRecord(c->ev[1], st));
       CK(c, cudaEventSynchronize(c->ev[1]));
       if (!used) break;
@@ -266,7 +266,7 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
     int rc = ring_shape<T>(c, ns, st, &shape);
     if (rc) return rc;
     CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
-                          c->wait_cycles, c->eig.status + 3, st, shape, &used));
+                          c->wait_cycles, c->eig.status + 3, st, shape, c->stall_test, &used));
     if (used && c->shape_fixed >= 0 && c->tuning.shape != shape) {
       int vy = 0, u = 0, by = 0, th = 0;
       ring_shape_info<T>(c->grid, shape, &vy, &u, &by, &th);
@@ -546,7 +546,8 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
   sparc_options o = opt ? *opt : sparc_options{SPARC_PREC_FP64, 1, 0, 0, 0, 0, 0};
   ARG(c, o.precision == SPARC_PREC_FP64 || o.precision == SPARC_PREC_MIXED, "bad precision");
   ARG(c, o.ns_max >= 1 && o.ns_max <= 65535, "ns_max must be in [1, 65535]");
-  ARG(c, (o.flags & ~7) == 0 && o.reserved == 0, "unknown option flags or nonzero reserved");
+  ARG(c, (o.flags & ~15) == 0 && o.reserved == 0, "unknown option flags or nonzero reserved");
+  c->stall_test = (o.flags & 8) != 0;
   ARG(c, o.timeout_cycles >= 0, "timeout_cycles must be >= 0");
   {
     const int nsh = o.precision == SPARC_PREC_MIXED ? ring_num_shapes<float>()

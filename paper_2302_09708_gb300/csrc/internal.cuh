@@ -109,7 +109,7 @@ template <typename T>
 cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const T* x, int64_t ldx,
                          T* y, int64_t ldy, const T* prev, int64_t ldp, int ns, double shift,
                          double s_h, double s_p, long long wait_cycles, int* status,
-                         cudaStream_t st, int shape, bool* used);
+                         cudaStream_t st, int shape, bool stall, bool* used);
 template <typename T>
 int ring_num_shapes();
 // rows per thread, planes per step, slab rows and threads of a shape on a grid
@@ -359,6 +359,7 @@ struct sparc_context {
   long long wait_cycles = 4000000000LL;  // bound of every device wait (SM clock cycles)
   // ring stencil thread shape: fixed (>= 0) or tuned per ns (-1)
   int shape_fixed = -1;
+  bool stall_test = false;  // options flag bit 3 (test hook, see sparc.h)
   std::vector<std::pair<int, int>> shape_by_ns;  // (ns, shape) tuned so far
   sparc_tuning tuning{};
   double* Y64 = nullptr;     // mixed handles: FP64 Yt = H Xt of a step (ld x ns_max)

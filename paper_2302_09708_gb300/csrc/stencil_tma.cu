@@ -142,6 +142,7 @@ struct RingArgs {
   typename Two<T>::t sh2, sp2;
   long long wait_cycles;  // bound of every mbarrier wait (SM clock cycles)
   int* status;
+  int stall;  // test hook: first wait on a barrier that nothing completes
 };
 
 // Local part of y = s_h (H - shift) x + s_p prev: the radius-6 Laplacian, Veff
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(MAXT, 1)
   constexpr int Q = 2 * R + U;                 // queue depth (planes)
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[16], empty[16];
+  __shared__ uint64_t never;    // test hook: a barrier no thread arrives on
   __shared__ int released[16];  // warps that have released each slot this round
   __shared__ int abort_sh;
   __shared__ int issued_hi;  // one past the last issued plane
@@ -199,6 +201,7 @@ __global__ void __launch_bounds__(MAXT, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&empty[s])), "r"(nwarps));
       released[s] = 0;
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&never)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_sh = 0;
     issued_hi = z0 - R;
@@ -253,6 +256,9 @@ __global__ void __launch_bounds__(MAXT, 1)
   const int plast = z1 + R;  // planes [pbase, plast) are needed
   if (tid == 0)
     for (int p = pbase; p < min(plast, pbase + S); ++p) issue(p, p - pbase);
+  // test hook: this wait can only run out (after wait_cycles); the CTA then
+  // stops like on any other timeout, its loads in flight drained below
+  if (a.stall) wait(su32(&never), 0);
   // Release plane p's slot (lane 0 of every warp, after the warp's reads).  The
   // last warp to release it refills it with plane p + S, once the slot's empty
   // barrier has completed (bounded wait; it completes with that last arrival),
@@ -602,7 +608,7 @@ template <typename T>
 cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const T* x, int64_t ldx,
                          T* y, int64_t ldy, const T* prev, int64_t ldp, int ns, double shift,
                          double s_h, double s_p, long long wait_cycles, int* status,
-                         cudaStream_t st, int shape, bool* used) {
+                         cudaStream_t st, int shape, bool stall, bool* used) {
   *used = false;
   constexpr int VX = sizeof(T) == 4 ? 4 : 2;
   if (shape < 0 || shape >= num_shapes<T>()) shape = 0;
@@ -631,6 +637,7 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
   a.sp2 = {T(s_p), T(s_p)};
   a.wait_cycles = wait_cycles;
   a.status = status;
+  a.stall = stall ? 1 : 0;
   // z split: enough CTAs to cover the SMs a few times
   const int64_t xy = (int64_t)a.nslab * ns;
   int nzc = (int)std::max<int64_t>(1, (2 * sm_count() + xy - 1) / xy);
@@ -662,11 +669,11 @@ template bool ring_plan<double>(const Grid&, int, int&, int&, uint32_t&, int&);
 template cudaError_t apply_h_ring<float>(const Grid&, const LapCoef&, const float*, const float*,
                                          int64_t, float*, int64_t, const float*, int64_t, int,
                                          double, double, double, long long, int*, cudaStream_t,
-                                         int, bool*);
+                                         int, bool, bool*);
 template cudaError_t apply_h_ring<double>(const Grid&, const LapCoef&, const double*,
                                           const double*, int64_t, double*, int64_t, const double*,
                                           int64_t, int, double, double, double, long long, int*,
-                                          cudaStream_t, int, bool*);
+                                          cudaStream_t, int, bool, bool*);
 template int ring_num_shapes<float>();
 template int ring_num_shapes<double>();
 template bool ring_shape_info<float>(const Grid&, int, int*, int*, int*, int*);

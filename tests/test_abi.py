@@ -84,7 +84,7 @@ def test_options_layout_and_validation_without_gpu():
     g = sparc.sparc_grid(13, 13, 13, 0.5, (ctypes.c_int * 3)(0, 0, 0))
     veff = np.ascontiguousarray(s.veff)
     out = ctypes.c_void_p()
-    for opt in (sparc.sparc_options(0, 4, 0, 8, 0, 0, 0),     # unknown flag bit
+    for opt in (sparc.sparc_options(0, 4, 0, 16, 0, 0, 0),    # unknown flag bit
                 sparc.sparc_options(0, 4, 0, 0, 0, 1, 0),     # reserved != 0
                 sparc.sparc_options(0, 4, 0, 0, 99, 0, 0),    # no such stencil shape
                 sparc.sparc_options(0, 4, 0, 0, -1, 0, 0),

@@ -2,10 +2,11 @@
 
 Every thread shape computes each point with the same operations in the same
 order, so H x and the filter must agree bit for bit across shapes; the shape
-the tuner picks is reported through sparc_get_tuning.  A wait bound of one
-clock cycle makes the stencil's first TMA wait run out: the kernel stops, lets
-its loads in flight land, and the step returns SPARC_ERR_TIMEOUT, after which
-the context is still usable."""
+the tuner picks is reported through sparc_get_tuning.  With the timeout test
+hook (options flag bit 3) the stencil first waits on a barrier that nothing
+completes: the wait runs out after timeout_cycles, the kernel stops once its
+loads in flight have landed, the step returns SPARC_ERR_TIMEOUT, and the
+context is still usable afterwards."""
 import numpy as np
 import pytest
 
@@ -85,16 +86,17 @@ def test_tuner_reports_timed_shapes():
 
 def test_wait_bound_runs_out_and_reports_timeout():
     """FP64 handle with SIMT GEMMs and ns < 64 (no other waiting kernel in the
-    step): with timeout_cycles = 1 the ring stencil's first wait runs out and
-    the step returns SPARC_ERR_TIMEOUT; a handle with the default bound then
-    steps the same system to the oracle's Ritz values."""
+    step), the timeout hook on and a wait bound of 2e6 cycles (about 1 ms):
+    every stencil launch's hooked wait runs out and the step returns
+    SPARC_ERR_TIMEOUT; a handle without the hook then steps the same system to
+    the oracle's Ritz values."""
     s = SYSTEMS["ring_periodic"]()
     o = oracle.Oracle(s)
     a0, b, *_ = o.lanczos(32, 0)
     a = a0 + 0.1 * (b - a0)
     ns, m = 16, 6
     X0 = synth.random_orbitals(s.nd, ns, seed=21)
-    h = sparc.Handle(s, "fp64", ns_max=ns, options_flags=2, timeout_cycles=1)
+    h = sparc.Handle(s, "fp64", ns_max=ns, options_flags=2 | 8, timeout_cycles=2_000_000)
     with pytest.raises(sparc.SparcError) as ei:
         h.chefsi_step(torch.from_numpy(X0).to(DEV), m, bounds=(a, b, a0))
     assert ei.value.status == sparc.SPARC_ERR_TIMEOUT
