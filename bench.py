@@ -29,14 +29,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CheFSI step time & Hpsi GB/s; mixed-FP32/batched vs FP64 speedup at <=1e-6 Ha"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 pipe of GB300: 2 FP64 FMA per SM per clock (4 FLOP), 152 SMs, 2070 MHz max.
-FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
-# DRAM bytes (read + write) per orbital of one stencil launch of a filter degree
-# on the 96^3 bulk grid, and the FP64-pipe activity, from the ncu captures
-# summarised in profiles/k_apply_h_ring_fp64_bulk96.md (scaled by orbital count)
-RING64_DRAM_BYTES_PER_ORBITAL = 2.3108e+07  # (1.0550 + 0.4240) GB / 64 orbitals
-RING64_FP64_PIPE_ACTIVE = 0.846
-RING32_DRAM_BYTES_PER_ORBITAL = None  # no capture of the current FP32 kernel
+# DRAM bytes (read + write) per orbital of one ring-stencil launch of a filter
+# degree on the 96^3 bulk grid (ncu captures at a smaller orbital count, scaled
+# by orbitals: every orbital is one independent pass over the grid), or None
+# where no capture of the current kernel exists
+RING64_DRAM_BYTES_PER_ORBITAL = None
+RING32_DRAM_BYTES_PER_ORBITAL = None
+# FLOP per point and orbital of one H application (finite-difference stencil,
+# Veff and recurrence), the count the roofline of the FP64 stencil uses
+STENCIL_FLOP_PER_POINT = 84
+FP64_FLOP_PER_SM_CLK = 4  # 2 FP64 FMA per SM per clock
 
 
 def parse():
@@ -51,6 +53,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-slab", action="store_true",
+                   help="skip the 64x64x160 slab leg (mixed precision, Ns 4800)")
     p.add_argument("--batch-systems", type=int, default=64)
     p.add_argument("--variants", default="all",
                    help="comma-separated forms to compare with the headline FP64 path, or all")
@@ -301,6 +305,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize(dev)
     rho_electrons = float(rho.sum()) * system.h ** 3
+    tuning = h.tuning()
     barrier(world)
     t_loc = e0.elapsed_time(e1) / 1e3
     t_max = max_over_ranks(t_loc, world, dev)
@@ -334,37 +339,12 @@ def main():
         "rotate": {"ms": st_ms["rotate_ms"],
                    "TFLOP/s": rot_flops / (st_ms["rotate_ms"] / 1e3) / 1e12},
     }
-    # dominant kernel roofline (FP64 path: the FP64 pipe is the binding roof)
-    dom = max(("filter", "project", "rotate"), key=lambda k: stage_rate[k]["ms"])
+    # roofline of the dominant kernel: the ring stencil of the filter (timed per
+    # launch by the library's events), against the FP64 pipe (FP64 arithmetic)
+    # or HBM (FP32)
     pk = peaks()
-    if dom == "filter" and prec == "fp64":
-        # one filter degree = k_nl_coef + k_apply_h_ring<double,2>: 48 FP64 flops
-        # per point-orbital (36 neighbours as pair sums, 7 weights, Veff,
-        # recurrence); FP64 arithmetic, so the FP64 pipe is the roof
-        ach = 48.0 * nd * ns * m / (st_ms["filter_ms"] / 1e3) / 1e12
-        roof = {"kernel": "filter degree: k_nl_coef<double> + k_apply_h_ring<double,2>",
-                "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SMs x 4 FP64 FLOP/clk x 2.07 GHz (FP64 pipe)",
-                "algorithmic_bytes": 24 * nd * ns,
-                "traffic": RING64_DRAM_BYTES_PER_ORBITAL * ns if RING64_DRAM_BYTES_PER_ORBITAL
-                else None,
-                "fp64_pipe_active_ncu": RING64_FP64_PIPE_ACTIVE}
-    elif dom == "filter":
-        ach = filt_gbs
-        roof = {"kernel": "filter degree: k_nl_coef<float> + k_apply_h_ring<float,4>",
-                "bound": "hbm", "achieved": ach, "peak": pk.get("hbm_gbs", 6674.5),
-                "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                "algorithmic_bytes": 12 * nd * ns,
-                "traffic": RING32_DRAM_BYTES_PER_ORBITAL * ns if RING32_DRAM_BYTES_PER_ORBITAL
-                else None}
-    else:
-        ms_ = st_ms[dom + "_ms"]
-        ach = (proj_flops if dom == "project" else rot_flops) / (ms_ / 1e3) / 1e12
-        roof = {"kernel": "k_tc_gemm (" + dom + ")", "bound": "tensor", "achieved": ach,
-                "peak": pk.get("bf16_tflops", 1908.3), "unit": "TFLOP/s (useful)",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)", "traffic": None}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["hbm_frac_filter"] = filt_gbs / pk.get("hbm_gbs", 6674.5)
+    roof = stencil_roofline(stage, nd, ns, prec, pk, dev)
+    roof["filter_stage_share"] = st_ms["filter_ms"] / st_ms["total_ms"]
 
     clocks = clk.summary()
 
@@ -415,6 +395,13 @@ def main():
         except Exception as exc:  # report, do not hide
             batched = {"error": repr(exc)}
 
+    slab = None
+    if not args.no_slab and world == 1 and args.workload == "bulk96":
+        try:
+            slab = run_slab(args, dev, stream)
+        except Exception as exc:  # report, do not hide
+            slab = {"error": repr(exc)}
+
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         r = oracle_sample(system, ns, m, args.cpu_seconds)
@@ -434,17 +421,25 @@ def main():
                    "l2": (f"inputs larger than L2 ({nd * ns * s_bytes / 1e9:.1f} GB block)"
                           if nd * ns * s_bytes > 2 * 129e6 else
                           "inputs fit in L2 (small workload; no flush)"),
-                   "bounds": "library (Lanczos 32, "
-                   "cut-off = previous max Ritz value)", "parallelism": f"replicas x{world}"},
+                   "bounds": "library: 32-step Lanczos run once per handle before the timed "
+                             "steps and cached (outside the timed region); cut-off = previous "
+                             "largest Ritz value",
+                   "projection_rotation": ("six-digit BF16 tcgen05 split, FP32-pair sums, "
+                                           "FP64-accurate to ~2^-45 of sum |x_k y_k|"
+                                           if prec == "fp64" else
+                                           "four-digit BF16 tcgen05 split (mixed precision)"),
+                   "parallelism": f"replicas x{world}"},
         "stages": stage_rate,
         "hpsi_gbs": hx_gbs,
         "roofline": roof,
+        "stencil_tuning": tuning,
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
         "mixed": mixed,
         "variants": {k: v for k, v in variants.items() if k != "mixed"} if isinstance(variants, dict) else variants,
         "batched": batched,
+        "slab": slab,
         "cpu_baseline": cpu,
         "setup_s": setup_s,
     }
@@ -454,6 +449,47 @@ def main():
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def fp64_peak_tflops(pk, dev):
+    """FP64 pipe peak derived from the SM count and the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    return sms * FP64_FLOP_PER_SM_CLK * mhz * 1e6 / 1e12, (
+        f"derived: {sms} SMs x {FP64_FLOP_PER_SM_CLK} FP64 FLOP/clk x {mhz:.0f} MHz "
+        "(FP64 pipe; no measured FP64 peak exists)")
+
+
+def stencil_roofline(stage, nd, ns, prec, pk, dev):
+    """Roofline object of the ring stencil: achieved = algorithmic work of one
+    launch / its average duration (library events over the timed steps).  FP64:
+    84 Nd Ns FLOP per launch against the FP64 pipe; FP32: 12 Nd Ns bytes (read
+    Y_i and Y_(i-1), write Y_(i+1)) against measured HBM."""
+    runs = [s for s in stage if s.get("stencil_launches", 0) > 0]
+    if not runs:
+        return {"kernel": "generic stencil (no ring launches)", "achieved": None, "frac": None}
+    per_launch_ms = statistics.median(s["stencil_ms"] / s["stencil_launches"] for s in runs)
+    nl_ms = statistics.median(s["nonlocal_ms"] / s["stencil_launches"] for s in runs)
+    if prec == "fp64":
+        flop = STENCIL_FLOP_PER_POINT * nd * ns
+        peak, src = fp64_peak_tflops(pk, dev)
+        ach = flop / (per_launch_ms / 1e3) / 1e12
+        traffic = RING64_DRAM_BYTES_PER_ORBITAL * ns if RING64_DRAM_BYTES_PER_ORBITAL else None
+        return {"kernel": "k_apply_h_ring<double> (local stencil, one filter degree)",
+                "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "peak_source": src, "traffic": traffic,
+                "algorithmic_flop": flop, "algorithmic_bytes": 24 * nd * ns,
+                "launch_ms": per_launch_ms, "nonlocal_pass_ms": nl_ms,
+                "achieved_gbs": 24 * nd * ns / (per_launch_ms / 1e3) / 1e9}
+    byts = 12 * nd * ns
+    peak = pk.get("hbm_gbs", 6688.8)
+    ach = byts / (per_launch_ms / 1e3) / 1e9
+    traffic = RING32_DRAM_BYTES_PER_ORBITAL * ns if RING32_DRAM_BYTES_PER_ORBITAL else None
+    return {"kernel": "k_apply_h_ring<float> (local stencil, one filter degree)",
+            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "traffic": traffic,
+            "algorithmic_bytes": byts, "launch_ms": per_launch_ms, "nonlocal_pass_ms": nl_ms}
 
 
 def fermi_occupied(lam, ne, kT=0.01):
@@ -498,11 +534,17 @@ def run_variants(system, X0, ns, m, args, dev, stream, h64):
         lam = h64.chefsi_step(X64, m, bounds=(a, b, a0))
         ref.append(lam)
         a = float(lam[-1])
+    ne = synth.electrons_for(ns)
+    # density of the FP64 path after the same steps (the reference of the
+    # variants' density error at this size, where the CPU oracle is too slow)
+    f64, _ = h64.occupations(torch.from_numpy(ref[-1]).to(dev), ne, 0.01)
+    rho_ref = h64.density(X64, f64).clone()
     del X64
     torch.cuda.empty_cache()
-    occ = fermi_occupied(ref[-1], synth.electrons_for(ns))
-    out = {"note": "Ritz-value differences vs the headline FP64 GPU path from the same start "
-                   "and bounds; occupied = Fermi-Dirac f > 1e-6 at kT = 0.01 Ha"}
+    occ = fermi_occupied(ref[-1], ne)
+    out = {"note": "Ritz-value and density differences vs the headline FP64 GPU path from the "
+                   "same start and bounds after 3 steps; occupied = Fermi-Dirac f > 1e-6 at "
+                   "kT = 0.01 Ha"}
     for key, prec, flags, what in VARIANTS:
         if args.variants != "all" and key not in args.variants.split(","):
             continue
@@ -514,6 +556,9 @@ def run_variants(system, X0, ns, m, args, dev, stream, h64):
                 lam = hv.chefsi_step(Xv, m, bounds=(cut[s_], b, a0))
                 errs.append(float(np.max(np.abs(lam - ref[s_]))))
             err_occ = float(np.max(np.abs(lam - ref[-1])[occ]))
+            fv, _ = hv.occupations(torch.from_numpy(lam).to(dev), ne, 0.01)
+            rho = hv.density(Xv, fv)
+            dens_l1 = float((rho - rho_ref).abs().sum()) * system.h ** 3 / ne
             torch.cuda.synchronize(dev)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -530,12 +575,60 @@ def run_variants(system, X0, ns, m, args, dev, stream, h64):
             filt_bytes = (2 + 3 * (m - 1)) * system.nd * ns * es
             out[key] = {"what": what, "ms_per_step": t * 1e3, "stage_ms": st,
                         "filter_GBps": filt_bytes / (st["filter_ms"] / 1e3) / 1e9,
-                        "ritz_err_vs_fp64_gpu_per_step": errs, "ritz_err_occupied": err_occ}
+                        "roofline": stencil_roofline(stage, system.nd, ns, prec, peaks(), dev),
+                        "stencil_tuning": hv.tuning(),
+                        "ritz_err_vs_fp64_gpu_per_step": errs, "ritz_err_occupied": err_occ,
+                        "density_l1_per_electron_vs_fp64_gpu": dens_l1}
             hv.close()
             del Xv
             torch.cuda.empty_cache()
         except Exception as exc:  # report, do not hide
             out[key] = {"error": repr(exc)}
+    return out
+
+
+def run_slab(args, dev, stream):
+    """The 64 x 64 x 160 slab (periodic x, y; Dirichlet z; h = 0.35; 600 atoms
+    in the central 60 % of z; Ns = 4800, degree 24) in mixed precision: time per
+    step and its stages, from a seeded random start drawn on the device (no
+    host orthonormalisation at this size: the step's Rayleigh-Ritz makes the
+    block orthonormal), library bounds, one warm-up and two timed steps."""
+    import torch
+
+    from paper_2302_09708_gb300 import sparc, synth
+
+    cfg = synth.WORKLOADS["slab64x64x160"]
+    t0 = time.perf_counter()
+    system = synth.make_workload_system("slab64x64x160")
+    ns, m = cfg["ns"], cfg["degree"]
+    h = sparc.Handle(system, "mixed", ns_max=ns, device=dev.index)
+    g = torch.Generator(device=dev).manual_seed(synth.workload_seed("slab64x64x160"))
+    X = torch.randn((ns, system.nd), generator=g, device=dev, dtype=torch.float32)
+    X /= system.nd ** 0.5
+    setup_s = time.perf_counter() - t0
+    h.chefsi_step(X, m)
+    stage = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    steps = 2
+    for _ in range(steps):
+        h.chefsi_step(X, m)
+        stage.append(h.timings())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / steps
+    st = {k: statistics.median(x[k] for x in stage) for k in stage[0]
+          if k not in ("launches", "stencil_launches")}
+    filt_bytes = (2 + 3 * (m - 1)) * system.nd * ns * 4
+    out = {"workload": cfg["name"], "ms_per_step": t, "steps": steps, "stage_ms": st,
+           "filter_GBps": filt_bytes / (st["filter_ms"] / 1e3) / 1e9,
+           "roofline": stencil_roofline(stage, system.nd, ns, "mixed", peaks(), dev),
+           "stencil_tuning": h.tuning(), "setup_s": setup_s,
+           "start": "seeded torch.randn on the device / sqrt(Nd)"}
+    h.close()
+    del X
+    torch.cuda.empty_cache()
     return out
 
 

@@ -152,6 +152,11 @@ typedef struct {
   float bounds_ms, filter_ms, hx_ms, project_ms, eig_ms, rotate_ms, total_ms;
   int64_t launches;
   float stage_in_ms, stage_out_ms, host_ms;
+  /* inside filter_ms, on grids that run the ring stencil: the summed durations
+     of the local stencil launches and of the nonlocal passes that follow them
+     (0 on the generic path), and the number of filter degrees they cover */
+  float stencil_ms, nonlocal_ms;
+  int32_t stencil_launches;
 } sparc_timings;
 
 /*

@@ -207,14 +207,14 @@ int ring_shape(sparc_context* c, int ns, cudaStream_t st, int* shape) {
     float t = 0.f;
     for (int rep = 0; rep < 3; ++rep) {
       bool used = false;
-      CK(c, cudaEventRecord(c->ev[0], st));
+      CK(c, cudaEventRecord(c->ev_tune[0], st));
       CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, c->ld, y, c->ld, y, c->ld, ns, 0.0, 1.0,
                             0.0, c->wait_cycles, c->eig.status + 3, st, s_, false, &used));
-      CK(c, cudaEventRecord(c->ev[1], st));
-      CK(c, cudaEventSynchronize(c->ev[1]));
+      CK(c, cudaEventRecord(c->ev_tune[1], st));
+      CK(c, cudaEventSynchronize(c->ev_tune[1]));
       if (!used) break;
       float ms = 0.f;
-      CK(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+      CK(c, cudaEventElapsedTime(&ms, c->ev_tune[0], c->ev_tune[1]));
       if (rep == 1 || (rep == 2 && ms < t)) t = ms;  // rep 0 warms up
     }
     tu.candidate_ms[s_] = t;
@@ -265,8 +265,20 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
     int shape = 0;
     int rc = ring_shape<T>(c, ns, st, &shape);
     if (rc) return rc;
+    // kernel timing events of this degree (grown on first use)
+    cudaEvent_t* kev = nullptr;
+    if (c->kev_on) {
+      while ((int)c->kev.size() < c->kev_n + 3) {
+        cudaEvent_t e;
+        CK(c, cudaEventCreate(&e));
+        c->kev.push_back(e);
+      }
+      kev = c->kev.data() + c->kev_n;
+      CK(c, cudaEventRecord(kev[0], st));
+    }
     CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
                           c->wait_cycles, c->eig.status + 3, st, shape, c->stall_test, &used));
+    if (kev) CK(c, cudaEventRecord(kev[1], st));
     if (used && c->shape_fixed >= 0 && c->tuning.shape != shape) {
       int vy = 0, u = 0, by = 0, th = 0;
       ring_shape_info<T>(c->grid, shape, &vy, &u, &by, &th);
@@ -281,6 +293,10 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
           CK(c, nl_reduce<T>(t, part, ns, nl.kp, nl.gamma, h3, D, st));
           if (next_done) *next_done = true;
         }
+      }
+      if (kev) {
+        CK(c, cudaEventRecord(kev[2], st));
+        c->kev_n += 3;
       }
       return SPARC_OK;
     }
@@ -458,7 +474,10 @@ int do_step(sparc_context* c, T* X, int64_t ldx, int ns, int m, double a, double
   // for Yt = H Xt; mixed precision evaluates Yt in FP64 from its own gather
   const bool f64 = std::is_same<T, double>::value;
   bool xt_d = false;
+  c->kev_n = 0;
+  c->kev_on = true;
   int rc = run_filter<T>(c, X, ldx, ns, m, a, b, a0, true, &Xt, &ldt, st, f64 ? &xt_d : nullptr);
+  c->kev_on = false;
   if (rc) return rc;
   CK(c, cudaEventRecord(c->ev[2], st));
   if (!f64) {
@@ -531,6 +550,9 @@ void destroy_ctx(sparc_context* c) {
     if (e) cudaEventDestroy(e);
   for (auto& e : c->ev_stage)
     if (e) cudaEventDestroy(e);
+  for (auto& e : c->ev_tune)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->kev) cudaEventDestroy(e);
   delete c;
 }
 
@@ -828,6 +850,7 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
   CK(c, cudaMemset(c->eig.status, 0, 16 * sizeof(int)));
   for (auto& e : c->ev) CK(c, cudaEventCreate(&e));
   for (auto& e : c->ev_stage) CK(c, cudaEventCreate(&e));
+  for (auto& e : c->ev_tune) CK(c, cudaEventCreate(&e));
   return SPARC_OK;
 }
 
@@ -1113,6 +1136,15 @@ int sparc_get_timings(sparc_handle c, sparc_timings* t) {
     CK(c, cudaEventElapsedTime(&t->stage_out_ms, c->ev_stage[2], c->ev_stage[3]));
   }
   t->host_ms = (float)c->host_ms;
+  t->stencil_ms = t->nonlocal_ms = 0.0f;
+  t->stencil_launches = c->kev_n / 3;
+  for (int i = 0; i + 2 < c->kev_n; i += 3) {
+    float a = 0.f, b = 0.f;
+    CK(c, cudaEventElapsedTime(&a, c->kev[i], c->kev[i + 1]));
+    CK(c, cudaEventElapsedTime(&b, c->kev[i + 1], c->kev[i + 2]));
+    t->stencil_ms += a;
+    t->nonlocal_ms += b;
+  }
   return SPARC_OK;
 }
 

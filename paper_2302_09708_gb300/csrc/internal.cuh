@@ -344,6 +344,12 @@ struct sparc_context {
   // timings
   cudaEvent_t ev[7] = {};
   cudaEvent_t ev_stage[4] = {};  // host-buffer staging: in start/end, out start/end
+  cudaEvent_t ev_tune[2] = {};   // the stencil shape tuner's launches
+  // per filter degree on the ring path: before the stencil, after it, after the
+  // nonlocal pass (recorded while kev_on)
+  std::vector<cudaEvent_t> kev;
+  int kev_n = 0;
+  bool kev_on = false;
   bool timed = false;
   bool staged = false;           // the last step staged a host block
   double host_ms = 0.0;          // wall time of the last sparc_chefsi_step call

@@ -69,7 +69,8 @@ class sparc_timings(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in
                 ("bounds_ms", "filter_ms", "hx_ms", "project_ms", "eig_ms", "rotate_ms",
                  "total_ms")] + [("launches", ctypes.c_int64)] + [
-        (n, ctypes.c_float) for n in ("stage_in_ms", "stage_out_ms", "host_ms")]
+        (n, ctypes.c_float) for n in ("stage_in_ms", "stage_out_ms", "host_ms", "stencil_ms",
+                                      "nonlocal_ms")] + [("stencil_launches", ctypes.c_int32)]
 
 
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_hpsi",
