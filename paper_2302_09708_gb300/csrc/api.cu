@@ -252,15 +252,23 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
   T* D = (T*)c->D;
   const double h3 = c->h * c->h * c->h;
   if (next_done) *next_done = false;
-  if (!d_ready) CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st));
-  if (std::is_same<T, double>::value && c->ring_enabled && c->df_stencil) {
+  // the ring path keeps D projector-major (its nonlocal pass stages rows of
+  // orbitals per projector); the fused stencils read it orbital-major
+  const bool has_nl = nl.natoms > 0 && nl.kp > 0;
+  const bool df = std::is_same<T, double>::value && c->ring_enabled && c->df_stencil;
+  const bool ring = !df && c->ring_enabled && (!has_nl || tiles_usable<T>(c)) &&
+                    ring_applicable<T>(c->grid, x, ldx, y, ldy, prev, ldp, veff);
+  // a D left by the previous degree's tiled pass is projector-major: any other
+  // path gathers its own
+  if (!d_ready || !ring) CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st, ring));
+  if (df) {
     bool used = false;
     CK(c, apply_h_ring_df(c->grid, c->lap, c->veff_df, c->nl64, (const double*)D,
                           (const double*)x, ldx, (double*)y, ldy, (const double*)prev, ldp, ns,
                           shift, s_h, s_p, c->eig.status + 3, st, &used));
     if (used) return SPARC_OK;
   }
-  if (c->ring_enabled && (nl.natoms == 0 || nl.kp == 0 || tiles_usable<T>(c))) {
+  if (ring) {
     bool used = false;
     int shape = 0;
     int rc = ring_shape<T>(c, ns, st, &shape);
@@ -300,6 +308,9 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
       }
       return SPARC_OK;
     }
+    // the ring kernel declined after all: D is projector-major, the generic
+    // kernel reads it orbital-major
+    if (has_nl) CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st, false));
   }
   CK(c, apply_h<T>(c->grid, c->lap, veff, nl, D, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
                    st));

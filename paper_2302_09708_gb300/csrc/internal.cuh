@@ -110,6 +110,11 @@ cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const 
                          T* y, int64_t ldy, const T* prev, int64_t ldp, int ns, double shift,
                          double s_h, double s_p, long long wait_cycles, int* status,
                          cudaStream_t st, int shape, bool stall, bool* used);
+// Whether the ring form runs for these buffers on this grid (some shape fits,
+// vector alignment, the tensor-map encoder is available).
+template <typename T>
+bool ring_applicable(const Grid& g, const T* x, int64_t ldx, const T* y, int64_t ldy,
+                     const T* prev, int64_t ldp, const T* veff);
 template <typename T>
 int ring_num_shapes();
 // rows per thread, planes per step, slab rows and threads of a shape on a grid
@@ -158,21 +163,23 @@ void nl_tiles_build(int64_t nd, const int* pull_ptr, const int* pull_k, const do
                     int kp, NlTilesHost& out);
 template <typename T>
 size_t nl_apply_smem(const NlTiles<T>& t);
-// y_i += s_h sum_k chi_k(i) D[n kp + k] at the support points of all ns
-// orbitals; with `part` (npairs x ns) also the per-tile partial sums of
-// chi_k^T y for nl_reduce.
+// y_i += s_h sum_k chi_k(i) D[k ns + n] (projector-major D) at the support
+// points of all ns orbitals; with `part` (npairs x ns) also the per-tile
+// partial sums of chi_k^T y for nl_reduce.
 template <typename T>
 cudaError_t nl_apply(const NlTiles<T>& t, const T* D, int kp, T* y, int64_t ldy, int ns,
                      double s_h, T* part, cudaStream_t st);
-// D[n kp + k] = gamma_k h3 sum over the tiles of k of part (tile order)
+// D[k ns + n] = gamma_k h3 sum over the tiles of k of part (tile order)
 template <typename T>
 cudaError_t nl_reduce(const NlTiles<T>& t, const T* part, int ns, int kp, const double* gamma,
                       double h3, T* D, cudaStream_t st);
 
-// D[n * kp + k] = gamma_k h^3 sum_s chi[s][k] x[idx_s + n ldx]
+// D = gamma_k h^3 sum_s chi[s][k] x[idx_s + n ldx], orbital-major at
+// D[n * kp + k] (the fused stencils), or projector-major at D[k * ns + n] with
+// `kmajor` (the nonlocal pass by support-point tiles)
 template <typename T>
 cudaError_t nl_coefficients(const Nonlocal<T>& nl, double h3, const T* x, int64_t ldx, int ns,
-                            T* D, cudaStream_t st);
+                            T* D, cudaStream_t st, bool kmajor = false);
 
 // Small vector kernels (stencil.cu): deterministic two-pass reductions.
 cudaError_t dot_f64(const double* u, const double* v, int64_t n, double* partial, double* out,

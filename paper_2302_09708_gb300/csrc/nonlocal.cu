@@ -7,6 +7,9 @@
 //              C_t[k] = sum_{i in tile t} chi_k(i) y_i    (next degree's D)
 //   nl_reduce: D[k] = gamma_k h^3 sum_t C_t[k]           (fixed tile order)
 //
+// D is projector-major here (D[k ns + n]), so a tile stages the coefficients
+// of its projectors for NB orbitals as contiguous rows.
+//
 // The support points (grid points inside at least one atom's cut-off sphere)
 // are cut into tiles of kTilePts consecutive points.  A CTA takes one tile and
 // NB orbitals: each thread owns one support point, loads its (k, chi) entries
@@ -104,9 +107,10 @@ __global__ void __launch_bounds__(kTilePts)
   const int YS = kTilePts + 1;  // padded row of ysh
   T* const Dsh = reinterpret_cast<T*>(nl_smem);  // [NB][KS]
   T* const ysh = Dsh + NB * KS;                   // [NB][YS]
+  // projector-major D: the NB values of one projector are contiguous
   for (int idx = threadIdx.x; idx < NB * nk; idx += blockDim.x) {
-    const int j = idx / nk, kl = idx - j * nk;
-    Dsh[j * KS + kl] = j < nb ? D[(int64_t)(nb0 + j) * kp + t.kset_k[k0 + kl]] : T(0);
+    const int kl = idx / NB, j = idx - kl * NB;
+    Dsh[j * KS + kl] = j < nb ? D[(int64_t)t.kset_k[k0 + kl] * ns + nb0 + j] : T(0);
   }
   __syncthreads();
   const int pl = threadIdx.x;
@@ -155,7 +159,7 @@ __global__ void k_nl_reduce(const int* __restrict__ kpair_ptr, const int* __rest
   const int k = (int)(idx / ns), n = (int)(idx - (int64_t)k * ns);
   T s = T(0);
   for (int p = kpair_ptr[k]; p < kpair_ptr[k + 1]; ++p) s += part[(int64_t)kpair[p] * ns + n];
-  D[(int64_t)n * kp + k] = T(s * (gamma[k] * h3));
+  D[(int64_t)k * ns + n] = T(s * (gamma[k] * h3));
 }
 
 }  // namespace

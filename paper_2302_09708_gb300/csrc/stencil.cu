@@ -327,7 +327,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 template <typename T>
 __global__ void __launch_bounds__(kNlThreads)
     k_nl_coef(const Nonlocal<T> nl, double h3, const T* __restrict__ x, int64_t ldx, int ns,
-              T* __restrict__ D) {
+              T* __restrict__ D, bool kmajor) {
   __shared__ T red[kNlThreads / 32][kNlOrb][kNlProj];
   const int J = blockIdx.x;
   const int64_t s0 = nl.supp_ptr[J];
@@ -374,7 +374,8 @@ __global__ void __launch_bounds__(kNlThreads)
         T v = T(0);
         for (int w = 0; w < kNlThreads / 32; ++w) v += red[w][n][q];
         const int k = k0 + qb + q;
-        D[(int64_t)(nb + n) * nl.kp + k] = T(v * (nl.gamma[k] * h3));
+        D[kmajor ? (int64_t)k * ns + nb + n : (int64_t)(nb + n) * nl.kp + k] =
+            T(v * (nl.gamma[k] * h3));
       }
     }
     __syncthreads();
@@ -385,17 +386,17 @@ __global__ void __launch_bounds__(kNlThreads)
 
 template <typename T>
 cudaError_t nl_coefficients(const Nonlocal<T>& nl, double h3, const T* x, int64_t ldx, int ns,
-                            T* D, cudaStream_t st) {
+                            T* D, cudaStream_t st, bool kmajor) {
   if (nl.natoms == 0 || nl.kp == 0) return cudaSuccess;
   dim3 grid(nl.natoms, (ns + kNlOrb - 1) / kNlOrb);
-  note_launch(), k_nl_coef<T><<<grid, kNlThreads, 0, st>>>(nl, h3, x, ldx, ns, D);
+  note_launch(), k_nl_coef<T><<<grid, kNlThreads, 0, st>>>(nl, h3, x, ldx, ns, D, kmajor);
   return cudaGetLastError();
 }
 
 template cudaError_t nl_coefficients<double>(const Nonlocal<double>&, double, const double*,
-                                             int64_t, int, double*, cudaStream_t);
+                                             int64_t, int, double*, cudaStream_t, bool);
 template cudaError_t nl_coefficients<float>(const Nonlocal<float>&, double, const float*,
-                                            int64_t, int, float*, cudaStream_t);
+                                            int64_t, int, float*, cudaStream_t, bool);
 
 // ---------------------------------------------------------------------------
 // Block copy between leading dimensions.

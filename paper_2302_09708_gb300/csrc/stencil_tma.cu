@@ -605,6 +605,23 @@ bool ring_shape_info(const Grid& g, int shape, int* vy, int* u, int* by, int* th
 }
 
 template <typename T>
+bool ring_applicable(const Grid& g, const T* x, int64_t ldx, const T* y, int64_t ldy,
+                     const T* prev, int64_t ldp, const T* veff) {
+  bool any = false;
+  for (int s = 0; s < num_shapes<T>() && !any; ++s) {
+    const RingShapeDef d = shape_def<T>(s);
+    int by, slots, th;
+    uint32_t sb;
+    any = local_ring_plan<T>(g, d.vy, d.maxt, by, slots, sb, th);
+  }
+  const int va = 16 / sizeof(T);
+  if (!any || !encoder() || ldx % va || ldy % va || (prev && ldp % va) || ((uintptr_t)x % 16) ||
+      ((uintptr_t)y % 16) || (prev && ((uintptr_t)prev % 16)) || ((uintptr_t)veff % 16))
+    return false;
+  return true;
+}
+
+template <typename T>
 cudaError_t apply_h_ring(const Grid& g, const LapCoef& lc, const T* veff, const T* x, int64_t ldx,
                          T* y, int64_t ldy, const T* prev, int64_t ldp, int ns, double shift,
                          double s_h, double s_p, long long wait_cycles, int* status,
@@ -674,6 +691,10 @@ template cudaError_t apply_h_ring<double>(const Grid&, const LapCoef&, const dou
                                           const double*, int64_t, double*, int64_t, const double*,
                                           int64_t, int, double, double, double, long long, int*,
                                           cudaStream_t, int, bool, bool*);
+template bool ring_applicable<float>(const Grid&, const float*, int64_t, const float*, int64_t,
+                                     const float*, int64_t, const float*);
+template bool ring_applicable<double>(const Grid&, const double*, int64_t, const double*, int64_t,
+                                      const double*, int64_t, const double*);
 template int ring_num_shapes<float>();
 template int ring_num_shapes<double>();
 template bool ring_shape_info<float>(const Grid&, int, int*, int*, int*, int*);

@@ -106,3 +106,28 @@ def test_wait_bound_runs_out_and_reports_timeout():
     _, rlam = o.chefsi_step(X0, m, a, b, a0)
     assert np.max(np.abs(lam - rlam)) < 1e-8
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_switching_stencil_paths_vs_oracle(precision):
+    """Leading dimension Nd + 3 on a ring grid: degrees that touch the caller's
+    block (not 16-byte aligned rows) take the generic stencil, the others the
+    ring stencil and the tiled nonlocal pass, so the step switches between the
+    two layouts of the projector coefficients; it still meets the oracle."""
+    s = SYSTEMS["ring_periodic"]()
+    o = oracle.Oracle(s)
+    a0, b, *_ = o.lanczos(32, 0)
+    a = a0 + 0.1 * (b - a0)
+    ns, m = 12, 8
+    X0 = synth.random_orbitals(s.nd, ns, seed=31)
+    ld = s.nd + 3
+    dt = torch.float32 if precision == "mixed" else torch.float64
+    Xd = torch.zeros((ns, ld), dtype=dt, device=DEV)
+    Xd[:, : s.nd] = torch.from_numpy(X0).to(DEV, dt)
+    h = sparc.Handle(s, precision, ns_max=ns)
+    lam = h.chefsi_step(Xd, m, bounds=(a, b, a0))
+    _, rlam = o.chefsi_step(X0, m, a, b, a0)
+    tol = 1e-6 if precision == "mixed" else 1e-8
+    assert np.max(np.abs(lam - rlam)) < tol, np.max(np.abs(lam - rlam))
+    assert float(Xd[:, s.nd:].abs().max()) == 0.0  # rows beyond Nd untouched
+    h.close()
