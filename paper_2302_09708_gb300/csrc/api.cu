@@ -173,12 +173,12 @@ bool tiles_usable(const sparc_context* c) {
 
 // Thread shape of the ring stencil for ns orbitals of type T: the fixed one,
 // one tuned before for this ns, or the fastest of the shapes that fit the grid
-// timed now (one warm-up and two timed launches each, x = W1, y = prev = W2 as
-// in the filter's recurrence; the contents of W1/W2 are scratch here).  The
-// shapes give bit-identical results.  Tuning waits for the stream; during a
-// stream capture the first shape is used untimed.
+// timed now: one warm-up and two timed launches each, reading the call's own
+// input block x (ldx) and writing a transient buffer, so no live data is
+// touched.  The shapes give bit-identical results.  Tuning waits for the
+// stream; during a stream capture the first shape is used untimed.
 template <typename T>
-int ring_shape(sparc_context* c, int ns, cudaStream_t st, int* shape) {
+int ring_shape(sparc_context* c, const T* x, int64_t ldx, int ns, cudaStream_t st, int* shape) {
   *shape = 0;
   const int nsh = ring_num_shapes<T>();
   if (c->shape_fixed >= 0) {
@@ -194,8 +194,12 @@ int ring_shape(sparc_context* c, int ns, cudaStream_t st, int* shape) {
   CK(c, cudaStreamIsCapturing(st, &cap));
   if (cap != cudaStreamCaptureStatusNone) return SPARC_OK;
   const T* veff = std::is_same<T, double>::value ? (const T*)c->veff64 : (const T*)c->veff32;
-  T* x = (T*)c->W1;
-  T* y = (T*)c->W2;
+  T* y = nullptr;
+  CK(c, cudaMalloc((void**)&y, (size_t)c->ld * ns * sizeof(T)));
+  struct Free {
+    void* p;
+    ~Free() { cudaFree(p); }
+  } free_y{y};
   sparc_tuning tu{};
   tu.candidates = std::min(nsh, 8);
   tu.ns = ns;
@@ -208,7 +212,7 @@ int ring_shape(sparc_context* c, int ns, cudaStream_t st, int* shape) {
     for (int rep = 0; rep < 3; ++rep) {
       bool used = false;
       CK(c, cudaEventRecord(c->ev_tune[0], st));
-      CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, c->ld, y, c->ld, y, c->ld, ns, 0.0, 1.0,
+      CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, ldx, y, c->ld, nullptr, 0, ns, 0.0, 1.0,
                             0.0, c->wait_cycles, c->eig.status + 3, st, s_, false, &used));
       CK(c, cudaEventRecord(c->ev_tune[1], st));
       CK(c, cudaEventSynchronize(c->ev_tune[1]));
@@ -271,7 +275,7 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
   if (ring) {
     bool used = false;
     int shape = 0;
-    int rc = ring_shape<T>(c, ns, st, &shape);
+    int rc = ring_shape<T>(c, x, ldx, ns, st, &shape);
     if (rc) return rc;
     // kernel timing events of this degree (grown on first use)
     cudaEvent_t* kev = nullptr;
