@@ -811,6 +811,7 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
       t.ntiles = (int)th.tile_ptr.size() - 1;
       t.npairs = (int)th.kset_k.size();
       t.kt_max = th.kt_max;
+      t.et_max = th.et_max;
       t.tile_ptr = tp_; t.pts = pt_; t.ent_ptr = ep_; t.ent_kl = ekl; t.ent_chi = ech;
       t.kset_ptr = ksp; t.kset_k = ksk; t.kent_ptr = kep; t.kent_pt = kpt; t.kent_chi = kch;
       t.kpair_ptr = kpp; t.kpair = kpr;

@@ -137,7 +137,7 @@ cudaError_t apply_h_ring_df(const Grid& g, const LapCoef& lc, const float2* veff
 constexpr int kTilePts = 256;  // support points per tile (= threads per CTA)
 template <typename T>
 struct NlTiles {
-  int ntiles = 0, npairs = 0, kt_max = 0;
+  int ntiles = 0, npairs = 0, kt_max = 0, et_max = 0;  // projectors, entries per tile (max)
   const int* tile_ptr = nullptr;      // ntiles + 1: each tile's range in pts
   const int* pts = nullptr;           // support points (grid indices), ascending
   const int* ent_ptr = nullptr;       // per support point: range of its entries
@@ -152,7 +152,7 @@ struct NlTiles {
   const int* kpair = nullptr;         // pair indices, ascending (tile order)
 };
 struct NlTilesHost {
-  int tp = 0, kt_max = 0;
+  int tp = 0, kt_max = 0, et_max = 0;
   std::vector<int> tile_ptr, pts, ent_ptr, kset_ptr, kset_k, kent_ptr, kpair_ptr, kpair;
   std::vector<uint16_t> ent_kl, kent_pt;
   std::vector<double> ent_chi, kent_chi;

@@ -17,9 +17,9 @@
 // coefficients D for those orbitals staged in shared memory.  The projector
 // tables therefore stream once per NB orbitals instead of once per orbital, and
 // every orbital's values move in coalesced rows.  The partial sums C_t are
-// taken per (tile, projector) pair in point order by one thread each, and the
-// reduction adds the tiles of a projector in tile order: no floating-point
-// atomics, so results are bit-reproducible.
+// taken per (tile, projector) pair in point order (one thread per projector
+// and eight orbitals), and the reduction adds the tiles of a projector in tile
+// order: no floating-point atomics, so results are bit-reproducible.
 #include <stdint.h>
 
 #include <algorithm>
@@ -63,6 +63,7 @@ void nl_tiles_build(int64_t nd, const int* pull_ptr, const int* pull_k, const do
       o.ent_ptr[pl + 1] = (int)o.ent_kl.size();
     }
     o.kt_max = std::max(o.kt_max, (int)ks.size());
+    o.et_max = std::max(o.et_max, o.ent_ptr[o.tile_ptr[t + 1]] - o.ent_ptr[o.tile_ptr[t]]);
     for (size_t kl = 0; kl < ks.size(); ++kl) {
       o.kset_k.push_back(ks[kl]);
       for (const auto& pc : bykl[kl]) {
@@ -87,6 +88,13 @@ void nl_tiles_build(int64_t nd, const int* pull_ptr, const int* pull_k, const do
 namespace {
 
 template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> { using t = float4; };
+template <>
+struct Vec4<double> { using t = double2; };
+
+template <typename T>
 struct NbOf;
 template <>
 struct NbOf<float> { static constexpr int v = 16; };
@@ -98,55 +106,111 @@ __global__ void __launch_bounds__(kTilePts)
     k_nl_apply(const NlTiles<T> t, const T* __restrict__ D, int kp, T* __restrict__ Y,
                int64_t ldy, int ns, T s_h, T* __restrict__ part) {
   extern __shared__ __align__(16) uint8_t nl_smem[];
-  const int tile = blockIdx.x;
-  const int nb0 = blockIdx.y * NB;
+  // the orbital blocks of one tile run back to back, so the tile's tables are
+  // read from DRAM once and from L2 by the other blocks
+  const int nblk = (ns + NB - 1) / NB;
+  const int tile = blockIdx.x / nblk;
+  const int nb0 = (blockIdx.x - tile * nblk) * NB;
   const int nb = min(NB, ns - nb0);
   const int p0 = t.tile_ptr[tile], np = t.tile_ptr[tile + 1] - p0;
   const int k0 = t.kset_ptr[tile], nk = t.kset_ptr[tile + 1] - k0;
-  const int KS = nk + 1;        // padded row of Dsh (bank spread)
-  const int YS = kTilePts + 1;  // padded row of ysh
-  T* const Dsh = reinterpret_cast<T*>(nl_smem);  // [NB][KS]
-  T* const ysh = Dsh + NB * KS;                   // [NB][YS]
+  const int e0t = t.ent_ptr[p0], ne = t.ent_ptr[p0 + np] - e0t;
+  const int ke0 = t.kent_ptr[k0];
+  // Dsh[kl][DS]: one projector's NB orbital values as a row, read with vector
+  // loads; the row stride DS = NB + 16 bytes puts the rows of eight
+  // consecutive projectors on distinct bank groups
+  using V = typename Vec4<T>::t;
+  constexpr int VW = 16 / sizeof(T);  // elements per 16-byte load
+  constexpr int DS = NB + 16 / (int)sizeof(T);
+  // shared layout: Dsh[nk][DS], ysh[kTilePts][DS] (a point's NB updated values
+  // as a row), the tile's entries (chi, then projector / point indices) in both
+  // orders
+  T* const Dsh = reinterpret_cast<T*>(nl_smem);
+  T* const ysh = Dsh + t.kt_max * DS;
+  T* const echi = ysh + kTilePts * DS;
+  T* const kchi = echi + t.et_max;
+  uint16_t* const ekl = reinterpret_cast<uint16_t*>(kchi + t.et_max);
+  uint16_t* const kpt = ekl + t.et_max;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    echi[e] = t.ent_chi[e0t + e];
+    ekl[e] = t.ent_kl[e0t + e];
+    kchi[e] = t.kent_chi[ke0 + e];
+    kpt[e] = t.kent_pt[ke0 + e];
+  }
   // projector-major D: the NB values of one projector are contiguous
   for (int idx = threadIdx.x; idx < NB * nk; idx += blockDim.x) {
     const int kl = idx / NB, j = idx - kl * NB;
-    Dsh[j * KS + kl] = j < nb ? D[(int64_t)t.kset_k[k0 + kl] * ns + nb0 + j] : T(0);
+    Dsh[kl * DS + j] = j < nb ? D[(int64_t)t.kset_k[k0 + kl] * ns + nb0 + j] : T(0);
+  }
+  const int pl = threadIdx.x;
+  int64_t i = 0;
+  int pe0 = 0, pe1 = 0;
+  T y[NB];
+  if (pl < np) {
+    i = t.pts[p0 + pl];
+    pe0 = t.ent_ptr[p0 + pl] - e0t;
+    pe1 = t.ent_ptr[p0 + pl + 1] - e0t;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) y[j] = j < nb ? Y[(int64_t)(nb0 + j) * ldy + i] : T(0);
   }
   __syncthreads();
-  const int pl = threadIdx.x;
   if (pl < np) {
-    // the point's entry range is in flight together with its NB orbital values
-    const int64_t i = t.pts[p0 + pl];
-    const int e0 = t.ent_ptr[p0 + pl], e1 = t.ent_ptr[p0 + pl + 1];
-    T y[NB], acc[NB];
+    T acc[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      y[j] = j < nb ? Y[(int64_t)(nb0 + j) * ldy + i] : T(0);
-      acc[j] = T(0);
-    }
-    for (int e = e0; e < e1; ++e) {
-      const int kl = t.ent_kl[e];
-      const T c = t.ent_chi[e];
+    for (int j = 0; j < NB; ++j) acc[j] = T(0);
+    for (int e = pe0; e < pe1; ++e) {
+      const V* row = reinterpret_cast<const V*>(Dsh + ekl[e] * DS);
+      const T c = echi[e];
 #pragma unroll
-      for (int j = 0; j < NB; ++j) acc[j] += c * Dsh[j * KS + kl];
+      for (int q = 0; q < NB / VW; ++q) {
+        const V d = row[q];
+        const T* dv = reinterpret_cast<const T*>(&d);
+#pragma unroll
+        for (int w = 0; w < VW; ++w) acc[q * VW + w] += c * dv[w];
+      }
     }
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       y[j] += s_h * acc[j];
       if (j < nb) Y[(int64_t)(nb0 + j) * ldy + i] = y[j];
-      ysh[j * YS + pl] = y[j];
+    }
+    V* yrow = reinterpret_cast<V*>(ysh + pl * DS);
+#pragma unroll
+    for (int q = 0; q < NB / VW; ++q) {
+      V v;
+      T* vv = reinterpret_cast<T*>(&v);
+#pragma unroll
+      for (int w = 0; w < VW; ++w) vv[w] = y[q * VW + w];
+      yrow[q] = v;
     }
   }
   if (!part) return;
   __syncthreads();
-  // C_t[k] for this tile's projectors, each (k, orbital) by one thread in point order
-  for (int idx = threadIdx.x; idx < nk * NB; idx += blockDim.x) {
-    const int kl = idx / NB, j = idx - kl * NB;
-    if (j >= nb) continue;
-    const int e1 = t.kent_ptr[k0 + kl + 1];
-    T s = T(0);
-    for (int e = t.kent_ptr[k0 + kl]; e < e1; ++e) s += t.kent_chi[e] * ysh[j * YS + t.kent_pt[e]];
-    part[(int64_t)(k0 + kl) * ns + nb0 + j] = s;
+  // C_t[k] for this tile's projectors: each thread takes one projector and PW
+  // orbitals and sums over the projector's entries in point order
+  constexpr int PW = 8;
+  constexpr int NQ = NB / PW;
+  for (int idx = threadIdx.x; idx < nk * NQ; idx += blockDim.x) {
+    const int kl = idx / NQ, j0 = (idx - kl * NQ) * PW;
+    if (j0 >= nb) continue;
+    const int e1 = t.kent_ptr[k0 + kl + 1] - ke0;
+    T sacc[PW];
+#pragma unroll
+    for (int w = 0; w < PW; ++w) sacc[w] = T(0);
+    for (int e = t.kent_ptr[k0 + kl] - ke0; e < e1; ++e) {
+      const T c = kchi[e];
+      const V* yr = reinterpret_cast<const V*>(ysh + kpt[e] * DS + j0);
+#pragma unroll
+      for (int q = 0; q < PW / VW; ++q) {
+        const V v = yr[q];
+        const T* vv = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int w = 0; w < VW; ++w) sacc[q * VW + w] += c * vv[w];
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < PW; ++w)
+      if (j0 + w < nb) part[(int64_t)(k0 + kl) * ns + nb0 + j0 + w] = sacc[w];
   }
 }
 
@@ -167,7 +231,9 @@ __global__ void k_nl_reduce(const int* __restrict__ kpair_ptr, const int* __rest
 template <typename T>
 size_t nl_apply_smem(const NlTiles<T>& t) {
   constexpr int NB = NbOf<T>::v;
-  return (size_t)NB * ((size_t)(t.kt_max + 1) + kTilePts + 1) * sizeof(T);
+  constexpr int DS = NB + 16 / (int)sizeof(T);
+  return ((size_t)t.kt_max * DS + (size_t)kTilePts * DS) * sizeof(T) +
+         (size_t)t.et_max * 2 * (sizeof(T) + sizeof(uint16_t)) + 16;
 }
 
 template <typename T>
@@ -183,7 +249,7 @@ cudaError_t nl_apply(const NlTiles<T>& t, const T* D, int kp, T* y, int64_t ldy,
     const cudaError_t e = smem_limit_once(&attr_bits, (const void*)k_nl_apply<T, NB>, smem_optin());
     if (e != cudaSuccess) return e;
   }
-  const dim3 grid((unsigned)t.ntiles, (unsigned)((ns + NB - 1) / NB));
+  const dim3 grid((unsigned)((int64_t)t.ntiles * ((ns + NB - 1) / NB)));
   note_launch(), k_nl_apply<T, NB><<<grid, kTilePts, smem, st>>>(t, D, kp, y, ldy, ns, T(s_h), part);
   return cudaGetLastError();
 }
