@@ -58,7 +58,7 @@ typedef enum {
 } sparc_status;
 
 enum { SPARC_PERIODIC = 0, SPARC_DIRICHLET = 1 };
-enum { SPARC_F64 = 0, SPARC_F32 = 1 };
+enum { SPARC_F64 = 0, SPARC_F32 = 1, SPARC_C128 = 2 /* complex FP64, (re, im) pairs */ };
 enum { SPARC_PREC_FP64 = 0, SPARC_PREC_MIXED = 1 };
 
 typedef struct sparc_context* sparc_handle;
@@ -168,6 +168,33 @@ typedef struct {
  */
 int sparc_create(const sparc_grid* g, const double* veff, const sparc_nonlocal* nl,
                  const sparc_options* opt, sparc_handle* out);
+
+/*
+ * sparc_create_kpoint — a handle for H(k) at the Bloch wavevector k (kvec, three
+ * components in 1/bohr; components on Dirichlet axes are unused).  The paper
+ * computes in real arithmetic at Gamma; at any other wavevector of a
+ * Brillouin-zone sampling every operation of Algorithm 1 is complex (Sec. III
+ * and the k-point slabs of Sec. IV):
+ *   - Bloch condition psi(r + L_d e_d) = exp(i k_d L_d) psi(r) on periodic axes
+ *     (L_d = N_d h): a stencil neighbour index j is read at j mod N_d and
+ *     multiplied by exp(i k_d L_d floor(j / N_d));
+ *   - projectors are Bloch sums: chi^k(r_i) = chi(r_i - R_J - T_i) exp(i k.T_i)
+ *     with T_i the periodic image nearest r_i (the cut-off must be below half of
+ *     every periodic cell length); positions: natoms x 3 host doubles (bohr), R_J;
+ *   - Hs = Xt^H Yt, Ms = Xt^H Xt, Hs Z = Ms Z D with Z^H Ms Z = I.
+ * g, veff, nl and opt as in sparc_create; opt->precision must be SPARC_PREC_FP64
+ * and ns_max <= 1022.  Orbital blocks of the handle are SPARC_C128 device blocks
+ * (column-major, interleaved (re, im) doubles, ld counted in complex entries).
+ * Calls accepted: sparc_hpsi, sparc_spectrum_bounds, sparc_cheb_filter,
+ * sparc_project, sparc_subspace_eig, sparc_rotate (their ns x ns matrices are
+ * complex, column-major, interleaved: 2 ns^2 doubles each; lam stays real),
+ * sparc_chefsi_step, sparc_occupations, sparc_get_timings; the others return
+ * INVALID_ARG.  The subspace eigensolve uses cyclic Jacobi rotations (returns
+ * NUMERIC if 40 sweeps do not converge).  Errors: as sparc_create.
+ */
+int sparc_create_kpoint(const sparc_grid* g, const double* veff, const sparc_nonlocal* nl,
+                        const double* positions, const sparc_options* opt, const double* kvec,
+                        sparc_handle* out);
 
 /* sparc_destroy — free the handle and all its device memory; NULL is a no-op. */
 int sparc_destroy(sparc_handle h);

@@ -152,6 +152,11 @@ int check_block(sparc_context* c, const void* X, int ns, int64_t ld, int dtype) 
   ARG(c, X != nullptr, "null orbital block");
   ARG(c, ns >= 1 && ns <= c->ns_max, "ns must be in [1, ns_max]");
   ARG(c, ld >= c->nd, "ld must be >= Nd");
+  if (c->kpt) {
+    ARG(c, dtype == SPARC_C128, "k-point handles take SPARC_C128 blocks");
+    ARG(c, is_device_ptr(X), "k-point handles take device blocks");
+    return SPARC_OK;
+  }
   int want = c->precision == SPARC_PREC_MIXED ? SPARC_F32 : SPARC_F64;
   ARG(c, dtype == want, "dtype must be SPARC_F64 on FP64 handles and SPARC_F32 on mixed handles");
   return SPARC_OK;
@@ -553,6 +558,7 @@ int stage_out(sparc_context* c, void* X, int ns, int64_t ld, int dtype, cudaStre
 
 void destroy_ctx(sparc_context* c) {
   if (!c) return;
+  kpoint_free(c);
   for (int i = 0; i < c->nl_nmem; ++i) cudaFree(c->nl_mem[i]);
   cudaFree(c->veff64); cudaFree(c->veff32); cudaFree(c->veff_df);
   cudaFree(c->W1); cudaFree(c->W2); cudaFree(c->Wstage); cudaFree(c->D);
@@ -572,7 +578,7 @@ void destroy_ctx(sparc_context* c) {
 }
 
 int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* nl,
-                const sparc_options* opt, sparc_context* c) {
+                const sparc_options* opt, sparc_context* c, bool kpoint = false) {
   ARG(c, g != nullptr && veff != nullptr, "grid and veff are required");
   ARG(c, g->nx >= 1 && g->ny >= 1 && g->nz >= 1, "grid sizes must be >= 1");
   ARG(c, g->h > 0.0 && std::isfinite(g->h), "h must be positive");
@@ -822,7 +828,9 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
         CK(c, cudaMalloc(&c->part, (size_t)std::max(t.npairs, 1) * c->ns_max * sizeof(TT)));
       return SPARC_OK;
     };
-    if ((rc = mixed ? put_tiles(c->tiles32, 0.0f) : put_tiles(c->tiles64, 0.0))) return rc;
+    // (k-point handles keep complex tables of their own, kpoint.cu)
+    if (!kpoint && (rc = mixed ? put_tiles(c->tiles32, 0.0f) : put_tiles(c->tiles64, 0.0)))
+      return rc;
   }
 
   // --- workspace ----------------------------------------------------------
@@ -832,6 +840,14 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
   c->df_stencil = c->precision == SPARC_PREC_MIXED || (opt && (opt->flags & 4));
   // mixed handles always take the tensor-core GEMMs; FP64 handles unless bit 1
   c->tc_gemm = c->precision == SPARC_PREC_MIXED || !(opt && (opt->flags & 2));
+  if (kpoint) {  // the complex workspaces are kpoint.cu's; the status words are here
+    CK(c, eig_alloc(c->eig, c->ns_max));
+    CK(c, cudaMemset(c->eig.status, 0, 16 * sizeof(int)));
+    for (auto& e : c->ev) CK(c, cudaEventCreate(&e));
+    for (auto& e : c->ev_stage) CK(c, cudaEventCreate(&e));
+    for (auto& e : c->ev_tune) CK(c, cudaEventCreate(&e));
+    return SPARC_OK;
+  }
   const size_t es = c->precision == SPARC_PREC_MIXED ? 4 : 8;
   const size_t blk = (size_t)c->ld * c->ns_max * es;
   CK(c, cudaMalloc(&c->W1, blk));
@@ -892,6 +908,37 @@ int sparc_create(const sparc_grid* g, const double* veff, const sparc_nonlocal* 
   return SPARC_OK;
 }
 
+int sparc_create_kpoint(const sparc_grid* g, const double* veff, const sparc_nonlocal* nl,
+                        const double* positions, const sparc_options* opt, const double* kvec,
+                        sparc_handle* out) {
+  if (!out) {
+    g_create_err = "invalid argument: out is NULL";
+    return SPARC_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  sparc_context* c = new sparc_context();
+  int rc = SPARC_OK;
+  if (!kvec || !std::isfinite(kvec[0]) || !std::isfinite(kvec[1]) || !std::isfinite(kvec[2])) {
+    c->err = "invalid argument: kvec must be three finite numbers";
+    rc = SPARC_ERR_INVALID_ARG;
+  } else if (opt && (opt->precision != SPARC_PREC_FP64 || opt->ns_max > 1022)) {
+    c->err = "invalid argument: k-point handles are FP64 with ns_max <= 1022";
+    rc = SPARC_ERR_INVALID_ARG;
+  } else if (nl && nl->natoms > 0 && !positions) {
+    c->err = "invalid argument: k-point handles with atoms need their positions";
+    rc = SPARC_ERR_INVALID_ARG;
+  }
+  if (!rc) rc = create_impl(g, veff, nl, opt, c, true);
+  if (!rc) rc = kpoint_init(c, kvec, positions, nl);
+  if (rc) {
+    g_create_err = c->err;
+    destroy_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return SPARC_OK;
+}
+
 int sparc_destroy(sparc_handle h) {
   if (!h) return SPARC_OK;
   cudaSetDevice(h->device);
@@ -913,6 +960,7 @@ int sparc_hpsi(sparc_handle c, const void* X, void* Y, int ns, int64_t ld, int d
   CK(c, cudaSetDevice(c->device));
   set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->kpt) return kpoint_hpsi(c, X, Y, ns, ld, st);
   // a stencil wait that runs out is reported by the next call that reads status
   CK(c, cudaMemsetAsync(c->eig.status + 3, 0, sizeof(int), st));
   if (dtype == SPARC_F64)
@@ -927,6 +975,7 @@ int sparc_spectrum_bounds(sparc_handle c, int iters, uint64_t seed, double* a0, 
   ARG(c, a0 && b, "null output");
   CK(c, cudaSetDevice(c->device));
   set_wait_cycles(c->wait_cycles);
+  if (c->kpt) return kpoint_bounds(c, iters, seed, a0, b, (cudaStream_t)stream);
   return lanczos(c, iters, seed, a0, b, (cudaStream_t)stream);
 }
 
@@ -941,6 +990,7 @@ int sparc_cheb_filter(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   CK(c, cudaSetDevice(c->device));
   set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->kpt) return kpoint_filter(c, X, ns, ld, degree, a, b, a0, st);
   const bool host = !is_device_ptr(X);
   void* Xd = X;
   int64_t ldd = ld;
@@ -974,6 +1024,7 @@ int sparc_project(sparc_handle c, const void* Xt, const void* Yt, int ns, int64_
   CK(c, cudaSetDevice(c->device));
   set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->kpt) return kpoint_project(c, Xt, Yt, ns, ld, Hs, Ms, st);
   // the tensor-core form's bounded waits report through the status word, which
   // this call then reads (synchronously); the FP64 SIMT form has no waits
   if (c->tc_gemm) CK(c, cudaMemsetAsync(c->eig.status, 0, 3 * sizeof(int), st));
@@ -993,6 +1044,7 @@ int sparc_subspace_eig(sparc_handle c, const double* Hs, const double* Ms, int n
   CK(c, cudaSetDevice(c->device));
   set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->kpt) return kpoint_eig(c, Hs, Ms, ns, lam, Z, st);
   CK(c, gen_eig(c->eig, Hs, Ms, ns, lam, Z, st));
   return read_status(c, st);
 }
@@ -1006,6 +1058,7 @@ int sparc_rotate(sparc_handle c, const void* Xt, void* Xout, const double* Z, in
   CK(c, cudaSetDevice(c->device));
   set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->kpt) return kpoint_rotate(c, Xt, Xout, Z, ns, ld, st);
   if (c->tc_gemm) CK(c, cudaMemsetAsync(c->eig.status, 0, 3 * sizeof(int), st));
   if (dtype == SPARC_F64)
     rc = do_rotate<double>(c, (const double*)Xt, ld, ns, Z, (double*)Xout, ld, st);
@@ -1036,7 +1089,8 @@ int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
     a0 = bounds[2];
   } else {
     if (!c->have_bounds) {
-      if ((rc = lanczos(c, 32, 0, &c->a0, &c->b, st))) return rc;
+      rc = c->kpt ? kpoint_bounds(c, 32, 0, &c->a0, &c->b, st) : lanczos(c, 32, 0, &c->a0, &c->b, st);
+      if (rc) return rc;
       c->have_bounds = true;
     }
     b = c->b;
@@ -1047,6 +1101,14 @@ int sparc_chefsi_step(sparc_handle c, void* X, int ns, int64_t ld, int dtype, in
   }
   ARG(c, std::isfinite(a) && std::isfinite(b) && std::isfinite(a0) && a0 < a && a < b,
       "bounds must satisfy a0 < a < b");
+  if (c->kpt) {
+    c->kev_n = 0;
+    if ((rc = kpoint_step(c, X, ns, ld, degree, a, b, a0, eig, eig_on_host, st))) return rc;
+    c->step_launches = launch_count() - launches0;
+    c->host_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    return SPARC_OK;
+  }
   const bool host = !is_device_ptr(X);
   void* Xd = X;
   int64_t ldd = ld;
@@ -1089,6 +1151,7 @@ int sparc_occupations(sparc_handle c, const double* lam, int ns, double ne, doub
 int sparc_density(sparc_handle c, const void* X, int ns, int64_t ld, int dtype, const double* occ,
                   double* rho, void* stream) {
   if (!c) return SPARC_ERR_INVALID_ARG;
+  ARG(c, !c->kpt, "sparc_density takes real (Gamma-point) handles");
   ARG(c, ns >= 0 && ns <= c->ns_max, "ns must be in [0, ns_max]");
   ARG(c, ld >= c->nd, "ld must be >= Nd");
   const int want = c->precision == SPARC_PREC_MIXED ? SPARC_F32 : SPARC_F64;
@@ -1108,6 +1171,7 @@ int sparc_density(sparc_handle c, const void* X, int ns, int64_t ld, int dtype, 
 int sparc_nonlocal_forces(sparc_handle c, const void* X, int ns, int64_t ld, int dtype,
                           const double* occ, double* F, void* stream) {
   if (!c) return SPARC_ERR_INVALID_ARG;
+  ARG(c, !c->kpt, "sparc_nonlocal_forces takes real (Gamma-point) handles");
   ARG(c, ns >= 0 && ns <= c->ns_max, "ns must be in [0, ns_max]");
   ARG(c, ld >= c->nd, "ld must be >= Nd");
   const int want = c->precision == SPARC_PREC_MIXED ? SPARC_F32 : SPARC_F64;
@@ -1405,8 +1469,10 @@ int sparc_batch_create(const sparc_handle* hs, int n, sparc_batch* out) {
     return SPARC_ERR_INVALID_ARG;
   }
   for (int i = 0; i < n; ++i)
-    if (!hs[i] || hs[i]->precision != hs[0]->precision || hs[i]->device != hs[0]->device) {
-      g_create_err = "invalid argument: handles must be non-null, same precision and device";
+    if (!hs[i] || hs[i]->precision != hs[0]->precision || hs[i]->device != hs[0]->device ||
+        hs[i]->kpt) {
+      g_create_err = "invalid argument: handles must be non-null real (Gamma-point) handles of "
+                     "one precision and device";
       return SPARC_ERR_INVALID_ARG;
     }
   sparc_batch_context* b = new sparc_batch_context();

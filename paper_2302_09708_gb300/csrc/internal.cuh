@@ -185,6 +185,8 @@ cudaError_t nl_coefficients(const Nonlocal<T>& nl, double h3, const T* x, int64_
 cudaError_t dot_f64(const double* u, const double* v, int64_t n, double* partial, double* out,
                     cudaStream_t st);
 cudaError_t fill_uniform_f64(double* v, int64_t n, uint64_t seed, cudaStream_t st);
+// n complex entries (interleaved): real part u(seed, i) - 1/2, imaginary part 0
+cudaError_t fill_uniform_re_c128(double* v, int64_t n, uint64_t seed, cudaStream_t st);
 cudaError_t lanczos_update(double* w, const double* v, double* vp, const double* alpha_beta,
                            int j, int64_t n, cudaStream_t st);
 cudaError_t lanczos_normalize(double* v, double* w, double* vp, double* alpha_beta, int j,
@@ -268,6 +270,26 @@ void eig_free(EigWork& w);
 // lam ascending, Z column-major with Z^T M Z = I. Writes *dev_status (device).
 cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, double* lam, double* Z,
                     cudaStream_t st);
+
+// Complex step at a Bloch wavevector (kpoint.cu) ---------------------------
+struct KpointState;
+// builds the phased projector tables and complex workspaces of a k-point handle
+int kpoint_init(sparc_context* c, const double kvec[3], const double* positions,
+                const sparc_nonlocal* nl);
+void kpoint_free(sparc_context* c);
+int kpoint_hpsi(sparc_context* c, const void* X, void* Y, int ns, int64_t ld, cudaStream_t st);
+int kpoint_bounds(sparc_context* c, int iters, uint64_t seed, double* a0, double* b,
+                  cudaStream_t st);
+int kpoint_filter(sparc_context* c, void* X, int ns, int64_t ld, int m, double a, double b,
+                  double a0, cudaStream_t st);
+int kpoint_project(sparc_context* c, const void* Xt, const void* Yt, int ns, int64_t ld, double* Hs,
+                   double* Ms, cudaStream_t st);
+int kpoint_eig(sparc_context* c, const double* Hs, const double* Ms, int ns, double* lam, double* Z,
+               cudaStream_t st);
+int kpoint_rotate(sparc_context* c, const void* Xt, void* Xout, const double* Z, int ns, int64_t ld,
+                  cudaStream_t st);
+int kpoint_step(sparc_context* c, void* X, int ns, int64_t ldx, int m, double a, double b,
+                double a0, double* eig, int eig_on_host, cudaStream_t st);
 
 // Batched form (batch.cu) -------------------------------------------------
 struct BatchSysHost {
@@ -373,6 +395,7 @@ struct sparc_context {
   // ring stencil thread shape: fixed (>= 0) or tuned per ns (-1)
   int shape_fixed = -1;
   bool stall_test = false;  // options flag bit 3 (test hook, see sparc.h)
+  sparc::KpointState* kpt = nullptr;  // set on handles of a Bloch wavevector (complex)
   std::vector<std::pair<int, int>> shape_by_ns;  // (ns, shape) tuned so far
   sparc_tuning tuning{};
   double* Y64 = nullptr;     // mixed handles: FP64 Yt = H Xt of a step (ld x ns_max)

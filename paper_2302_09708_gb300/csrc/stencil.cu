@@ -481,6 +481,16 @@ __global__ void k_fill_uniform(double* v, int64_t n, uint64_t seed) {
   }
 }
 
+// complex (interleaved) vector with real part u(seed, i) - 1/2, imaginary part 0
+__global__ void k_fill_uniform_re(double* v, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = mix64(seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ULL);
+    v[2 * i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    v[2 * i + 1] = 0.0;
+  }
+}
+
 // ab layout: ab[2j] = alpha_j, ab[2j+1] = beta_j; ab[-1] slot handled by j == 0.
 __global__ void k_lz_sub_prev(double* __restrict__ w, const double* __restrict__ vp,
                               const double* __restrict__ ab, int j, int64_t n) {
@@ -564,6 +574,11 @@ cudaError_t dot_f64(const double* u, const double* v, int64_t n, double* partial
 
 cudaError_t fill_uniform_f64(double* v, int64_t n, uint64_t seed, cudaStream_t st) {
   note_launch(), k_fill_uniform<<<grid_for(n), 256, 0, st>>>(v, n, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t fill_uniform_re_c128(double* v, int64_t n, uint64_t seed, cudaStream_t st) {
+  note_launch(), k_fill_uniform_re<<<grid_for(n), 256, 0, st>>>(v, n, seed);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ SPARC_ERR_NOT_SPD = 4
 SPARC_ERR_NUMERIC = 5
 SPARC_ERR_TIMEOUT = 6
 SPARC_PERIODIC, SPARC_DIRICHLET = 0, 1
-SPARC_F64, SPARC_F32 = 0, 1
+SPARC_F64, SPARC_F32, SPARC_C128 = 0, 1, 2
 SPARC_PREC_FP64, SPARC_PREC_MIXED = 0, 1
 
 _STATUS = {1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_SPD", 5: "NUMERIC", 6: "TIMEOUT"}
@@ -78,7 +78,8 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_hpsi",
            "sparc_rotate", "sparc_chefsi_step", "sparc_get_timings", "sparc_project_noalloc",
            "sparc_occupations", "sparc_density", "sparc_nonlocal_forces",
            "sparc_batch_create", "sparc_batch_destroy", "sparc_batch_last_error",
-           "sparc_batch_chefsi_step", "sparc_batch_get_info", "sparc_get_tuning"]
+           "sparc_batch_chefsi_step", "sparc_batch_get_info", "sparc_get_tuning",
+           "sparc_create_kpoint"]
 
 _lib = None
 
@@ -99,6 +100,9 @@ def load(build: bool = True):
     vp, i, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
     L.sparc_create.argtypes = [ctypes.POINTER(sparc_grid), vp, ctypes.POINTER(sparc_nonlocal),
                                ctypes.POINTER(sparc_options), ctypes.POINTER(vp)]
+    L.sparc_create_kpoint.argtypes = [ctypes.POINTER(sparc_grid), vp,
+                                      ctypes.POINTER(sparc_nonlocal), vp,
+                                      ctypes.POINTER(sparc_options), vp, ctypes.POINTER(vp)]
     L.sparc_destroy.argtypes = [vp]
     L.sparc_last_error.argtypes = [vp]
     L.sparc_last_error.restype = ctypes.c_char_p
@@ -155,7 +159,8 @@ def _block(X):
         import torch
         if X.dim() != 2 or X.stride(1) != 1:
             raise ValueError("orbital block must be a (ns, ld) tensor with unit inner stride")
-        dt = {torch.float64: SPARC_F64, torch.float32: SPARC_F32}.get(X.dtype)
+        dt = {torch.float64: SPARC_F64, torch.float32: SPARC_F32,
+              torch.complex128: SPARC_C128}.get(X.dtype)
         ptr = X.data_ptr()
         return ptr, X.shape[0], X.stride(0), dt
     if dt is None:
@@ -169,10 +174,12 @@ def _arr(a, dtype):
 
 # -- C-named functions -------------------------------------------------------
 def sparc_create(system, precision: int = SPARC_PREC_FP64, ns_max: int = 1, device: int = 0,
-                 flags: int = 0, stencil_shape: int = 0, timeout_cycles: int = 0):
+                 flags: int = 0, stencil_shape: int = 0, timeout_cycles: int = 0, kvec=None):
     """Create a handle for a `synth.System`-like object (grid, Veff, projectors).
     flags, stencil_shape and timeout_cycles are the sparc_options fields of the
-    same names (flags bit 0 selects the generic stencil form)."""
+    same names (flags bit 0 selects the generic stencil form).  With `kvec`
+    (three components, 1/bohr) the handle is H(k) at that Bloch wavevector
+    (sparc_create_kpoint; complex blocks)."""
     L = load()
     g = sparc_grid(system.nx, system.ny, system.nz, system.h, (ctypes.c_int * 3)(*system.bc))
     keep = [_arr(system.veff, np.float64), _arr(system.supp_ptr, np.int64),
@@ -184,8 +191,17 @@ def sparc_create(system, precision: int = SPARC_PREC_FP64, ns_max: int = 1, devi
                         cp.ctypes.data, chi.ctypes.data, pp.ctypes.data, gam.ctypes.data)
     opt = sparc_options(precision, ns_max, device, flags, stencil_shape, 0, timeout_cycles)
     out = ctypes.c_void_p()
-    rc = L.sparc_create(ctypes.byref(g), veff.ctypes.data, ctypes.byref(nl), ctypes.byref(opt),
-                        ctypes.byref(out))
+    if kvec is not None:
+        pos = _arr(np.asarray(system.positions).reshape(-1, 3) if system.natoms else
+                   np.zeros((1, 3)), np.float64)
+        kv = _arr(kvec, np.float64).reshape(3)
+        keep += [pos, kv]
+        rc = L.sparc_create_kpoint(ctypes.byref(g), veff.ctypes.data, ctypes.byref(nl),
+                                   pos.ctypes.data, ctypes.byref(opt), kv.ctypes.data,
+                                   ctypes.byref(out))
+    else:
+        rc = L.sparc_create(ctypes.byref(g), veff.ctypes.data, ctypes.byref(nl),
+                            ctypes.byref(opt), ctypes.byref(out))
     _check(None, rc)
     return out
 
@@ -298,17 +314,20 @@ class Handle:
     """Convenience wrapper owning one sparc_handle."""
 
     def __init__(self, system, precision="fp64", ns_max=1, device=0, options_flags=0,
-                 stencil_shape=0, timeout_cycles=0):
+                 stencil_shape=0, timeout_cycles=0, kvec=None):
         prec = SPARC_PREC_MIXED if precision == "mixed" else SPARC_PREC_FP64
         self.system = system
         self.precision = precision
         self.ns_max = ns_max
+        self.kvec = kvec
         self.h = sparc_create(system, prec, ns_max, device, options_flags, stencil_shape,
-                              timeout_cycles)
+                              timeout_cycles, kvec)
 
     @property
     def dtype(self):
         import torch
+        if self.kvec is not None:
+            return torch.complex128
         return torch.float32 if self.precision == "mixed" else torch.float64
 
     def close(self):
@@ -334,19 +353,27 @@ class Handle:
         return sparc_cheb_filter(self.h, X, degree, a, b, a0, stream)
 
     def project(self, Xt, Yt, stream=None):
+        """(Hs, Ms).  Real handles: the column-major results as (ns, ns) tensors
+        (symmetric, so their orientation does not matter).  k-point handles:
+        the complex Hermitian matrices in their proper orientation."""
         import torch
         ns = Xt.shape[0]
-        Hs = torch.empty((ns, ns), dtype=torch.float64, device=Xt.device)
-        Ms = torch.empty((ns, ns), dtype=torch.float64, device=Xt.device)
-        return sparc_project(self.h, Xt, Yt, Hs, Ms, stream)
+        dt = torch.complex128 if self.kvec is not None else torch.float64
+        Hs = torch.empty((ns, ns), dtype=dt, device=Xt.device)
+        Ms = torch.empty((ns, ns), dtype=dt, device=Xt.device)
+        sparc_project(self.h, Xt, Yt, Hs, Ms, stream)
+        if self.kvec is not None:
+            return Hs.t(), Ms.t()
+        return Hs, Ms
 
     def subspace_eig(self, Hs, Ms, stream=None):
         """Returns (lam, Z) with Z an ordinary (row, col) matrix."""
         import torch
         ns = Hs.shape[0]
         lam = torch.empty(ns, dtype=torch.float64, device=Hs.device)
-        Zt = torch.empty((ns, ns), dtype=torch.float64, device=Hs.device)
-        sparc_subspace_eig(self.h, Hs.contiguous(), Ms.contiguous(), lam, Zt, stream)
+        Zt = torch.empty((ns, ns), dtype=Hs.dtype, device=Hs.device)
+        # column-major storage of a matrix is the row-major storage of its transpose
+        sparc_subspace_eig(self.h, Hs.t().contiguous(), Ms.t().contiguous(), lam, Zt, stream)
         return lam, Zt.t()
 
     def rotate(self, Xt, Z, Xout=None, stream=None):
