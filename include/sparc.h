@@ -187,7 +187,9 @@ int sparc_create(const sparc_grid* g, const double* veff, const sparc_nonlocal* 
  * (column-major, interleaved (re, im) doubles, ld counted in complex entries).
  * Calls accepted: sparc_hpsi, sparc_spectrum_bounds, sparc_cheb_filter,
  * sparc_project, sparc_subspace_eig, sparc_rotate (their ns x ns matrices are
- * complex, column-major, interleaved: 2 ns^2 doubles each; lam stays real),
+ * complex, column-major, interleaved: 2 ns^2 doubles each; lam stays real;
+ * sparc_project makes Hs and Ms Hermitian from their upper triangles, so their
+ * diagonals are real),
  * sparc_chefsi_step, sparc_occupations, sparc_get_timings; the others return
  * INVALID_ARG.  The subspace eigensolve uses cyclic Jacobi rotations (returns
  * NUMERIC if 40 sweeps do not converge).  Errors: as sparc_create.

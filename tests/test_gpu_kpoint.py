@@ -97,9 +97,13 @@ def test_project_and_rotate_kpoint():
     rH, rM = kpoint.project(X, Y)
     aX, aY = np.abs(X), np.abs(Y)
     bH, bM = 1e-12 * (aX @ aY.T), 1e-12 * (aX @ aX.T)
-    # the GPU form takes Hs from its upper triangle and mirrors it Hermitian
-    iu = np.triu_indices(24)
-    assert np.all(np.abs(Hs.cpu().numpy()[iu] - rH[iu]) <= bH[iu])
+    # the GPU form makes Hs Hermitian from its upper triangle (real diagonal),
+    # as it is in a step (Yt = H Xt): strict upper triangle and real diagonal
+    iu = np.triu_indices(24, 1)
+    Hg = Hs.cpu().numpy()
+    assert np.all(np.abs(Hg[iu] - rH[iu]) <= bH[iu])
+    assert np.all(np.abs(np.diag(Hg) - np.diag(rH).real) <= np.diag(bH))
+    assert np.max(np.abs(Hg - Hg.conj().T)) == 0.0
     assert np.all(np.abs(Ms.cpu().numpy() - rM) <= bM)
     Z = np.random.default_rng(5).standard_normal((24, 24)) + 1j * np.random.default_rng(6).standard_normal((24, 24))
     R = h.rotate(cplx(X), cplx(Z)).cpu().numpy()
