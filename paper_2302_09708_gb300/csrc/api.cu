@@ -484,6 +484,22 @@ int mixed_yt_project(sparc_context* c, const float* Xt, int64_t ldt, int ns, cud
   return SPARC_OK;
 }
 
+// The handle's tensor-core GEMM buffers, lent to the subspace eigensolver (idle
+// between the projection and the rotation); null when the handle has none.
+EigGemm eig_gemm_of(const sparc_context* c) {
+  EigGemm g;
+  if (!c->tc_gemm || !c->S1 || !c->SZ || !c->esc) return g;
+  const bool f64 = c->precision != SPARC_PREC_MIXED;
+  g.SA = c->S1;
+  g.SZ = c->SZ;
+  g.esc = c->esc;
+  g.sa_elems = tc_slice_elems(c->ld, c->nd, c->ns_max, f64);
+  g.sz_elems = (size_t)tc_digits(true) * ((c->ns_max + 7) / 8 * 8) * c->ns_max;
+  g.esc_bytes = tc_esc_bytes(c->ld, c->nd, c->ns_max);
+  g.status = c->eig.status + 2;
+  return g;
+}
+
 template <typename T>
 int do_step(sparc_context* c, T* X, int64_t ldx, int ns, int m, double a, double b, double a0,
             double* eig, int eig_on_host, cudaStream_t st) {
@@ -511,7 +527,10 @@ int do_step(sparc_context* c, T* X, int64_t ldx, int ns, int m, double a, double
   }
   if (rc) return rc;
   CK(c, cudaEventRecord(c->ev[4], st));
-  CK(c, gen_eig(c->eig, c->Hs, c->Ms, ns, c->lam, c->Z, st));
+  {
+    const EigGemm eg = eig_gemm_of(c);
+    CK(c, gen_eig(c->eig, c->Hs, c->Ms, ns, c->lam, c->Z, st, &eg));
+  }
   CK(c, cudaEventRecord(c->ev[5], st));
   rc = do_rotate<T>(c, Xt, ldt, ns, c->Z, X, ldx, st);
   if (rc) return rc;
@@ -871,7 +890,9 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
     CK(c, cudaMalloc(&c->S1, se * sizeof(__nv_bfloat16)));
     CK(c, cudaMalloc(&c->S2, se * sizeof(__nv_bfloat16)));
     const size_t zk = (size_t)(c->ns_max + 7) / 8 * 8;
-    CK(c, cudaMalloc(&c->SZ, (size_t)tc_digits(f64) * zk * c->ns_max * sizeof(__nv_bfloat16)));
+    // six digits whatever the precision: the subspace eigensolver's FP64-accurate
+    // products borrow this buffer
+    CK(c, cudaMalloc(&c->SZ, (size_t)tc_digits(true) * zk * c->ns_max * sizeof(__nv_bfloat16)));
     CK(c, cudaMalloc(&c->esc, tc_esc_bytes(c->ld, nd, c->ns_max)));
     if (!f64) CK(c, cudaMalloc(&c->Y64, (size_t)c->ld * c->ns_max * sizeof(double)));
   }
@@ -1045,7 +1066,9 @@ int sparc_subspace_eig(sparc_handle c, const double* Hs, const double* Ms, int n
   set_wait_cycles(c->wait_cycles);
   cudaStream_t st = (cudaStream_t)stream;
   if (c->kpt) return kpoint_eig(c, Hs, Ms, ns, lam, Z, st);
-  CK(c, gen_eig(c->eig, Hs, Ms, ns, lam, Z, st));
+  CK(c, cudaMemsetAsync(c->eig.status + 2, 0, sizeof(int), st));
+  const EigGemm eg = eig_gemm_of(c);
+  CK(c, gen_eig(c->eig, Hs, Ms, ns, lam, Z, st, &eg));
   return read_status(c, st);
 }
 
@@ -1416,7 +1439,9 @@ int batch_step_impl(sparc_batch_context* b, void* const* X, const int* ns, const
         rc = mixed_yt_project(c, (const float*)xt[i], ldt[i], ns[i], nullptr, w);
       else
         rc = do_project<T>(c, xt[i], ldt[i], yt[i], c->ld, ns[i], c->Hs, c->Ms, w);
-      if (!rc && gen_eig(c->eig, c->Hs, c->Ms, ns[i], c->lam, c->Z, w) != cudaSuccess) rc = SPARC_ERR_CUDA;
+      const EigGemm eg = eig_gemm_of(c);
+      if (!rc && gen_eig(c->eig, c->Hs, c->Ms, ns[i], c->lam, c->Z, w, &eg) != cudaSuccess)
+        rc = SPARC_ERR_CUDA;
       if (!rc) rc = do_rotate<T>(c, xt[i], ldt[i], ns[i], c->Z, (T*)X[i], ld[i], w);
       if (rc) b->err = c->err;
     }

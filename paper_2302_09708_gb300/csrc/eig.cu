@@ -25,6 +25,7 @@ namespace sparc {
 namespace {
 
 constexpr int kNb = 32;  // Cholesky panel width
+constexpr int kTcEigMin = 256;  // smallest n for the tensor-core mode
 
 enum { ST_OK = 0, ST_NOT_SPD = 4, ST_NUMERIC = 5 };
 
@@ -737,6 +738,10 @@ cudaError_t eig_alloc(EigWork& w, int nmax) {
   take(&w.status, 64);
   take(&w.clus, (size_t)2 * nmax * 4 + 8);
   take(&w.piv, nn * 4);
+  if (nmax >= kTcEigMin) {
+    take(&w.X0, nn * 8);
+    take(&w.X1, nn * 8);
+  }
   if (err != cudaSuccess) eig_free(w);
   return err;
 }
@@ -744,8 +749,108 @@ cudaError_t eig_alloc(EigWork& w, int nmax) {
 void eig_free(EigWork& w) {
   cudaFree(w.L); cudaFree(w.A); cudaFree(w.W); cudaFree(w.V); cudaFree(w.d); cudaFree(w.e);
   cudaFree(w.tau); cudaFree(w.lu); cudaFree(w.scal); cudaFree(w.status); cudaFree(w.clus);
-  cudaFree(w.piv);
+  cudaFree(w.piv); cudaFree(w.X0); cudaFree(w.X1);
   w = EigWork{};
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core mode (n >= kTcEigMin): the O(n^3) products of the reduction, the
+// re-orthonormalisation and the back-substitution as FP64-accurate six-digit
+// tensor-core GEMMs (tc_rotate: C = A B, A m x k with a leading dimension, B
+// k x k contiguous), with the triangular factors inverted explicitly:
+//   inv([[L11, 0], [L21, L22]]) = [[X11, 0], [-X22 L21 X11, X22]],
+// X21 formed as -(U^T X22^T)^T with U = L21 X11, so that every product has a
+// square right factor; blocks of <= 128 rows are inverted by substitution.
+// ---------------------------------------------------------------------------
+// B (n x m, ldb) = scale A^T (A m x n, lda), or B = scale A without transposing
+__global__ void k_copy_scaled(const double* __restrict__ A, int64_t lda, int m, int n,
+                              double* __restrict__ B, int64_t ldb, int transpose, double scale) {
+  __shared__ double tile[32][33];
+  const int bi = blockIdx.x * 32, bj = blockIdx.y * 32;  // A rows, columns
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = bi + threadIdx.x, j = bj + r;
+    if (i < m && j < n) tile[r][threadIdx.x] = A[i + (int64_t)j * lda];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    if (transpose) {
+      const int i = bj + threadIdx.x, j = bi + r;  // B row i = A column, B column j = A row
+      if (i < n && j < m) B[i + (int64_t)j * ldb] = scale * tile[threadIdx.x][r];
+    } else {
+      const int i = bi + threadIdx.x, j = bj + r;
+      if (i < m && j < n) B[i + (int64_t)j * ldb] = scale * tile[r][threadIdx.x];
+    }
+  }
+}
+
+// X = L^-1 for a lower-triangular n x n block (n <= 128): thread j forms
+// column j by forward substitution on e_j; the upper triangle is zeroed
+__global__ void k_trinv_leaf(const double* __restrict__ L, int64_t ldl, int n, double* X,
+                             int64_t ldx) {
+  const int j = threadIdx.x;
+  if (j >= n) return;
+  for (int i = 0; i < j; ++i) X[i + (int64_t)j * ldx] = 0.0;
+  for (int i = j; i < n; ++i) {
+    double a = i == j ? 1.0 : 0.0;
+    for (int k = j; k < i; ++k) a -= L[i + (int64_t)k * ldl] * X[k + (int64_t)j * ldx];
+    X[i + (int64_t)j * ldx] = a / L[i + (int64_t)i * ldl];
+  }
+}
+
+cudaError_t copy_scaled(const double* A, int64_t lda, int m, int n, double* B, int64_t ldb,
+                        bool transpose, double scale, cudaStream_t st) {
+  const dim3 g((unsigned)((m + 31) / 32), (unsigned)((n + 31) / 32));
+  note_launch(), k_copy_scaled<<<g, dim3(32, 8), 0, st>>>(A, lda, m, n, B, ldb, transpose ? 1 : 0,
+                                                          scale);
+  return cudaGetLastError();
+}
+
+// C (m x k, ldc) = A (m x k, lda) B (k x k contiguous)
+cudaError_t gemm_tc(const EigGemm& g, const double* A, int64_t lda, int m, int k, const double* B,
+                    double* C, int64_t ldc, cudaStream_t st) {
+  return tc_rotate(A, lda, m, k, B, C, ldc, g.SA, g.SZ, g.esc, g.status, st);
+}
+
+// X (ldx) = L^-1 for lower-triangular L (n x n, ldl); scratch: 2 n^2 doubles
+cudaError_t trinv_lower(const EigGemm& g, const double* L, int64_t ldl, int n, double* X,
+                        int64_t ldx, double* scratch, cudaStream_t st) {
+  if (n <= 128) {
+    note_launch(), k_trinv_leaf<<<1, 128, 0, st>>>(L, ldl, n, X, ldx);
+    return cudaGetLastError();
+  }
+  const int n1 = (n / 2 + 63) / 64 * 64, n2 = n - n1;
+  cudaError_t e;
+  if ((e = trinv_lower(g, L, ldl, n1, X, ldx, scratch, st)) != cudaSuccess) return e;
+  if ((e = trinv_lower(g, L + n1 + (int64_t)n1 * ldl, ldl, n2, X + n1 + (int64_t)n1 * ldx, ldx,
+                       scratch, st)) != cudaSuccess)
+    return e;
+  double* S0 = scratch;                      // X11 contiguous (n1 x n1)
+  double* U = S0 + (int64_t)n1 * n1;         // L21 X11 (n2 x n1)
+  double* Ut = U + (int64_t)n2 * n1;         // U^T (n1 x n2)
+  double* S3 = Ut + (int64_t)n1 * n2;        // X22^T contiguous (n2 x n2)
+  double* W = S0;                            // U^T X22^T (n1 x n2), over S0 once U is made
+  if ((e = copy_scaled(X, ldx, n1, n1, S0, n1, false, 1.0, st)) != cudaSuccess) return e;
+  if ((e = gemm_tc(g, L + n1, ldl, n2, n1, S0, U, n2, st)) != cudaSuccess) return e;
+  if ((e = copy_scaled(U, n2, n2, n1, Ut, n1, true, 1.0, st)) != cudaSuccess) return e;
+  if ((e = copy_scaled(X + n1 + (int64_t)n1 * ldx, ldx, n2, n2, S3, n2, true, 1.0, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = gemm_tc(g, Ut, n1, n1, n2, S3, W, n1, st)) != cudaSuccess) return e;
+  // X21 = -W^T; X12 = 0
+  if ((e = copy_scaled(W, n1, n1, n2, X + n1, ldx, true, -1.0, st)) != cudaSuccess) return e;
+  return cudaMemset2DAsync(X + (int64_t)n1 * ldx, ldx * sizeof(double), 0, n1 * sizeof(double),
+                           n2, st);
+}
+
+// Whether the tensor-core mode runs for n: the GEMM's digit buffers must hold
+// six digits of an n x n operand (both factors) and its exponent tables.
+bool tc_eig_fits(const EigGemm* g, int n) {
+  if (!g || !g->SA || !g->SZ || !g->esc || n < kTcEigMin) return false;
+  const size_t ldk = (size_t)(n + 7) / 8 * 8;
+  const size_t need = 6 * (size_t)((n + 127) / 128 * 128) * ldk;
+  const size_t nq = (ldk + 255) / 256, MP = (n + 127) / 128 * 128;
+  const size_t esc = 4 * ((n + 63) / 64 * 64) + nq * 2 * MP + 256;
+  return g->sa_elems >= need && g->sz_elems >= 6 * ldk * n && g->esc_bytes >= esc;
 }
 
 // Checked enqueue: return the first failing runtime call's error at once.
@@ -763,7 +868,7 @@ void eig_free(EigWork& w) {
   } while (0)
 
 cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, double* lam, double* Z,
-                    cudaStream_t st) {
+                    cudaStream_t st, const EigGemm* g) {
   // Buffers (n x n unless noted): L (Cholesky factor of Ms, kept to the end),
   // A, W, V, lu (4 n x n), piv (n x n ints).  status[0]: NOT_SPD/NUMERIC of the
   // problem; status[1]: failure of the internal re-orthonormalisation.
@@ -779,10 +884,19 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
   EL(k_tril_copy<<<nb, 256, 0, st>>>(w.W, w.L, n));
   EL(k_transpose<<<tg, tb, 0, st>>>(w.L, w.V, n));  // V = L row-major (forward solves)
   // 2. A = sym(L^-1 (L^-1 Hs)^T)
-  EK(trsm<true>(w.V, Hs, w.W, n, st0, st));          // W = L^-1 Hs
-  EL(k_transpose<<<tg, tb, 0, st>>>(w.W, w.A, n));  // A = W^T
-  EK(trsm<true>(w.V, w.A, w.W, n, st0, st));         // W = L^-1 W^T
-  EL(k_symmetrize<<<nb, 256, 0, st>>>(w.W, w.A, n));
+  const bool tcm = tc_eig_fits(g, n) && w.X0 && w.X1;
+  if (tcm) {
+    EK(trinv_lower(*g, w.L, n, n, w.X0, n, w.lu, st));           // X0 = L^-1
+    EK(copy_scaled(w.X0, n, n, n, w.X1, n, true, 1.0, st));       // X1 = L^-T
+    EK(gemm_tc(*g, Hs, n, n, n, w.X1, w.W, n, st));                // W = Hs L^-T
+    EK(gemm_tc(*g, w.X0, n, n, n, w.W, w.V, n, st));               // V = L^-1 Hs L^-T
+    EL(k_symmetrize<<<nb, 256, 0, st>>>(w.V, w.A, n));
+  } else {
+    EK(trsm<true>(w.V, Hs, w.W, n, st0, st));          // W = L^-1 Hs
+    EL(k_transpose<<<tg, tb, 0, st>>>(w.W, w.A, n));  // A = W^T
+    EK(trsm<true>(w.V, w.A, w.W, n, st0, st));         // W = L^-1 W^T
+    EL(k_symmetrize<<<nb, 256, 0, st>>>(w.W, w.A, n));
+  }
   // 3. Householder tridiagonalisation; reflectors in the rows of Hv = lu[0, nn)
   double* Hv = w.lu;
   double* p = w.tau;
@@ -841,7 +955,17 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
                                                     w.piv, VT));
   EL(k_inviter_cluster<<<n, 256, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv, VT));
   //    Cholesky-QR pass: G = VT^T VT = R R^T, Q = VT R^-T  (Q^T = R^-1 VT^T)
-  {
+  if (tcm) {
+    double* G = w.lu + nn;
+    EK(copy_scaled(VT, n, n, n, w.V, n, true, 1.0, st));            // V = VT^T
+    EK(gemm_tc(*g, w.V, n, n, n, VT, G, n, st));                     // G = VT^T VT
+    EK(cholesky(G, n, st1, st));
+    EL(k_tril_copy<<<nb, 256, 0, st>>>(G, w.V, n));                  // V = R (lower)
+    EK(trinv_lower(*g, w.V, n, n, w.X0, n, w.lu + 2 * nn, st));      // X0 = R^-1
+    EK(copy_scaled(w.X0, n, n, n, G, n, true, 1.0, st));             // G = R^-T
+    EK(gemm_tc(*g, VT, n, n, n, G, w.V, n, st));                     // V = VT R^-T = Q
+    EK(cudaMemcpyAsync(VT, w.V, nn * 8, cudaMemcpyDeviceToDevice, st));
+  } else {
     double* G1 = w.lu;           // unused copy (projection writes two outputs)
     double* G = w.lu + nn;
     double* work = w.lu + 2 * nn;  // 2 nn doubles for one split
@@ -863,7 +987,10 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
     EL(k_backtransform<<<(n + wpb - 1) / wpb, wpb * 32, smem, st>>>(w.A, VT, n));
   }
   // 7. Z = L^-T V; sign convention; NaN check
-  EK(trsm<false>(w.L, VT, Z, n, st0, st));
+  if (tcm)
+    EK(gemm_tc(*g, w.X1, n, n, n, VT, Z, n, st));
+  else
+    EK(trsm<false>(w.L, VT, Z, n, st0, st));
   EL(k_fix_signs<<<(n * 32 + 255) / 256, 256, 0, st>>>(Z, n, lam, st0));
   return cudaSuccess;
 }

@@ -264,12 +264,27 @@ struct EigWork {
   int* status = nullptr;   // device status word
   int* clus = nullptr;     // cluster bookkeeping (2 n ints)
   int* piv = nullptr;      // inverse-iteration pivot flags (n x n ints)
+  double* X0 = nullptr;    // tensor-core mode: triangular inverses (n x n each)
+  double* X1 = nullptr;
 };
 cudaError_t eig_alloc(EigWork& w, int nmax);
 void eig_free(EigWork& w);
+// Digit buffers of the FP64-accurate tensor-core GEMM (tc_rotate) that the
+// eigensolver may borrow for its O(n^3) products (the handle's projection /
+// rotation workspace); sa_elems / sz_elems are their sizes in BF16 elements.
+struct EigGemm {
+  __nv_bfloat16* SA = nullptr;
+  __nv_bfloat16* SZ = nullptr;
+  int* esc = nullptr;
+  size_t sa_elems = 0, sz_elems = 0, esc_bytes = 0;
+  int* status = nullptr;  // status word of the GEMM's bounded waits
+};
 // lam ascending, Z column-major with Z^T M Z = I. Writes *dev_status (device).
+// With `g` (and n >= 256, buffers large enough) the reduction to standard form,
+// the re-orthonormalisation and the back-substitution run as tensor-core GEMMs
+// with an explicit triangular inverse.
 cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, double* lam, double* Z,
-                    cudaStream_t st);
+                    cudaStream_t st, const EigGemm* g = nullptr);
 
 // Complex step at a Bloch wavevector (kpoint.cu) ---------------------------
 struct KpointState;

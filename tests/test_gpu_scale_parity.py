@@ -58,10 +58,32 @@ def _spd_pair(n, cond, rng, levels=None):
 
 @pytest.fixture(scope="module")
 def free_handle():
-    s = synth.free_system((16, 16, 16), 0.5, (0, 0, 0), v0=0.3)
+    """An FP64 handle whose grid (48^3 points) is large enough for the
+    tensor-core GEMM buffers to hold n x n operands up to n = 4800, so the
+    eigensolver runs its tensor-core mode (triangular inverses and GEMMs) for
+    n >= 256."""
+    s = synth.free_system((48, 48, 48), 0.5, (0, 0, 0), v0=0.3)
     h = sparc.Handle(s, "fp64", ns_max=4800)
     yield h
     h.close()
+
+
+@pytest.mark.parametrize("n,cond", [(300, 1e6), (1300, 1e4)])
+def test_subspace_eig_tensor_core_mode_matches_simt_mode(free_handle, n, cond):
+    """The same pair through the tensor-core mode and through the FP64 SIMT
+    form (a handle without tensor-core buffers, options bit 1)."""
+    rng = np.random.default_rng(n + 1)
+    H, M, _ = _spd_pair(n, cond, rng)
+    lam1, Z1 = free_handle.subspace_eig(to_dev(H), to_dev(M))
+    s = synth.free_system((16, 16, 16), 0.5, (0, 0, 0), v0=0.3)
+    simt = sparc.Handle(s, "fp64", ns_max=n, options_flags=2)
+    lam2, Z2 = simt.subspace_eig(to_dev(H), to_dev(M))
+    scale = max(1.0, cond / 1e4)
+    l1, l2 = lam1.cpu().numpy(), lam2.cpu().numpy()
+    assert np.max(np.abs(l1 - l2)) < 1e-10 * scale * np.max(np.abs(l2))
+    Z1 = Z1.cpu().numpy()
+    assert np.max(np.abs(Z1.T @ M @ Z1 - np.eye(n))) < 1e-9 * scale
+    simt.close()
 
 
 @pytest.mark.parametrize("n,cond", [(257, 1e8), (1300, 1e6)])
