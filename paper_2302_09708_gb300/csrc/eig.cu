@@ -370,14 +370,14 @@ __global__ void __launch_bounds__(256)
     acc = 0.0;
     for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += vsh[i] * p[i];
     const double K = block_sum_d(acc, sh);
-    const int m = n - k - 1;
-    const int64_t mm = (int64_t)m * m;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < mm;
-         t += (int64_t)gridDim.x * blockDim.x) {
-      const int i = k + 1 + (int)(t % m), j = k + 1 + (int)(t / m);
-      const double vi = vsh[i], vj = vsh[j];
-      const double qi = p[i] - K * vi, qj = p[j] - K * vj;
-      A[i + (int64_t)j * n] -= 2.0 * (vi * qj + qi * vj);
+    // rank-2 update of the trailing block: a warp per column, lanes along it
+    for (int j = k + 1 + gwarp; j < n; j += nwarps) {
+      const double vj = vsh[j], qj = p[j] - K * vj;
+      double* colj = A + (int64_t)j * n;
+      for (int i = k + 1 + lane; i < n; i += 32) {
+        const double vi = vsh[i];
+        colj[i] -= 2.0 * (vi * qj + (p[i] - K * vi) * vj);
+      }
     }
     if (!grid_barrier(gb, nb, &abort_sh)) return;
   }
@@ -842,6 +842,73 @@ cudaError_t trinv_lower(const EigGemm& g, const double* L, int64_t ldl, int n, d
                            n2, st);
 }
 
+// Lw = strict lower triangle of S + I / 2 (b x b): the transpose of T^-1 for a
+// block of unit reflectors H = I - 2 v v^T (S = Y^T Y)
+__global__ void k_wy_tinv_t(const double* __restrict__ S, int b, double* __restrict__ Lw) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b * b) return;
+  const int i = t % b, j = t / b;
+  Lw[t] = i > j ? S[t] : (i == j ? 0.5 : 0.0);
+}
+
+// X (m x n, ldx) -= P (m x n, ldp)
+__global__ void k_sub_block(double* __restrict__ X, int64_t ldx, const double* __restrict__ P,
+                            int64_t ldp, int m, int n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * n) return;
+  const int i = (int)(t % m), j = (int)(t / m);
+  X[i + (int64_t)j * ldx] -= P[i + (int64_t)j * ldp];
+}
+
+// X <- H_0 H_1 ... H_{n-3} X for the reflectors stored as the columns of Hv
+// (column k: v_k, entries k + 1 .. n - 1), in blocks of kWy reflectors from
+// the last block to the first: a block is I - Y T Y^T with T upper triangular,
+// T^-1 = strict upper triangle of Y^T Y + I / 2 (compact WY form), applied as
+// X_r -= Y_r (T (Y_r^T X_r)) on the rows r >= j0 + 1 the block touches, all
+// products tensor-core GEMMs.  scratch: 4 n^2 doubles.
+constexpr int kWy = 128;
+cudaError_t backtransform_wy(const EigGemm& g, const double* Hv, double* X, int n,
+                             double* scratch, cudaStream_t st) {
+  const int nref = n - 2;  // reflectors 0 .. n - 3
+  if (nref <= 0) return cudaSuccess;
+  double* Yt = scratch;                          // b x n_r
+  double* S = Yt + (int64_t)kWy * n;             // b x b
+  double* Lw = S + kWy * kWy;                    // b x b
+  double* TT = Lw + kWy * kWy;                   // b x b (T^T)
+  double* T = TT + kWy * kWy;                    // b x b
+  double* W1 = T + kWy * kWy;                    // b x n
+  double* W2 = W1 + (int64_t)kWy * n;            // b x n
+  double* P = W2 + (int64_t)kWy * n;             // n_r x n
+  cudaError_t e;
+  for (int j0 = (nref - 1) / kWy * kWy; j0 >= 0; j0 -= kWy) {
+    const int b = std::min(kWy, nref - j0);
+    const int r0 = j0 + 1, nr = n - r0;
+    const double* Yr = Hv + r0 + (int64_t)j0 * n;  // n_r x b, ld n
+    if ((e = copy_scaled(Yr, n, nr, b, Yt, b, true, 1.0, st)) != cudaSuccess) return e;
+    if ((e = tc_gemm_f64(Yt, b, b, nr, Yr, n, b, S, b, g.SA, g.SZ, g.esc, g.status, st)) !=
+        cudaSuccess)
+      return e;
+    note_launch(), k_wy_tinv_t<<<(b * b + 255) / 256, 256, 0, st>>>(S, b, Lw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    note_launch(), k_trinv_leaf<<<1, 128, 0, st>>>(Lw, b, b, TT, b);  // TT = T^T
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = copy_scaled(TT, b, b, b, T, b, true, 1.0, st)) != cudaSuccess) return e;
+    if ((e = tc_gemm_f64(Yt, b, b, nr, X + r0, n, n, W1, b, g.SA, g.SZ, g.esc, g.status, st)) !=
+        cudaSuccess)
+      return e;
+    if ((e = tc_gemm_f64(T, b, b, b, W1, b, n, W2, b, g.SA, g.SZ, g.esc, g.status, st)) !=
+        cudaSuccess)
+      return e;
+    if ((e = tc_gemm_f64(Yr, n, nr, b, W2, b, n, P, nr, g.SA, g.SZ, g.esc, g.status, st)) !=
+        cudaSuccess)
+      return e;
+    note_launch(), k_sub_block<<<(unsigned)(((int64_t)nr * n + 255) / 256), 256, 0, st>>>(
+        X + r0, n, P, nr, nr, n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Whether the tensor-core mode runs for n: the GEMM's digit buffers must hold
 // six digits of an n x n operand (both factors) and its exponent tables.
 bool tc_eig_fits(const EigGemm* g, int n) {
@@ -978,7 +1045,9 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
     EL(k_transpose<<<tg, tb, 0, st>>>(w.lu + nn, VT, n));      // VT = Q
   }
   // 6. V = Q_house VT (all reflectors, warp per column)
-  {
+  if (tcm) {
+    EK(backtransform_wy(*g, w.A, VT, n, w.lu, st));
+  } else {
     int wpb = col_warps(n);
     size_t smem = (size_t)wpb * n * sizeof(double);
     if (smem > 48 * 1024)

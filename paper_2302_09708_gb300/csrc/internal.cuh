@@ -232,6 +232,12 @@ cudaError_t tc_rotate(const float* Xt, int64_t ld, int64_t nd, int ns, const dou
 cudaError_t tc_rotate(const double* Xt, int64_t ld, int64_t nd, int ns, const double* Z,
                       double* Xout, int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc,
                       int* status, cudaStream_t st);
+// C (m x n, ldc) = A (m x k, lda) B (k x n, ldb), FP64-accurate six-digit split
+// (SA: 6 MP ldk digits, MP = m rounded up to 128, ldk = k rounded up to 8; SZ:
+// 6 n ldk digits; esc: exponent tables of the rotation form)
+cudaError_t tc_gemm_f64(const double* A, int64_t lda, int64_t m, int k, const double* B,
+                        int64_t ldb, int n, double* C, int64_t ldc, __nv_bfloat16* SA,
+                        __nv_bfloat16* SZ, int* esc, int* status, cudaStream_t st);
 
 // density.cu: Fermi occupations (one block) and rho = (2/h^3) sum f_n x_n^2.
 cudaError_t fermi_occupations(const double* lam, int ns, double ne, double kT, double* occ,

@@ -704,16 +704,18 @@ __global__ void k_chunk_exp_rows(const T* __restrict__ X, int64_t ldx, int64_t n
 
 // Chunk exponents of the rows of the row-scaled Z (rotation B operand, row j =
 // output column j): esc[q * NP + j] = E(max over k in chunk q of |Z[k + j n]| 2^f_k).
-__global__ void k_chunk_exp_z(const double* __restrict__ Z, int n, const int* __restrict__ fcol,
-                              int nq, int NP, int8_t* __restrict__ esc) {
+// Z: K x N, column-major with leading dimension ldz
+__global__ void k_chunk_exp_z(const double* __restrict__ Z, int K, int N, int64_t ldz,
+                              const int* __restrict__ fcol, int nq, int NP,
+                              int8_t* __restrict__ esc) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= (int64_t)n * nq) return;
-  const int j = (int)(w % n), q = (int)(w / n);
+  if (w >= (int64_t)N * nq) return;
+  const int j = (int)(w % N), q = (int)(w / N);
   long long m = 0;
-  const int k1 = min((q + 1) * kQ, n);
+  const int k1 = min((q + 1) * kQ, K);
   for (int k = q * kQ + lane; k < k1; k += 32)
-    m = max(m, mag_key(Z[k + (int64_t)j * n], -fcol[k]));
+    m = max(m, mag_key(Z[k + (int64_t)j * ldz], -fcol[k]));
   m = warp_max(m);
   if (lane == 0) esc[(int64_t)q * NP + j] = chunk_exponent_key(m);
 }
@@ -770,18 +772,18 @@ __global__ void k_slice_transpose(const T* __restrict__ X, int64_t ldx, int64_t 
 // Z digits of the row-scaled Z: S[s][j][k] = digit s of Z[k + j n] 2^f_k at
 // column j's exponent, ld = ldk  (X Z = (X 2^-f) (2^f Z): the scalings cancel)
 template <int D>
-__global__ void k_slice_z(const double* __restrict__ Z, int n, const int* __restrict__ fcol,
-                          const int8_t* __restrict__ esc, int NP, __nv_bfloat16* __restrict__ S,
-                          int64_t ldk) {
-  const int64_t plane = ldk * n;
-  const int64_t tot = (int64_t)n * ldk;
+__global__ void k_slice_z(const double* __restrict__ Z, int K, int N, int64_t ldz,
+                          const int* __restrict__ fcol, const int8_t* __restrict__ esc, int NP,
+                          __nv_bfloat16* __restrict__ S, int64_t ldk) {
+  const int64_t plane = ldk * N;
+  const int64_t tot = (int64_t)N * ldk;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / ldk), k = (int)(e % ldk);
     __nv_bfloat16 d[D];
     // digits of z 2^f at exponent E are the digits of z at exponent E - f
-    digits<D>(k < n ? Z[k + (int64_t)j * n] : 0.0,
-              (int)esc[(int64_t)(k / kQ) * NP + j] - (k < n ? fcol[k] : 0), d);
+    digits<D>(k < K ? Z[k + (int64_t)j * ldz] : 0.0,
+              (int)esc[(int64_t)(k / kQ) * NP + j] - (k < K ? fcol[k] : 0), d);
 #pragma unroll
     for (int q = 0; q < D; ++q) S[q * plane + e] = d[q];
   }
@@ -922,16 +924,17 @@ cudaError_t tc_project_t(const TX* Xt, int64_t ldx, const TY* Yt, int64_t ldy, i
   return project_reduce(work, nsp, ns, Hs, Ms, st);
 }
 
+// Xout (nd x N, ldo) = Xt (nd x ns, ld) Z (ns x N, column-major, ldz)
 template <typename T>
-cudaError_t tc_rotate_t(const T* Xt, int64_t ld, int64_t nd, int ns, const double* Z, T* Xout,
-                        int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc, int* status,
-                        cudaStream_t st) {
+cudaError_t tc_rotate_t(const T* Xt, int64_t ld, int64_t nd, int ns, const double* Z, int64_t ldz,
+                        int N, T* Xout, int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ,
+                        int* esc, int* status, cudaStream_t st) {
   using P = typename PlanOf<T>::type;
   constexpr int D = P::kD;
   // digits of Xt per grid point t (over its ns entries) and of Z per column j
   const int64_t ldk = (ns + 7) / 8 * 8;
   const int nq = (int)((ldk + kQ - 1) / kQ);
-  const int MP = (int)((nd + 127) / 128 * 128), NP = (ns + 127) / 128 * 128;
+  const int MP = (int)((nd + 127) / 128 * 128), NP = (N + 127) / 128 * 128;
   int* fcol = esc;  // ns entries: column exponents of Xt
   int8_t* escT = reinterpret_cast<int8_t*>(esc + ((ns + 63) / 64 * 64));
   int8_t* escZ = escT + (size_t)nq * MP;
@@ -939,26 +942,26 @@ cudaError_t tc_rotate_t(const T* Xt, int64_t ld, int64_t nd, int ns, const doubl
   note_launch(), k_chunk_exp_rows<T><<<dim3((unsigned)std::min<int64_t>((nd + 255) / 256, 4096),
                                             nq),
                                        256, 0, st>>>(Xt, ld, nd, ns, fcol, MP, escT);
-  note_launch(), k_chunk_exp_z<<<(unsigned)(((int64_t)ns * nq * 32 + 255) / 256), 256, 0, st>>>(
-      Z, ns, fcol, nq, NP, escZ);
+  note_launch(), k_chunk_exp_z<<<(unsigned)(((int64_t)N * nq * 32 + 255) / 256), 256, 0, st>>>(
+      Z, ns, N, ldz, fcol, nq, NP, escZ);
   dim3 tg((unsigned)((nd + 31) / 32), (unsigned)((ldk + 31) / 32));
   note_launch(), k_slice_transpose<T, D><<<tg, dim3(32, 8), 0, st>>>(Xt, ld, nd, ns, fcol, escT,
                                                                      MP, SA, ldk);
-  note_launch(), k_slice_z<D><<<(unsigned)std::min<int64_t>(((int64_t)ns * ldk + 255) / 256,
+  note_launch(), k_slice_z<D><<<(unsigned)std::min<int64_t>(((int64_t)N * ldk + 255) / 256,
                                                             4096),
-                                256, 0, st>>>(Z, ns, fcol, escZ, NP, SZ, ldk);
+                                256, 0, st>>>(Z, ns, N, ldz, fcol, escZ, NP, SZ, ldk);
   CUtensorMap mA, mZ;
   if (!make_map<P>(&mA, SA, (uint64_t)ldk, (uint64_t)nd, (uint64_t)ldk, kBM) ||
-      !make_map<P>(&mZ, SZ, (uint64_t)ldk, (uint64_t)ns, (uint64_t)ldk, kBN))
+      !make_map<P>(&mZ, SZ, (uint64_t)ldk, (uint64_t)N, (uint64_t)ldk, kBN))
     return cudaErrorInvalidValue;
   TcArgs a{};
   a.M = (int)nd;
-  a.N = ns;
+  a.N = N;
   a.K = ldk;
   a.kchunk = (ldk + kQ - 1) / kQ * kQ;
   a.upper = 0;
   a.tiles_m = (int)((nd + kBM - 1) / kBM);
-  a.tiles_n = (ns + kBN - 1) / kBN;
+  a.tiles_n = (N + kBN - 1) / kBN;
   if (std::is_same<T, float>::value) {
     a.out32 = reinterpret_cast<float*>(Xout);
     a.mode = 1;
@@ -1034,12 +1037,17 @@ cudaError_t tc_project(const double* Xt, const double* Yt, int64_t ld, int64_t n
 cudaError_t tc_rotate(const float* Xt, int64_t ld, int64_t nd, int ns, const double* Z, float* Xout,
                       int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc, int* status,
                       cudaStream_t st) {
-  return tc_rotate_t<float>(Xt, ld, nd, ns, Z, Xout, ldo, SA, SZ, esc, status, st);
+  return tc_rotate_t<float>(Xt, ld, nd, ns, Z, ns, ns, Xout, ldo, SA, SZ, esc, status, st);
 }
 cudaError_t tc_rotate(const double* Xt, int64_t ld, int64_t nd, int ns, const double* Z,
                       double* Xout, int64_t ldo, __nv_bfloat16* SA, __nv_bfloat16* SZ, int* esc,
                       int* status, cudaStream_t st) {
-  return tc_rotate_t<double>(Xt, ld, nd, ns, Z, Xout, ldo, SA, SZ, esc, status, st);
+  return tc_rotate_t<double>(Xt, ld, nd, ns, Z, ns, ns, Xout, ldo, SA, SZ, esc, status, st);
+}
+cudaError_t tc_gemm_f64(const double* A, int64_t lda, int64_t m, int k, const double* B,
+                        int64_t ldb, int n, double* C, int64_t ldc, __nv_bfloat16* SA,
+                        __nv_bfloat16* SZ, int* esc, int* status, cudaStream_t st) {
+  return tc_rotate_t<double>(A, lda, m, k, B, ldb, n, C, ldc, SA, SZ, esc, status, st);
 }
 
 }  // namespace sparc
