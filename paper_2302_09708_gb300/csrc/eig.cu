@@ -370,14 +370,14 @@ __global__ void __launch_bounds__(256)
     acc = 0.0;
     for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += vsh[i] * p[i];
     const double K = block_sum_d(acc, sh);
-    // rank-2 update of the trailing block: a warp per column, lanes along it
-    for (int j = k + 1 + gwarp; j < n; j += nwarps) {
-      const double vj = vsh[j], qj = p[j] - K * vj;
-      double* colj = A + (int64_t)j * n;
-      for (int i = k + 1 + lane; i < n; i += 32) {
-        const double vi = vsh[i];
-        colj[i] -= 2.0 * (vi * qj + (p[i] - K * vi) * vj);
-      }
+    const int m = n - k - 1;
+    const int64_t mm = (int64_t)m * m;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < mm;
+         t += (int64_t)gridDim.x * blockDim.x) {
+      const int i = k + 1 + (int)(t % m), j = k + 1 + (int)(t / m);
+      const double vi = vsh[i], vj = vsh[j];
+      const double qi = p[i] - K * vi, qj = p[j] - K * vj;
+      A[i + (int64_t)j * n] -= 2.0 * (vi * qj + qi * vj);
     }
     if (!grid_barrier(gb, nb, &abort_sh)) return;
   }
