@@ -634,8 +634,8 @@ def run_slab(args, dev, stream):
 
 def run_batched(args, dev, stream):
     """Batched form on 64 uneven small systems (N^3 grids, N in 24..48, 4-40
-    atoms, Ns 40-300, degree 16-24, fixed bounds per member): time per batched step (one launch per
-    Chebyshev degree for all members, replayed CUDA graph) against the same
+    atoms, Ns 40-300, degree 16-24, fixed bounds per member): time per batched step (member
+    chains on concurrent streams and one batched eigensolve, replayed CUDA graph) against the same
     members stepped one after another through sparc_chefsi_step, in FP64 and
     mixed precision, with the largest Ritz-value difference between the two."""
     import numpy as np

@@ -346,12 +346,14 @@ int sparc_nonlocal_forces(sparc_handle h, const void* X, int ns, int64_t ld, int
  * Batched form — many independent systems (the paper treats the eigenproblems
  * of different k-points / spins / configurations as independent, Sec. II).
  * A batch is built from existing handles (same precision and device; each keeps
- * its own workspace).  One batched step runs Algorithm 1 on every member: each
- * Chebyshev degree of all members is one launch of the nonlocal-coefficient
- * kernel plus one launch of the stencil kernel; the Rayleigh-Ritz parts of the
- * members run concurrently on library streams.  The whole step is captured as a
- * CUDA graph on the first call and replayed on later calls with the same X
- * pointers, ld, ns and degrees (otherwise it is re-captured).
+ * its own workspace).  One batched step runs Algorithm 1 on every member, the
+ * whole step one CUDA graph: each member's filter, Yt = H Xt and projection
+ * (the kernels of sparc_chefsi_step) run as one chain on one of the library's
+ * streams, the members concurrently; then one batched eigensolve for all
+ * members (see sparc_batch_subspace_eig); then the rotations.  The graph is
+ * captured on the first call and replayed while the X pointers, ld, ns,
+ * degrees and bounds stay the same; otherwise it is captured again and the
+ * executable graph updated.
  */
 typedef struct sparc_batch_context* sparc_batch;
 
@@ -380,6 +382,25 @@ int sparc_batch_chefsi_step(sparc_batch b, void* const* X, const int* ns, const 
 
 /* Kernel launches per batched step (nodes of the captured graph). */
 int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step);
+
+/*
+ * sparc_batch_subspace_eig — the generalised eigensolve of sparc_subspace_eig
+ * (Algorithm 1, diagonalisation) for every member i = 0..n-1 at once.
+ * Hs[i], Ms[i]: device ns[i] x ns[i] FP64 column-major, symmetric, read only;
+ * lam[i]: device ns[i] doubles (ascending); Z[i]: device ns[i] x ns[i]
+ * column-major with Z^T Ms Z = I and each column's largest-magnitude entry
+ * positive.  1 <= ns[i] <= member i's ns_max.  Members with ns[i] <= 512 are
+ * solved together, one launch per cluster size: one thread-block cluster per
+ * member runs the steps of sparc_subspace_eig (Cholesky, reduction to
+ * standard form, Householder tridiagonalisation, multisection, inverse
+ * iteration with Cholesky-QR, back-transformation) with cluster barriers
+ * between them; larger members use sparc_subspace_eig's solver one after
+ * another.  Uses each member's eigensolver workspace.  Synchronous.  Errors:
+ * INVALID_ARG, NOT_SPD, NUMERIC, TIMEOUT, CUDA; the message names the first
+ * failing member.  sparc_batch_chefsi_step runs the same solver.
+ */
+int sparc_batch_subspace_eig(sparc_batch b, const double* const* Hs, const double* const* Ms,
+                             const int* ns, double* const* lam, double* const* Z, void* stream);
 
 /*
  * sparc_project_noalloc — the FP64 projection of sparc_project (Hs = Xt^T Yt,

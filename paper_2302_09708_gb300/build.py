@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsparc.so")
-SOURCES = ["api.cu", "stencil.cu", "stencil_tma.cu", "dense.cu", "eig.cu", "tc_gemm.cu", "batch.cu",
+SOURCES = ["api.cu", "stencil.cu", "stencil_tma.cu", "dense.cu", "eig.cu", "tc_gemm.cu",
            "density.cu", "stencil_df.cu", "forces.cu", "nonlocal.cu", "kpoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

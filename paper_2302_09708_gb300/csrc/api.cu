@@ -246,10 +246,14 @@ int ring_shape(sparc_context* c, const T* x, int64_t ldx, int ns, cudaStream_t s
 }
 
 // y = s_h (H - shift) x + s_p prev.  The nonlocal coefficients D of x are in
-// c->D when `d_ready`, else they are gathered first (k_nl_coef).  On the ring
-// path the local stencil runs first and the nonlocal term follows by support-
-// point tiles; with `want_next` that pass also leaves the coefficients of y in
-// c->D (the next recurrence step's D) and sets *next_done.
+// c->D when `d_ready`, else they are gathered first (k_nl_coef).  In the split
+// form (every handle with support-point tiles of its working precision) the
+// local stencil runs first, the TMA ring where the grid and the blocks allow
+// it and the generic tiled stencil elsewhere, and the nonlocal term follows by
+// support-point tiles; with `want_next` that pass also leaves the
+// coefficients of y in c->D (the next recurrence step's D) and sets
+// *next_done.  Without tiles (the double-FP32 stencils, the mixed form's FP64
+// Yt) the generic stencil adds the nonlocal term point by point.
 template <typename T>
 int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
           int64_t ldp, int ns, double shift, double s_h, double s_p, cudaStream_t st,
@@ -261,15 +265,16 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
   T* D = (T*)c->D;
   const double h3 = c->h * c->h * c->h;
   if (next_done) *next_done = false;
-  // the ring path keeps D projector-major (its nonlocal pass stages rows of
+  // the split form keeps D projector-major (its nonlocal pass stages rows of
   // orbitals per projector); the fused stencils read it orbital-major
   const bool has_nl = nl.natoms > 0 && nl.kp > 0;
   const bool df = std::is_same<T, double>::value && c->ring_enabled && c->df_stencil;
-  const bool ring = !df && c->ring_enabled && (!has_nl || tiles_usable<T>(c)) &&
+  const bool split = !df && (!has_nl || tiles_usable<T>(c));
+  const bool ring = split && c->ring_enabled &&
                     ring_applicable<T>(c->grid, x, ldx, y, ldy, prev, ldp, veff);
   // a D left by the previous degree's tiled pass is projector-major: any other
   // path gathers its own
-  if (!d_ready || !ring) CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st, ring));
+  if (!d_ready || !split) CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st, split));
   if (df) {
     bool used = false;
     CK(c, apply_h_ring_df(c->grid, c->lap, c->veff_df, c->nl64, (const double*)D,
@@ -317,9 +322,23 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
       }
       return SPARC_OK;
     }
-    // the ring kernel declined after all: D is projector-major, the generic
-    // kernel reads it orbital-major
-    if (has_nl) CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st, false));
+    // the ring kernel declined after all: the generic local stencil follows
+  }
+  if (split) {
+    Nonlocal<T> local = nl;
+    local.kp = 0;  // local part only; the tiled pass adds the nonlocal term
+    CK(c, apply_h<T>(c->grid, c->lap, veff, local, D, x, ldx, y, ldy, prev, ldp, ns, shift, s_h,
+                     s_p, st));
+    if (has_nl) {
+      const NlTiles<T>& t = tiles_of<T>(c);
+      T* part = want_next ? (T*)c->part : nullptr;
+      CK(c, nl_apply<T>(t, D, nl.kp, y, ldy, ns, s_h, part, st));
+      if (want_next) {
+        CK(c, nl_reduce<T>(t, part, ns, nl.kp, nl.gamma, h3, D, st));
+        if (next_done) *next_done = true;
+      }
+    }
+    return SPARC_OK;
   }
   CK(c, apply_h<T>(c->grid, c->lap, veff, nl, D, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
                    st));
@@ -1254,17 +1273,23 @@ int sparc_get_timings(sparc_handle c, sparc_timings* t) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Batched CheFSI step (many independent systems, one launch per degree).
+// Batched CheFSI step over many independent systems (the paper treats the
+// eigenproblems of different k-points, spins or configurations as independent,
+// Sec. II).  One CUDA graph holds the whole step of every member: each
+// member's filter, Yt = H Xt and projection run as one chain of launches (the
+// same kernels as sparc_chefsi_step: the TMA ring stencil where the grid
+// allows it, the generic tiled stencil elsewhere, the tiled nonlocal pass) on
+// one of a pool of forked streams, so that members proceed concurrently and
+// fill the GPU together; then one batched eigensolve for all members (a
+// thread-block cluster per member); then the rotations, again on the pool.
+// The filter's scalars are launch arguments, so the graph is captured again
+// (and the executable graph updated in place) when the blocks, sizes, degrees
+// or bounds change.
 // ---------------------------------------------------------------------------
 struct sparc_batch_context {
   std::vector<sparc_context*> hs;
   int precision = SPARC_PREC_FP64;
   int device = 0;
-  void* d_sys = nullptr;
-  void* d_items = nullptr;
-  void* h_items = nullptr;  // pinned staging of the per-degree tables
-  int max_rows = 0;         // degrees + 1 rows of nsys items
-  int64_t cta_total = 0, nl_total = 0;
   cudaStream_t cs = nullptr;
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> joins;
@@ -1273,19 +1298,28 @@ struct sparc_batch_context {
   std::vector<int64_t> key;
   long long graph_launches = 0;
   long long last_launches = 0;
+  // batched subspace eigensolve of the step: members with ns_max <=
+  // kEigBatchMax, grouped by cluster size (one launch per group); the others
+  // run gen_eig one by one
+  struct EigGroup {
+    int cluster, first, count, nmax;
+  };
+  std::vector<EigGroup> eig_groups;
+  std::vector<int> eig_large;
+  void* d_eig_items = nullptr;  // the step's table (fixed per batch)
+  void* d_eig_call = nullptr;   // table of sparc_batch_subspace_eig calls
   std::string err;
 };
 
 namespace {
 
-constexpr int kBatchWorkers = 8;
+constexpr int kBatchWorkers = 16;
 
 void batch_free(sparc_batch_context* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
-  cudaFree(b->d_sys);
-  cudaFree(b->d_items);
-  cudaFreeHost(b->h_items);
+  cudaFree(b->d_eig_items);
+  cudaFree(b->d_eig_call);
   for (auto s : b->workers) cudaStreamDestroy(s);
   for (auto e : b->joins) cudaEventDestroy(e);
   if (b->cs) cudaStreamDestroy(b->cs);
@@ -1294,37 +1328,45 @@ void batch_free(sparc_batch_context* b) {
   delete b;
 }
 
+// Groups of the batched eigensolve for problem sizes n[i]: members with
+// n <= kEigBatchMax sorted by (cluster size, n) descending into `order`, one
+// group per cluster size; the others listed in `large`.
+void eig_plan(const std::vector<int>& n, std::vector<int>* order,
+              std::vector<sparc_batch_context::EigGroup>* groups, std::vector<int>* large) {
+  std::vector<std::pair<int, int>> key;  // (cluster, member)
+  for (int i = 0; i < (int)n.size(); ++i) {
+    if (n[i] > kEigBatchMax)
+      large->push_back(i);
+    else
+      key.push_back({eig_batch_cluster(n[i]), i});
+  }
+  std::stable_sort(key.begin(), key.end(), [&](const std::pair<int, int>& a,
+                                               const std::pair<int, int>& c) {
+    return a.first != c.first ? a.first > c.first : n[a.second] > n[c.second];
+  });
+  for (size_t q = 0; q < key.size(); ++q) {
+    order->push_back(key[q].second);
+    if (groups->empty() || groups->back().cluster != key[q].first)
+      groups->push_back({key[q].first, (int)q, 0, 0});
+    groups->back().count++;
+    groups->back().nmax = std::max(groups->back().nmax, n[key[q].second]);
+  }
+}
+
 template <typename T>
 int batch_step_impl(sparc_batch_context* b, void* const* X, const int* ns, const int64_t* ld,
                     const int* degree, const double* bounds, double* const* eig,
                     cudaStream_t caller) {
   const int n = (int)b->hs.size();
-  const size_t isz = batch_item_bytes();
-  int mmax = 0;
-  for (int i = 0; i < n; ++i) mmax = std::max(mmax, degree[i]);
-  if (mmax + 1 > b->max_rows) {
-    cudaFree(b->d_items);
-    cudaFreeHost(b->h_items);
-    b->d_items = nullptr;
-    b->h_items = nullptr;
-    b->max_rows = mmax + 1;
-    if (cudaMalloc(&b->d_items, (size_t)b->max_rows * n * isz) != cudaSuccess ||
-        cudaMallocHost(&b->h_items, (size_t)b->max_rows * n * isz) != cudaSuccess) {
-      b->err = "cannot allocate batch tables";
-      return SPARC_ERR_OOM;
-    }
-  }
-  // per-system bounds and the buffer plan of the filter (as in run_filter)
-  std::vector<T*> xt(n), yt(n);
-  std::vector<int64_t> ldt(n);
-  uint8_t* tab = static_cast<uint8_t*>(b->h_items);
+  constexpr bool f64 = std::is_same<T, double>::value;
+  // per-member bounds, as sparc_chefsi_step takes them
+  std::vector<double> A(n), Bv(n), A0(n);
   for (int i = 0; i < n; ++i) {
     sparc_context* c = b->hs[i];
-    double a, bb, a0;
     if (bounds) {
-      a = bounds[3 * i];
-      bb = bounds[3 * i + 1];
-      a0 = bounds[3 * i + 2];
+      A[i] = bounds[3 * i];
+      Bv[i] = bounds[3 * i + 1];
+      A0[i] = bounds[3 * i + 2];
     } else {
       if (!c->have_bounds) {
         int rc = lanczos(c, 32, 0, &c->a0, &c->b, b->cs);
@@ -1334,126 +1376,133 @@ int batch_step_impl(sparc_batch_context* b, void* const* X, const int* ns, const
         }
         c->have_bounds = true;
       }
-      bb = c->b;
-      a0 = c->a0;
-      a = c->have_prev ? c->prev_max : a0 + 0.1 * (bb - a0);
-      a = std::min(std::max(a, a0 + 1e-3 * (bb - a0)), bb - 1e-3 * (bb - a0));
+      Bv[i] = c->b;
+      A0[i] = c->a0;
+      double a = c->have_prev ? c->prev_max : A0[i] + 0.1 * (Bv[i] - A0[i]);
+      A[i] = std::min(std::max(a, A0[i] + 1e-3 * (Bv[i] - A0[i])), Bv[i] - 1e-3 * (Bv[i] - A0[i]));
     }
-    if (!(a0 < a && a < bb)) {
+    if (!(A0[i] < A[i] && A[i] < Bv[i])) {
       b->err = "invalid argument: bounds must satisfy a0 < a < b";
       return SPARC_ERR_INVALID_ARG;
     }
-    const int m = degree[i];
-    const double e = (bb - a) / 2.0, cc = (bb + a) / 2.0;
-    double sigma = e / (a0 - cc);
-    const double sigma1 = sigma, tau = 2.0 / sigma1;
-    std::vector<T*> buf(m + 1);
-    std::vector<int64_t> lds(m + 1);
-    T* Xi = (T*)X[i];
-    buf[0] = Xi;
-    lds[0] = ld[i];
-    for (int k = 1; k <= m; ++k) {
-      T* out = (m % 2 == 1) ? ((k % 2 == 1) ? (T*)c->W1 : Xi) : ((k % 2 == 1) ? (T*)c->W1 : (T*)c->W2);
-      buf[k] = out;
-      lds[k] = out == Xi ? ld[i] : c->ld;
-    }
-    for (int k = 0; k < mmax; ++k) {
-      BatchItemHost it{};
-      if (k < m) {
-        const int deg = k + 1;
-        it.x = buf[deg - 1];
-        it.ldx = lds[deg - 1];
-        it.y = buf[deg];
-        it.ldy = lds[deg];
-        it.shift = cc;
-        it.active = 1;
-        if (deg == 1) {
-          it.prev = nullptr;
-          it.s_h = sigma1 / e;
-          it.s_p = 0.0;
-        } else {
-          const double sn = 1.0 / (tau - sigma);
-          it.prev = buf[deg - 2];
-          it.ldp = lds[deg - 2];
-          it.s_h = 2.0 * sn / e;
-          it.s_p = -sigma * sn;
-          sigma = sn;
-        }
-      }
-      batch_pack_item(it, tab + ((size_t)k * n + i) * isz);
-    }
-    xt[i] = buf[m];
-    ldt[i] = lds[m];
-    yt[i] = buf[m] == (T*)c->W1 ? (T*)c->W2 : (T*)c->W1;
-    BatchItemHost hx{};
-    hx.x = xt[i];
-    hx.ldx = ldt[i];
-    hx.y = yt[i];
-    hx.ldy = c->ld;
-    hx.s_h = 1.0;
-    hx.active = 1;
-    batch_pack_item(hx, tab + ((size_t)mmax * n + i) * isz);
   }
-  // rows beyond mmax are unused; upload the table
+  auto bits = [](double v) {
+    int64_t r;
+    memcpy(&r, &v, sizeof(r));
+    return r;
+  };
   std::vector<int64_t> key;
-  key.push_back(mmax);
   for (int i = 0; i < n; ++i) {
     key.push_back((int64_t)(uintptr_t)X[i]);
     key.push_back(ns[i]);
     key.push_back(ld[i]);
     key.push_back(degree[i]);
+    key.push_back(bits(A[i]));
+    key.push_back(bits(Bv[i]));
+    key.push_back(bits(A0[i]));
   }
   CK(b, cudaEventRecord(b->start, caller));
   CK(b, cudaStreamWaitEvent(b->cs, b->start, 0));
-  CK(b, cudaMemcpyAsync(b->d_items, b->h_items, (size_t)(mmax + 1) * n * isz,
-                        cudaMemcpyHostToDevice, b->cs));
   for (int i = 0; i < n; ++i)
     CK(b, cudaMemsetAsync(b->hs[i]->eig.status, 0, 4 * sizeof(int), b->cs));
   if (!b->exec || key != b->key) {
-    if (b->exec) {
-      cudaGraphExecDestroy(b->exec);
-      b->exec = nullptr;
+    // members to streams: largest filter work first, each to the stream with
+    // the least work so far
+    const int nw = (int)b->workers.size();
+    std::vector<int> order(n), lane(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto work = [&](int i) { return (double)b->hs[i]->nd * ns[i] * degree[i]; };
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return work(p) > work(q); });
+    std::vector<double> load(nw, 0.0);
+    for (int i : order) {
+      const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      lane[i] = w;
+      load[w] += work(i);
     }
+    auto fork = [&]() {
+      cudaEventRecord(b->fork, b->cs);
+      for (auto w : b->workers) cudaStreamWaitEvent(w, b->fork, 0);
+    };
+    auto join = [&]() {
+      for (size_t k = 0; k < b->workers.size(); ++k) {
+        cudaEventRecord(b->joins[k], b->workers[k]);
+        cudaStreamWaitEvent(b->cs, b->joins[k], 0);
+      }
+    };
     const long long l0 = launch_count();
     CK(b, cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
-    // mixed precision evaluates Yt per member in FP64 (mixed_yt_project), so
-    // the batched launches stop after the last filter degree
-    const int kend = std::is_same<T, float>::value ? mmax - 1 : mmax;
-    for (int k = 0; k <= kend; ++k) {
-      const uint8_t* rows = static_cast<const uint8_t*>(b->d_items) + (size_t)k * n * isz;
-      cudaError_t e = batch_degree<T>(b->d_sys, rows, n, b->cta_total, b->nl_total, b->cs);
-      if (e != cudaSuccess) {
-        cudaGraph_t g;
-        cudaStreamEndCapture(b->cs, &g);
-        b->err = std::string("batched degree launch: ") + cudaGetErrorString(e);
-        return SPARC_ERR_CUDA;
+    int rc = SPARC_OK;
+    std::vector<T*> xt(n);
+    std::vector<int64_t> ldt(n);
+    // filter, Yt = H Xt and projection, member by member on its stream
+    fork();
+    for (int i : order) {
+      if (rc) break;
+      sparc_context* c = b->hs[i];
+      cudaStream_t w = b->workers[lane[i]];
+      bool xt_d = false;
+      rc = run_filter<T>(c, (T*)X[i], ld[i], ns[i], degree[i], A[i], Bv[i], A0[i], true, &xt[i],
+                         &ldt[i], w, f64 ? &xt_d : nullptr);
+      if (!rc) {
+        if (!f64) {
+          rc = mixed_yt_project(c, (const float*)xt[i], ldt[i], ns[i], nullptr, w);
+        } else {
+          T* Yt = xt[i] == (T*)c->W1 ? (T*)c->W2 : (T*)c->W1;
+          rc = hstep<T>(c, xt[i], ldt[i], Yt, c->ld, nullptr, 0, ns[i], 0.0, 1.0, 0.0, w, xt_d);
+          if (!rc) rc = do_project<T>(c, xt[i], ldt[i], Yt, c->ld, ns[i], c->Hs, c->Ms, w);
+        }
+      }
+      if (rc) b->err = "system " + std::to_string(i) + ": " + c->err;
+    }
+    join();
+    // batched eigensolve (one launch per cluster size, concurrent)
+    fork();
+    size_t wk = 0;
+    for (const auto& g : b->eig_groups) {
+      cudaStream_t w = b->workers[wk++ % b->workers.size()];
+      const EigBatchItem* tab = static_cast<const EigBatchItem*>(b->d_eig_items) + g.first;
+      if (!rc && eig_batch(tab, g.count, g.cluster, g.nmax, w) != cudaSuccess) {
+        rc = SPARC_ERR_CUDA;
+        b->err = "batched eigensolve launch failed";
       }
     }
-    cudaEventRecord(b->fork, b->cs);
-    for (auto w : b->workers) cudaStreamWaitEvent(w, b->fork, 0);
-    int rc = SPARC_OK;
-    for (int i = 0; i < n && !rc; ++i) {
+    for (int i : b->eig_large) {
       sparc_context* c = b->hs[i];
-      cudaStream_t w = b->workers[i % b->workers.size()];
-      if (std::is_same<T, float>::value)
-        rc = mixed_yt_project(c, (const float*)xt[i], ldt[i], ns[i], nullptr, w);
-      else
-        rc = do_project<T>(c, xt[i], ldt[i], yt[i], c->ld, ns[i], c->Hs, c->Ms, w);
+      cudaStream_t w = b->workers[wk++ % b->workers.size()];
       const EigGemm eg = eig_gemm_of(c);
-      if (!rc && gen_eig(c->eig, c->Hs, c->Ms, ns[i], c->lam, c->Z, w, &eg) != cudaSuccess)
+      if (!rc && gen_eig(c->eig, c->Hs, c->Ms, ns[i], c->lam, c->Z, w, &eg) != cudaSuccess) {
         rc = SPARC_ERR_CUDA;
-      if (!rc) rc = do_rotate<T>(c, xt[i], ldt[i], ns[i], c->Z, (T*)X[i], ld[i], w);
-      if (rc) b->err = c->err;
+        b->err = "eigensolve launch failed";
+      }
     }
-    for (size_t k = 0; k < b->workers.size(); ++k) {
-      cudaEventRecord(b->joins[k], b->workers[k]);
-      cudaStreamWaitEvent(b->cs, b->joins[k], 0);
+    join();
+    // rotations
+    fork();
+    for (int i : order) {
+      if (rc) break;
+      sparc_context* c = b->hs[i];
+      rc = do_rotate<T>(c, xt[i], ldt[i], ns[i], c->Z, (T*)X[i], ld[i], b->workers[lane[i]]);
+      if (rc) b->err = "system " + std::to_string(i) + ": " + c->err;
     }
+    join();
     cudaGraph_t graph;
     cudaError_t ec = cudaStreamEndCapture(b->cs, &graph);
-    if (rc) return rc;
+    if (rc) {
+      if (ec == cudaSuccess) cudaGraphDestroy(graph);
+      return rc;
+    }
     CK(b, ec);
-    ec = cudaGraphInstantiate(&b->exec, graph, 0);
+    bool updated = false;
+    if (b->exec) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(b->exec, graph, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+      }
+    }
+    if (!updated) ec = cudaGraphInstantiate(&b->exec, graph, 0);
     cudaGraphDestroy(graph);
     CK(b, ec);
     b->key = key;
@@ -1511,43 +1560,6 @@ int sparc_batch_create(const sparc_handle* hs, int n, sparc_batch* out) {
   };
   cudaError_t e = cudaSetDevice(b->device);
   if (e != cudaSuccess) return fail("cudaSetDevice", e);
-  std::vector<BatchSysHost> sys(n);
-  for (int i = 0; i < n; ++i) {
-    sparc_context* c = hs[i];
-    BatchSysHost& s = sys[i];
-    s = BatchSysHost{};
-    s.nx = c->grid.nx; s.ny = c->grid.ny; s.nz = c->grid.nz;
-    for (int d = 0; d < 3; ++d) s.bc[d] = c->grid.bc[d];
-    s.ns = c->ns_max;
-    s.diag = c->lap.diag;
-    for (int p = 0; p <= kRadius; ++p) s.off[p] = c->lap.off[p];
-    s.h3 = c->h * c->h * c->h;
-    const bool mixed = c->precision == SPARC_PREC_MIXED;
-    s.veff = mixed ? (const void*)c->veff32 : (const void*)c->veff64;
-    s.natoms = c->nl64.natoms;
-    s.kp = c->nl64.kp;
-    s.pull_ptr = c->nl64.pull_ptr;
-    s.pull_k = c->nl64.pull_k;
-    s.pull_chi = mixed ? (const void*)c->nl32.pull_chi : (const void*)c->nl64.pull_chi;
-    s.supp_ptr = c->nl64.supp_ptr;
-    s.supp_idx = c->nl64.supp_idx;
-    s.nproj = c->nl64.nproj;
-    s.chi_ptr = c->nl64.chi_ptr;
-    s.chi = mixed ? (const void*)c->nl32.chi : (const void*)c->nl64.chi;
-    s.proj_ptr = c->nl64.proj_ptr;
-    s.gamma = c->nl64.gamma;
-    s.D = c->D;
-  }
-  if (b->precision == SPARC_PREC_MIXED)
-    batch_layout<float>(sys, &b->cta_total, &b->nl_total);
-  else
-    batch_layout<double>(sys, &b->cta_total, &b->nl_total);
-  std::vector<uint8_t> packed(batch_sys_bytes() * n);
-  for (int i = 0; i < n; ++i) batch_pack_sys(sys[i], packed.data() + i * batch_sys_bytes());
-  if ((e = cudaMalloc(&b->d_sys, packed.size())) != cudaSuccess) return fail("cudaMalloc", e);
-  if ((e = cudaMemcpy(b->d_sys, packed.data(), packed.size(), cudaMemcpyHostToDevice)) !=
-      cudaSuccess)
-    return fail("cudaMemcpy", e);
   if ((e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking)) != cudaSuccess)
     return fail("cudaStreamCreate", e);
   const int nw = std::min(kBatchWorkers, n);
@@ -1565,6 +1577,23 @@ int sparc_batch_create(const sparc_handle* hs, int n, sparc_batch* out) {
     if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
       return fail("cudaEventCreate", e);
   if ((e = cudaEventCreate(&b->stop)) != cudaSuccess) return fail("cudaEventCreate", e);
+  // the step's batched eigensolve: each member solves its ns_max problem in
+  // its own subspace buffers and eigensolver workspace
+  std::vector<int> nsz(n), order;
+  for (int i = 0; i < n; ++i) nsz[i] = hs[i]->ns_max;
+  eig_plan(nsz, &order, &b->eig_groups, &b->eig_large);
+  std::vector<EigBatchItem> tab;
+  for (int i : order) {
+    sparc_context* c = hs[i];
+    tab.push_back(eig_batch_item(c->eig, c->Hs, c->Ms, c->ns_max, c->lam, c->Z));
+  }
+  const size_t tb = std::max<size_t>(1, (size_t)n) * sizeof(EigBatchItem);
+  if ((e = cudaMalloc(&b->d_eig_items, tb)) != cudaSuccess) return fail("cudaMalloc", e);
+  if ((e = cudaMalloc(&b->d_eig_call, tb)) != cudaSuccess) return fail("cudaMalloc", e);
+  if (!tab.empty() &&
+      (e = cudaMemcpy(b->d_eig_items, tab.data(), tab.size() * sizeof(EigBatchItem),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail("cudaMemcpy", e);
   *out = b;
   return SPARC_OK;
 }
@@ -1604,6 +1633,54 @@ int sparc_batch_chefsi_step(sparc_batch b, void* const* X, const int* ns, const 
 int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step) {
   if (!b || !launches_per_step) return SPARC_ERR_INVALID_ARG;
   *launches_per_step = b->last_launches;
+  return SPARC_OK;
+}
+
+int sparc_batch_subspace_eig(sparc_batch b, const double* const* Hs, const double* const* Ms,
+                             const int* ns, double* const* lam, double* const* Z,
+                             void* stream) {
+  if (!b) return SPARC_ERR_INVALID_ARG;
+  ARG(b, Hs && Ms && ns && lam && Z, "null argument");
+  const int n = (int)b->hs.size();
+  std::vector<int> nsz(n);
+  for (int i = 0; i < n; ++i) {
+    sparc_context* c = b->hs[i];
+    ARG(b, ns[i] >= 1 && ns[i] <= c->ns_max, "ns[i] must be in [1, member i's ns_max]");
+    ARG(b, is_device_ptr(Hs[i]) && is_device_ptr(Ms[i]) && is_device_ptr(lam[i]) &&
+               is_device_ptr(Z[i]),
+        "Hs, Ms, lam and Z must be device pointers");
+    nsz[i] = ns[i];
+  }
+  CK(b, cudaSetDevice(b->device));
+  set_wait_cycles(b->hs[0]->wait_cycles);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int> order, large;
+  std::vector<sparc_batch_context::EigGroup> groups;
+  eig_plan(nsz, &order, &groups, &large);
+  std::vector<EigBatchItem> tab;
+  for (int i : order)
+    tab.push_back(eig_batch_item(b->hs[i]->eig, Hs[i], Ms[i], ns[i], lam[i], Z[i]));
+  for (int i = 0; i < n; ++i)
+    CK(b, cudaMemsetAsync(b->hs[i]->eig.status, 0, 5 * sizeof(int), st));
+  if (!tab.empty())
+    CK(b, cudaMemcpyAsync(b->d_eig_call, tab.data(), tab.size() * sizeof(EigBatchItem),
+                          cudaMemcpyHostToDevice, st));
+  for (const auto& g : groups)
+    CK(b, eig_batch(static_cast<const EigBatchItem*>(b->d_eig_call) + g.first, g.count,
+                    g.cluster, g.nmax, st));
+  for (int i : large) {
+    const EigGemm eg = eig_gemm_of(b->hs[i]);
+    CK(b, gen_eig(b->hs[i]->eig, Hs[i], Ms[i], ns[i], lam[i], Z[i], st, &eg));
+  }
+  CK(b, cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i) {
+    sparc_context* c = b->hs[i];
+    int rc = read_status(c, st);
+    if (rc) {
+      b->err = "system " + std::to_string(i) + ": " + c->err;
+      return rc;
+    }
+  }
   return SPARC_OK;
 }
 

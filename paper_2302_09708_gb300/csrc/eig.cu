@@ -370,14 +370,23 @@ __global__ void __launch_bounds__(256)
     acc = 0.0;
     for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += vsh[i] * p[i];
     const double K = block_sum_d(acc, sh);
+    // element r + m c of the trailing block, stepped by the grid size with
+    // (r, c) carried instead of divided out
     const int m = n - k - 1;
-    const int64_t mm = (int64_t)m * m;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < mm;
-         t += (int64_t)gridDim.x * blockDim.x) {
-      const int i = k + 1 + (int)(t % m), j = k + 1 + (int)(t / m);
+    const int nthr = gridDim.x * blockDim.x;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sq = nthr / m, sr = nthr % m;
+    for (int r = gtid % m, c = gtid / m; c < m;) {
+      const int i = k + 1 + r, j = k + 1 + c;
       const double vi = vsh[i], vj = vsh[j];
       const double qi = p[i] - K * vi, qj = p[j] - K * vj;
       A[i + (int64_t)j * n] -= 2.0 * (vi * qj + qi * vj);
+      r += sr;
+      c += sq;
+      if (r >= m) {
+        r -= m;
+        ++c;
+      }
     }
     if (!grid_barrier(gb, nb, &abort_sh)) return;
   }
@@ -1065,5 +1074,513 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
 }
 #undef EL
 #undef EK
+
+// ---------------------------------------------------------------------------
+// Batched eigensolver.  One thread-block cluster ("team") per problem runs the
+// steps of gen_eig above, in the same order, with cluster barriers (release /
+// acquire at cluster scope, so each step sees the global-memory writes of the
+// previous one) in place of kernel boundaries and grid barriers.  On one SM or
+// a few, the FP64 pipe bounds this kernel, so two steps take a form with fewer
+// FP64 instructions than gen_eig's: the triangular solves go 32 unknowns at a
+// time (a reciprocal of each pivot instead of a division per row, no
+// reduction across the warp per row), and the eigenvalues of T come from plain
+// bisection (one Sturm count per bit) instead of multisection.  Work inside a
+// step is spread over the team's threads (element loops), warps (one
+// right-hand side or matrix column per warp) or single threads (one
+// eigenvalue each).  Buffers: A (Ms copy, then the reduced matrix, then the
+// reflectors, reflector k in column k below the diagonal), L / V (Cholesky
+// factor column- and row-major), W (L^-1 Hs, later the eigenvectors of T), lu
+// (4 n^2: scratch, then the inverse-iteration factors, then the
+// re-orthonormalisation's factor, Gram matrix and Q).  Every control decision
+// (loop bounds, a non-positive pivot) depends only on values that every
+// thread of the team reads after the same barrier, so all CTAs of a cluster
+// pass the same barriers and leave together.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kEbThreads = 512;
+constexpr int kEbWarps = kEbThreads / 32;
+
+struct Team {
+  int tid, nthr, warp, nwarps, lane;
+  bool lead;  // thread 0 of the team's first CTA
+};
+
+__device__ __forceinline__ void team_sync() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Cholesky S = L L^T of the symmetric n x n S (column-major; the lower triangle
+// is read and updated in place, right-looking, one column per step).  Writes
+// the factor column-major into Lc and row-major into Lr (lower entries only).
+// Returns false, on every thread alike, at a non-positive or non-finite pivot.
+__device__ bool team_cholesky(double* S, double* Lc, double* Lr, int n, const Team& t) {
+  for (int k = 0; k < n; ++k) {
+    const double akk = S[k + (int64_t)k * n];
+    if (!(akk > 0.0) || !isfinite(akk)) return false;
+    const double s = sqrt(akk);
+    const double linv = 1.0 / s;
+    for (int i = k + t.tid; i < n; i += t.nthr) {
+      const double l = i == k ? s : S[i + (int64_t)k * n] * linv;
+      Lc[i + (int64_t)k * n] = l;
+      Lr[(int64_t)i * n + k] = l;
+    }
+    for (int j = k + 1 + t.warp; j < n; j += t.nwarps) {
+      const double lj = S[j + (int64_t)k * n] * linv;
+      for (int i = j + t.lane; i < n; i += 32)
+        S[i + (int64_t)j * n] -= (S[i + (int64_t)k * n] * linv) * lj;
+    }
+    team_sync();
+  }
+  return true;
+}
+
+// One warp solves L x = b (FWD) or L^T x = b (!FWD) for lower-triangular L,
+// with b and x in the warp's shared memory, 32 unknowns at a time: lane l
+// owns unknown i = i0 + l.  The sum over the unknowns of earlier blocks is
+// each lane's own dot product, read coalesced from F (FWD: L column-major,
+// F[i + k n] = L(i, k); !FWD: L row-major, F[k n + i] = L(k, i)); inside the
+// 32 x 32 diagonal block the unknowns follow one another, each broadcast by a
+// shuffle and multiplied by the reciprocal of its pivot.
+template <bool FWD>
+__device__ void warp_trsv(const double* __restrict__ F, int n, const double* b, double* x,
+                          int lane) {
+  const int nblk = (n + 31) / 32;
+  for (int bq = 0; bq < nblk; ++bq) {
+    const int i0 = FWD ? bq * 32 : (nblk - 1 - bq) * 32;
+    const int nb = min(32, n - i0);
+    const int i = i0 + lane;
+    const bool act = lane < nb;
+    double s0 = 0.0, s1 = 0.0;
+    if (act) {
+      if (FWD) {
+        int k = 0;
+        for (; k + 1 < i0; k += 2) {
+          s0 += F[i + (int64_t)k * n] * x[k];
+          s1 += F[i + (int64_t)(k + 1) * n] * x[k + 1];
+        }
+        if (k < i0) s0 += F[i + (int64_t)k * n] * x[k];
+      } else {
+        int k = i0 + 32;
+        for (; k + 1 < n; k += 2) {
+          s0 += F[(int64_t)k * n + i] * x[k];
+          s1 += F[(int64_t)(k + 1) * n + i] * x[k + 1];
+        }
+        if (k < n) s0 += F[(int64_t)k * n + i] * x[k];
+      }
+    }
+    double r = act ? b[i] - (s0 + s1) : 0.0;
+    const double dinv = act ? 1.0 / F[i + (int64_t)i * n] : 0.0;
+    for (int q = 0; q < nb; ++q) {
+      const int qq = FWD ? q : nb - 1 - q;
+      const double xq = __shfl_sync(0xffffffffu, r * dinv, qq);
+      if (lane == qq) x[i] = xq;
+      if (act && (FWD ? lane > qq : lane < qq))
+        r -= (FWD ? F[i + (int64_t)(i0 + qq) * n] : F[(int64_t)(i0 + qq) * n + i]) * xq;
+    }
+    __syncwarp();
+  }
+}
+
+// Columns c = warp, warp + nwarps, ...: x = L^-1 b with b[i] = B[c bc + i bs],
+// stored to X[c xc + i xs]; Lc: L column-major.
+__device__ void team_forward(const double* Lc, const double* B, int64_t bc, int64_t bs, double* X,
+                             int64_t xc, int64_t xs, int n, double* wb, double* wx,
+                             const Team& t) {
+  for (int c = t.warp; c < n; c += t.nwarps) {
+    for (int i = t.lane; i < n; i += 32) wb[i] = B[c * bc + i * bs];
+    __syncwarp();
+    warp_trsv<true>(Lc, n, wb, wx, t.lane);
+    for (int i = t.lane; i < n; i += 32) X[c * xc + i * xs] = wx[i];
+    __syncwarp();
+  }
+}
+
+// block-wide sum over the CTA's threads (every thread gets the result)
+__device__ double cta_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+__global__ void __launch_bounds__(kEbThreads, 1)
+    k_eig_batch(const EigBatchItem* __restrict__ items, int count) {
+  extern __shared__ double ebsh[];
+  __shared__ double red[32];
+  unsigned rank, csize;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
+  const int item = (int)(blockIdx.x / csize);
+  if (item >= count) return;  // whole clusters only
+  const EigBatchItem P = items[item];
+  const int n = P.n;
+  const int64_t nn = (int64_t)n * n;
+  Team t;
+  t.tid = (int)(rank * blockDim.x + threadIdx.x);
+  t.nthr = (int)(csize * blockDim.x);
+  t.lane = threadIdx.x & 31;
+  t.warp = t.tid >> 5;
+  t.nwarps = t.nthr >> 5;
+  t.lead = t.tid == 0;
+  double* vsh = ebsh;      // reflector (n)
+  double* qsh = ebsh + n;  // 2 q of the rank-2 update (n)
+  double* wb = ebsh + 2 * (int64_t)n + (int64_t)(threadIdx.x >> 5) * 2 * n;  // per warp
+  double* wx = wb + n;
+  double *A = P.A, *L = P.L, *V = P.V, *W = P.W, *lu = P.lu;
+
+  // 1. Ms = L L^T (A <- Ms; factor into L column-major and V row-major)
+  for (int64_t q = t.tid; q < nn; q += t.nthr) A[q] = P.Ms[q];
+  team_sync();
+  if (!team_cholesky(A, L, V, n, t)) {
+    if (t.lead) atomicCAS(P.status, 0, ST_NOT_SPD);
+    return;
+  }
+  // 2. W = L^-1 Hs; lu = L^-1 W^T; A = sym(lu)
+  team_forward(L, P.Hs, n, 1, W, n, 1, n, wb, wx, t);
+  team_sync();
+  team_forward(L, W, 1, n, lu, n, 1, n, wb, wx, t);
+  team_sync();
+  for (int j = t.warp; j < n; j += t.nwarps)
+    for (int i = t.lane; i < n; i += 32)
+      A[i + (int64_t)j * n] = 0.5 * (lu[i + (int64_t)j * n] + lu[j + (int64_t)i * n]);
+  team_sync();
+  // 3. Householder reduction (steps as in k_house_persistent); reflector k is
+  //    kept in column k of A below the diagonal (no later step reads it)
+  double* p = P.tau;
+  for (int k = 0; k + 2 < n; ++k) {
+    const double* col = A + (int64_t)k * n;
+    double acc = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += col[i] * col[i];
+    const double xn = sqrt(cta_sum(acc, red));
+    const double x0 = col[k + 1];
+    const double alpha = x0 >= 0.0 ? -xn : xn;
+    double vn2 = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const double v = col[i] - (i == k + 1 ? alpha : 0.0);
+      vn2 += v * v;
+    }
+    const double vn = sqrt(cta_sum(vn2, red));
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
+      vsh[i] = (xn > 0.0 && vn > 0.0) ? (col[i] - (i == k + 1 ? alpha : 0.0)) / vn : 0.0;
+    __syncthreads();
+    if (t.lead) {
+      P.d[k] = col[k];
+      P.e[k] = xn > 0.0 ? alpha : 0.0;
+    }
+    for (int i = k + 1 + t.warp; i < n; i += t.nwarps) {  // p = A v, warp per row
+      const double* row = A + (int64_t)i * n;
+      double s2 = 0.0;
+      for (int j = k + 1 + t.lane; j < n; j += 32) s2 += row[j] * vsh[j];
+      s2 = warp_sum_d(s2);
+      if (t.lane == 0) p[i] = s2;
+    }
+    team_sync();
+    acc = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += vsh[i] * p[i];
+    const double K = cta_sum(acc, red);
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) qsh[i] = 2.0 * (p[i] - K * vsh[i]);
+    __syncthreads();
+    // element q = r + m c of the trailing block (row k+1+r, column k+1+c);
+    // each thread steps q by the team size, carrying (r, c) without dividing
+    const int m = n - k - 1;
+    const int sq = t.nthr / m, sr = t.nthr % m;
+    for (int r = t.tid % m, c = t.tid / m; c < m;) {
+      const int i = k + 1 + r, j = k + 1 + c;
+      A[i + (int64_t)j * n] -= vsh[i] * qsh[j] + qsh[i] * vsh[j];
+      r += sr;
+      c += sq;
+      if (r >= m) {
+        r -= m;
+        ++c;
+      }
+    }
+    if (rank == 0)
+      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)k * n] = vsh[i];
+    team_sync();
+  }
+  if (t.lead) {
+    for (int k = n >= 2 ? n - 2 : 0; k < n; ++k) P.d[k] = A[k + (int64_t)k * n];
+    if (n >= 2) P.e[n - 2] = A[(n - 1) + (int64_t)(n - 2) * n];
+  }
+  team_sync();
+  // 4. eigenvalues of T: Gershgorin interval (first CTA), then multisection
+  double* e2 = P.tau + n;
+  if (rank == 0) {
+    double lo = 1e300, hi = -1e300, emax = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double r = (i > 0 ? fabs(P.e[i - 1]) : 0.0) + (i + 1 < n ? fabs(P.e[i]) : 0.0);
+      lo = fmin(lo, P.d[i] - r);
+      hi = fmax(hi, P.d[i] + r);
+      if (i + 1 < n) {
+        e2[i] = P.e[i] * P.e[i];
+        emax = fmax(emax, e2[i]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    }
+    __shared__ double gsh[3][32];
+    if (t.lane == 0) {
+      gsh[0][threadIdx.x >> 5] = lo;
+      gsh[1][threadIdx.x >> 5] = hi;
+      gsh[2][threadIdx.x >> 5] = emax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        lo = fmin(lo, gsh[0][w]);
+        hi = fmax(hi, gsh[1][w]);
+        emax = fmax(emax, gsh[2][w]);
+      }
+      const double tnorm = fmax(fabs(lo), fabs(hi));
+      const double pad = 2.2e-16 * tnorm * n + 1e-300;
+      P.scal[0] = lo - pad;
+      P.scal[1] = hi + pad;
+      P.scal[2] = fmax(2.2250738585072014e-308 * fmax(1.0, emax), 1e-300);
+      P.scal[3] = tnorm;
+    }
+  }
+  team_sync();
+  {
+    // one thread per eigenvalue (plain bisection: the fewest Sturm counts per
+    // bit, which is what counts here, where the FP64 pipe is the limit),
+    // eigenvalues dealt round-robin over the cluster's CTAs; stops at the
+    // multisection's relative width, or when the midpoint no longer moves
+    const double pivmin = P.scal[2];
+    for (int j = (int)(rank + csize * threadIdx.x); j < n; j += t.nthr) {
+      double lo = P.scal[0], hi = P.scal[1];
+      for (int it = 0; it < 192; ++it) {
+        if (hi - lo <= 2.0 * 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        if (sturm(P.d, e2, n, mid, pivmin) > j)
+          hi = mid;
+        else
+          lo = mid;
+      }
+      P.lam[j] = 0.5 * (lo + hi);
+    }
+  }
+  team_sync();
+  if (t.lead) {  // clusters of nearly equal eigenvalues (as k_clusters)
+    const double tol = 1e-9 * fmax(P.scal[3], 1e-300);
+    int start = 0;
+    for (int j = 1; j <= n; ++j) {
+      if (j == n || P.lam[j] - P.lam[j - 1] > tol) {
+        for (int q = start; q < j; ++q) {
+          P.clus[q] = start;
+          P.clus[n + q] = j - start;
+        }
+        start = j;
+      }
+    }
+  }
+  team_sync();
+  // 5. eigenvectors of T into W by inverse iteration: singletons thread per
+  //    eigenvalue, clusters warp per cluster (members in order, Gram-Schmidt
+  //    twice against the earlier ones), then Cholesky-QR
+  {
+    const double pivmin = fmax(2.2e-16 * P.scal[3], 1e-300);
+    for (int j = (int)(rank + csize * threadIdx.x); j < n; j += t.nthr) {
+      if (P.clus[n + j] != 1) continue;
+      TriLU F{lu, P.piv, n, n, j};
+      tri_factor(F, P.d, P.e, P.lam[j], pivmin);
+      double* x = W + (int64_t)j * n;
+      for (int i = 0; i < n; ++i) x[i] = start_value(0x5EEDull + j, i);
+      for (int it = 0; it < kInvIters; ++it) {
+        scale_maxabs(x, n);
+        tri_solve(F, x);
+      }
+      double s = 0.0;
+      for (int i = 0; i < n; ++i) s += x[i] * x[i];
+      const double inv = 1.0 / sqrt(s);
+      for (int i = 0; i < n; ++i) x[i] *= inv;
+    }
+    const double sep = 10.0 * 2.2e-16 * fmax(P.scal[3], 1e-300);
+    for (int j0 = t.warp; j0 < n; j0 += t.nwarps) {
+      if (P.clus[j0] != j0 || P.clus[n + j0] < 2) continue;
+      const int size = P.clus[n + j0];
+      double shift_prev = 0.0;
+      for (int m = 0; m < size; ++m) {
+        const int j = j0 + m;
+        double sigma = P.lam[j];
+        if (m > 0 && sigma - shift_prev < sep) sigma = shift_prev + sep;
+        shift_prev = sigma;
+        TriLU F{lu, P.piv, n, n, j};
+        if (t.lane == 0) tri_factor(F, P.d, P.e, sigma, pivmin);
+        double* x = W + (int64_t)j * n;
+        for (int i = t.lane; i < n; i += 32) x[i] = start_value(0x5EEDull + j, i);
+        __syncwarp();
+        for (int it = 0; it < kInvIters; ++it) {
+          if (t.lane == 0) {
+            scale_maxabs(x, n);
+            tri_solve(F, x);
+          }
+          __syncwarp();
+          for (int pass = 0; pass < 2; ++pass) {
+            for (int q = 0; q < m; ++q) {
+              const double* y = W + (int64_t)(j0 + q) * n;
+              double acc = 0.0;
+              for (int i = t.lane; i < n; i += 32) acc += y[i] * x[i];
+              const double c = warp_sum_d(acc);
+              for (int i = t.lane; i < n; i += 32) x[i] -= c * y[i];
+              __syncwarp();
+            }
+          }
+          double acc = 0.0;
+          for (int i = t.lane; i < n; i += 32) acc += x[i] * x[i];
+          const double nrm = sqrt(warp_sum_d(acc));
+          const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+          for (int i = t.lane; i < n; i += 32) x[i] *= inv;
+          __syncwarp();
+        }
+      }
+    }
+  }
+  team_sync();
+  //    G = W^T W (lower triangle, into lu[n^2, 2n^2)), G = R R^T, Q = W R^-T
+  double* G = lu + nn;
+  for (int j = t.warp; j < n; j += t.nwarps) {
+    const double* wj = W + (int64_t)j * n;
+    for (int i = t.lane; i < n; i += 32) wb[i] = wj[i];
+    __syncwarp();
+    for (int i = j; i < n; ++i) {
+      const double* wi = W + (int64_t)i * n;
+      double acc = 0.0;
+      for (int r = t.lane; r < n; r += 32) acc += wi[r] * wb[r];
+      acc = warp_sum_d(acc);
+      if (t.lane == 0) G[i + (int64_t)j * n] = acc;
+    }
+    __syncwarp();
+  }
+  team_sync();
+  if (!team_cholesky(G, lu, lu + 2 * nn, n, t)) {
+    if (t.lead) atomicCAS(P.status + 1, 0, ST_NUMERIC);
+    return;
+  }
+  //    row c of Q = R^-1 (row c of W), into lu[3 n^2, 4 n^2)
+  double* Q = lu + 3 * nn;
+  team_forward(lu, W, 1, n, Q, 1, n, n, wb, wx, t);
+  team_sync();
+  // 6.-7. per column c (warp): apply the reflectors to column c of Q, solve
+  //    L^T z = (that column), make its largest-magnitude entry positive
+  for (int c = t.warp; c < n; c += t.nwarps) {
+    for (int i = t.lane; i < n; i += 32) wb[i] = Q[i + (int64_t)c * n];
+    __syncwarp();
+    for (int k = n - 3; k >= 0; --k) {
+      const double* v = A + (int64_t)k * n;
+      double s = 0.0;
+      for (int i = k + 1 + t.lane; i < n; i += 32) s += v[i] * wb[i];
+      s = 2.0 * warp_sum_d(s);
+      for (int i = k + 1 + t.lane; i < n; i += 32) wb[i] -= s * v[i];
+      __syncwarp();
+    }
+    warp_trsv<false>(V, n, wb, wx, t.lane);
+    double best = -1.0;
+    int bi = 0;
+    bool finite = true;
+    for (int i = t.lane; i < n; i += 32) {
+      const double a = fabs(wx[i]);
+      finite = finite && isfinite(wx[i]);
+      if (a > best) {
+        best = a;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    const double sg = wx[bi] < 0.0 ? -1.0 : 1.0;
+    for (int i = t.lane; i < n; i += 32) P.Z[i + (int64_t)c * n] = sg * wx[i];
+    if (!__all_sync(0xffffffffu, finite) && t.lane == 0) atomicCAS(P.status, 0, ST_NUMERIC);
+    __syncwarp();
+  }
+  for (int j = t.tid; j < n; j += t.nthr)
+    if (!isfinite(P.lam[j])) atomicCAS(P.status, 0, ST_NUMERIC);
+}
+
+size_t eig_batch_smem(int nmax) { return (size_t)(2 + 2 * kEbWarps) * nmax * sizeof(double); }
+
+}  // namespace
+
+EigBatchItem eig_batch_item(const EigWork& w, const double* Hs, const double* Ms, int n,
+                            double* lam, double* Z) {
+  EigBatchItem it{};
+  it.Hs = Hs; it.Ms = Ms; it.lam = lam; it.Z = Z;
+  it.L = w.L; it.A = w.A; it.W = w.W; it.V = w.V; it.lu = w.lu;
+  it.d = w.d; it.e = w.e; it.tau = w.tau; it.scal = w.scal;
+  it.status = w.status; it.clus = w.clus; it.piv = w.piv;
+  it.n = n;
+  return it;
+}
+
+int eig_batch_cluster(int n) {
+  int c = n <= 128 ? 1 : n <= 176 ? 2 : n <= 240 ? 4 : 8;
+  // largest cluster the device co-schedules with this kernel's shared memory
+  static int max_ok[9] = {0};
+  static bool probed = false;
+  if (!probed) {
+    probed = true;
+    const size_t smem = eig_batch_smem(kEigBatchMax);
+    cudaFuncSetAttribute(k_eig_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int cs = 1; cs <= 8; cs *= 2) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(kEbThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nc = 0;
+      max_ok[cs] = cudaOccupancyMaxActiveClusters(&nc, k_eig_batch, &cfg) == cudaSuccess && nc > 0;
+      cudaGetLastError();
+    }
+  }
+  while (c > 1 && !max_ok[c]) c /= 2;
+  return c;
+}
+
+cudaError_t eig_batch(const EigBatchItem* items, int count, int cluster, int nmax,
+                      cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = eig_batch_smem(std::max(nmax, 1));
+  cudaError_t e =
+      cudaFuncSetAttribute(k_eig_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(count * cluster));
+  cfg.blockDim = dim3(kEbThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  note_launch();
+  return cudaLaunchKernelEx(&cfg, k_eig_batch, items, count);
+}
 
 }  // namespace sparc

@@ -292,6 +292,40 @@ struct EigGemm {
 cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, double* lam, double* Z,
                     cudaStream_t st, const EigGemm* g = nullptr);
 
+// Batched form of gen_eig: one launch solves many independent problems, each
+// by one thread-block cluster (eig_batch_cluster(n) CTAs) that runs all steps
+// of gen_eig with cluster barriers between them.  Every problem of one launch
+// uses the same cluster size; n <= kEigBatchMax.  The table lives in device
+// memory; each entry's work buffers come from an EigWork of nmax >= n.
+constexpr int kEigBatchMax = 512;
+struct EigBatchItem {
+  const double* Hs;
+  const double* Ms;
+  double* lam;
+  double* Z;
+  double* L;
+  double* A;
+  double* W;
+  double* V;
+  double* lu;
+  double* d;
+  double* e;
+  double* tau;
+  double* scal;
+  int* status;
+  int* clus;
+  int* piv;
+  int n;
+  int pad;
+};
+EigBatchItem eig_batch_item(const EigWork& w, const double* Hs, const double* Ms, int n,
+                            double* lam, double* Z);
+// CTAs per problem of size n, reduced if the device cannot co-schedule them
+int eig_batch_cluster(int n);
+// items: device table of `count` entries, largest n first; nmax = max n
+cudaError_t eig_batch(const EigBatchItem* items, int count, int cluster, int nmax,
+                      cudaStream_t st);
+
 // Complex step at a Bloch wavevector (kpoint.cu) ---------------------------
 struct KpointState;
 // builds the phased projector tables and complex workspaces of a k-point handle
@@ -311,44 +345,6 @@ int kpoint_rotate(sparc_context* c, const void* Xt, void* Xout, const double* Z,
                   cudaStream_t st);
 int kpoint_step(sparc_context* c, void* X, int ns, int64_t ldx, int m, double a, double b,
                 double a0, double* eig, int eig_on_host, cudaStream_t st);
-
-// Batched form (batch.cu) -------------------------------------------------
-struct BatchSysHost {
-  int nx, ny, nz, bc[3];
-  int ns, tiles_x, tiles_y, nzc, bz;
-  int natoms, kp;
-  int64_t cta_begin, nl_cta_begin;
-  double diag, off[kRadius + 1], h3;
-  const void* veff;
-  const int* pull_ptr;
-  const int* pull_k;
-  const void* pull_chi;
-  const int64_t* supp_ptr;
-  const int* supp_idx;
-  const int* nproj;
-  const int64_t* chi_ptr;
-  const void* chi;
-  const int* proj_ptr;
-  const double* gamma;
-  void* D;
-};
-struct BatchItemHost {
-  const void* x;
-  void* y;
-  const void* prev;
-  int64_t ldx, ldy, ldp;
-  double shift, s_h, s_p;
-  int active;
-};
-template <typename T>
-void batch_layout(std::vector<BatchSysHost>& hs, int64_t* cta_total, int64_t* nl_total);
-size_t batch_sys_bytes();
-size_t batch_item_bytes();
-void batch_pack_sys(const BatchSysHost& h, void* out);
-void batch_pack_item(const BatchItemHost& h, void* out);
-template <typename T>
-cudaError_t batch_degree(const void* sys, const void* items, int nsys, int64_t cta_total,
-                         int64_t nl_total, cudaStream_t st);
 
 }  // namespace sparc
 

@@ -79,7 +79,7 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_hpsi",
            "sparc_occupations", "sparc_density", "sparc_nonlocal_forces",
            "sparc_batch_create", "sparc_batch_destroy", "sparc_batch_last_error",
            "sparc_batch_chefsi_step", "sparc_batch_get_info", "sparc_get_tuning",
-           "sparc_create_kpoint"]
+           "sparc_create_kpoint", "sparc_batch_subspace_eig"]
 
 _lib = None
 
@@ -126,6 +126,7 @@ def load(build: bool = True):
     L.sparc_batch_last_error.restype = ctypes.c_char_p
     L.sparc_batch_chefsi_step.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, vp]
     L.sparc_batch_get_info.argtypes = [vp, ctypes.POINTER(i64)]
+    L.sparc_batch_subspace_eig.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("sparc_last_error", "sparc_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -458,6 +459,24 @@ class Batch:
         if rc != SPARC_OK:
             raise SparcError(rc, L.sparc_batch_last_error(self.b).decode())
         return eigs
+
+    def subspace_eig(self, Hs, Ms, stream=None):
+        """sparc_batch_subspace_eig on lists of device (n_i, n_i) FP64 tensors;
+        returns (lams, Zs), each Z an ordinary (row, col) matrix."""
+        import torch
+        L = load()
+        n = len(Hs)
+        sizes = [int(H.shape[0]) for H in Hs]
+        Hc = [H.t().contiguous() for H in Hs]  # column-major storage of H
+        Mc = [M.t().contiguous() for M in Ms]
+        lam = [torch.empty(k, dtype=torch.float64, device=H.device) for k, H in zip(sizes, Hs)]
+        Zc = [torch.empty((k, k), dtype=torch.float64, device=H.device) for k, H in zip(sizes, Hs)]
+        arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])  # noqa: E731
+        rc = L.sparc_batch_subspace_eig(self.b, arr(Hc), arr(Mc), (ctypes.c_int * n)(*sizes),
+                                        arr(lam), arr(Zc), _stream(stream))
+        if rc != SPARC_OK:
+            raise SparcError(rc, L.sparc_batch_last_error(self.b).decode())
+        return lam, [z.t() for z in Zc]
 
     def launches(self):
         v = ctypes.c_int64()
