@@ -173,7 +173,7 @@ const NlTiles<float>& tiles_of<float>(const sparc_context* c) { return c->tiles3
 template <typename T>
 bool tiles_usable(const sparc_context* c) {
   const bool mixed = c->precision == SPARC_PREC_MIXED;
-  return c->tiles_ok && (std::is_same<T, float>::value == mixed);
+  return std::is_same<T, float>::value ? (mixed && c->tiles32_ok) : c->tiles64_ok;
 }
 
 // Thread shape of the ring stencil for ns orbitals of type T: the fixed one,
@@ -269,18 +269,24 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
   // orbitals per projector); the fused stencils read it orbital-major
   const bool has_nl = nl.natoms > 0 && nl.kp > 0;
   const bool df = std::is_same<T, double>::value && c->ring_enabled && c->df_stencil;
-  const bool split = !df && (!has_nl || tiles_usable<T>(c));
-  const bool ring = split && c->ring_enabled &&
+  const bool split = !has_nl || tiles_usable<T>(c);
+  const bool ring = split && !df && c->ring_enabled &&
                     ring_applicable<T>(c->grid, x, ldx, y, ldy, prev, ldp, veff);
-  // a D left by the previous degree's tiled pass is projector-major: any other
-  // path gathers its own
-  if (!d_ready || !split) CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st, split));
   if (df) {
+    // the double-FP32 ring reads D orbital-major; where it does not fit the
+    // grid, the split form follows (projector-major D) or, without tiles, the
+    // fused generic stencil
+    CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st, false));
     bool used = false;
     CK(c, apply_h_ring_df(c->grid, c->lap, c->veff_df, c->nl64, (const double*)D,
                           (const double*)x, ldx, (double*)y, ldy, (const double*)prev, ldp, ns,
                           shift, s_h, s_p, c->eig.status + 3, st, &used));
     if (used) return SPARC_OK;
+    if (split && has_nl) CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st, true));
+  } else if (!d_ready || !split) {
+    // a D left by the previous degree's tiled pass is projector-major: any
+    // other path gathers its own
+    CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st, split));
   }
   if (ring) {
     bool used = false;
@@ -325,10 +331,17 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
     // the ring kernel declined after all: the generic local stencil follows
   }
   if (split) {
-    Nonlocal<T> local = nl;
-    local.kp = 0;  // local part only; the tiled pass adds the nonlocal term
-    CK(c, apply_h<T>(c->grid, c->lap, veff, local, D, x, ldx, y, ldy, prev, ldp, ns, shift, s_h,
-                     s_p, st));
+    // local part only (slab stencil, or the tiled one on grids it does not
+    // fit); the tiled pass adds the nonlocal term
+    bool used = false;
+    CK(c, apply_h_local<T>(c->grid, c->lap, veff, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
+                           st, &used));
+    if (!used) {
+      Nonlocal<T> local = nl;
+      local.kp = 0;
+      CK(c, apply_h<T>(c->grid, c->lap, veff, local, D, x, ldx, y, ldy, prev, ldp, ns, shift, s_h,
+                       s_p, st));
+    }
     if (has_nl) {
       const NlTiles<T>& t = tiles_of<T>(c);
       T* part = want_next ? (T*)c->part : nullptr;
@@ -827,8 +840,8 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
       n32.grp_k = dgk;
       n32.grp_chi = dgc;
     }
-    // support-point tiles of the working precision (nonlocal pass of the
-    // ring stencil path)
+    // support-point tiles of the working precision (nonlocal pass of the split
+    // form); mixed handles also get FP64 tiles, for their FP64 Yt = H Xt
     NlTilesHost th;
     nl_tiles_build(nd, pull_ptr.data(), pull_k.data(), pull_chi.data(), kp, th);
     const bool mixed = c->precision == SPARC_PREC_MIXED;
@@ -861,14 +874,22 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
       t.kpair_ptr = kpp; t.kpair = kpr;
       int optin = 0;
       CK(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-      c->tiles_ok = nl_apply_smem(t) <= (size_t)optin;
-      if (c->tiles_ok)
-        CK(c, cudaMalloc(&c->part, (size_t)std::max(t.npairs, 1) * c->ns_max * sizeof(TT)));
+      const bool ok = nl_apply_smem(t) <= (size_t)optin;
+      (sizeof(TT) == 4 ? c->tiles32_ok : c->tiles64_ok) = ok;
+      // one partial-sum buffer serves both precisions (sized for the larger)
+      const size_t pb = (size_t)std::max(t.npairs, 1) * c->ns_max * sizeof(TT);
+      if (ok && pb > c->part_bytes) {
+        cudaFree(c->part);
+        c->part = nullptr;
+        c->part_bytes = 0;
+        CK(c, cudaMalloc(&c->part, pb));
+        c->part_bytes = pb;
+      }
       return SPARC_OK;
     };
     // (k-point handles keep complex tables of their own, kpoint.cu)
-    if (!kpoint && (rc = mixed ? put_tiles(c->tiles32, 0.0f) : put_tiles(c->tiles64, 0.0)))
-      return rc;
+    if (!kpoint && mixed && (rc = put_tiles(c->tiles32, 0.0f))) return rc;
+    if (!kpoint && (rc = put_tiles(c->tiles64, 0.0))) return rc;
   }
 
   // --- workspace ----------------------------------------------------------

@@ -98,6 +98,14 @@ template <typename T>
 cudaError_t apply_h(const Grid& g, const LapCoef& lc, const T* veff, const Nonlocal<T>& nl,
                     const T* D, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
                     int64_t ldp, int ns, double shift, double s_h, double s_p, cudaStream_t st);
+// Generic local part only (stencil.cu), any grid with nx >= kRadius:
+// y = s_h ((-1/2 Lap + Veff - shift) x) + s_p prev by y-slabs of whole rows;
+// the nonlocal term follows with nl_apply.  *used = false when the grid does
+// not fit it (nx < kRadius or too wide a row).
+template <typename T>
+cudaError_t apply_h_local(const Grid& g, const LapCoef& lc, const T* veff, const T* x,
+                          int64_t ldx, T* y, int64_t ldy, const T* prev, int64_t ldp, int ns,
+                          double shift, double s_h, double s_p, cudaStream_t st, bool* used);
 // TMA plane-ring form (stencil_tma.cu) of the local part only:
 // y = s_h ((-1/2 Lap + Veff - shift) x) + s_p prev; the nonlocal term follows
 // with nl_apply.  *used = false when the grid or the buffers do not fit it.
@@ -406,7 +414,8 @@ struct sparc_context {
   // handle's working precision, partial sums npairs x ns_max
   sparc::NlTiles<double> tiles64;
   sparc::NlTiles<float> tiles32;
-  bool tiles_ok = false;  // the tables of the working precision are built and fit
+  bool tiles32_ok = false, tiles64_ok = false;  // tiles built and within shared memory
+  size_t part_bytes = 0;                         // size of `part`
   void* part = nullptr;
   long long wait_cycles = 4000000000LL;  // bound of every device wait (SM clock cycles)
   // ring stencil thread shape: fixed (>= 0) or tuned per ns (-1)

@@ -305,6 +305,197 @@ template cudaError_t apply_h<float>(const Grid&, const LapCoef&, const float*,
                                     double, cudaStream_t);
 
 // ---------------------------------------------------------------------------
+// Generic local stencil by y-slabs of whole rows (any nx >= kRadius):
+// y = s_h ((-1/2 Lap + Veff - shift) x) + s_p prev, the nonlocal term added
+// afterwards by the tiled pass.  One CTA owns rows y0 .. y0 + by - 1 of one
+// orbital for a z range and marches along z; each thread owns PPT points of
+// the slab (consecutive threads, consecutive points, so every global access
+// is coalesced) and keeps their 13 values along z in a register queue.  Per
+// plane the CTA writes its own centre values into shared memory, loads the 2R
+// halo rows above and below, and repeats the first and last R columns of
+// every row beside it (periodic x; zero columns for Dirichlet x), so that the
+// x and y neighbours are read from shared memory without index wrapping.
+// Global reads per plane: the own points once, plus 2R / by halo rows.
+// Arithmetic in the same order as k_apply_h's local part.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kSlabThreads = 256;
+
+template <typename T>
+struct SlabArgs {
+  const T* x;
+  int64_t ldx;
+  T* y;
+  int64_t ldy;
+  const T* prev;
+  int64_t ldp;
+  const T* veff;
+  int nx, ny, nz, bcx, bcy, bcz;
+  int by, bz;
+  T dms;               // -1/2 * 3 w0/h^2 - shift
+  T off[kRadius + 1];  // -1/2 w_p/h^2
+  T s_h, s_p;
+};
+
+template <typename T, int PPT>
+__global__ void __launch_bounds__(kSlabThreads, sizeof(T) == 4 ? 4 : 2)
+    k_apply_h_slab(const SlabArgs<T> a) {
+  constexpr int R = kRadius;
+  extern __shared__ __align__(16) unsigned char slab_raw[];
+  T* const s = reinterpret_cast<T*>(slab_raw);
+  const int W = a.nx + 2 * R;  // shared row: R ghost columns, nx, R ghost columns
+  const int n = blockIdx.y;
+  const int y0 = blockIdx.x * a.by;
+  const int byl = min(a.by, a.ny - y0);
+  const int npts = byl * a.nx;
+  const int z0 = blockIdx.z * a.bz, z1 = min(z0 + a.bz, a.nz);
+  const int64_t nxy = (int64_t)a.nx * a.ny;
+  const T* __restrict__ xn = a.x + (int64_t)n * a.ldx;
+  const bool perx = a.bcx == SPARC_PERIODIC;
+  for (int e = threadIdx.x; e < (a.by + 2 * R) * W; e += blockDim.x) s[e] = T(0);
+
+  int pofs[PPT], sidx[PPT];
+  unsigned own = 0, dup_r = 0, dup_l = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int p = threadIdx.x + k * blockDim.x;
+    pofs[k] = 0;
+    sidx[k] = R * W + R;
+    if (p < npts) {
+      const int ry = p / a.nx, rx = p - ry * a.nx;
+      pofs[k] = (y0 + ry) * a.nx + rx;
+      sidx[k] = (ry + R) * W + rx + R;
+      own |= 1u << k;
+      if (perx && rx < R) dup_r |= 1u << k;           // also right of the row
+      if (perx && rx >= a.nx - R) dup_l |= 1u << k;   // also left of the row
+    }
+  }
+  T q[2 * R + 1][PPT];
+  auto load_q = [&](int zz, T(&d)[PPT]) {
+    const bool ok = map_coord(zz, a.nz, a.bcz);
+    const T* __restrict__ pl = xn + (int64_t)zz * nxy;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) d[k] = (ok && ((own >> k) & 1u)) ? __ldg(pl + pofs[k]) : T(0);
+  };
+#pragma unroll
+  for (int j = 0; j < 2 * R + 1; ++j) load_q(z0 - R + j, q[j]);
+
+  for (int z = z0; z < z1; ++z) {
+    // this plane's Veff and previous iterate, and the queue's next plane, are
+    // requested first, so that their latency overlaps the barrier below
+    const int64_t gz = (int64_t)z * nxy;
+    T vf[PPT], pv[PPT], nq[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const bool o = (own >> k) & 1u;
+      vf[k] = o ? __ldg(a.veff + gz + pofs[k]) : T(0);
+      pv[k] = (o && a.prev) ? a.prev[(int64_t)n * a.ldp + gz + pofs[k]] : T(0);
+    }
+    load_q(z + R + 1, nq);
+    // own centre values of plane z, with their ghost copies
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      if ((own >> k) & 1u) {
+        s[sidx[k]] = q[R][k];
+        if ((dup_r >> k) & 1u) s[sidx[k] + a.nx] = q[R][k];
+        if ((dup_l >> k) & 1u) s[sidx[k] - a.nx] = q[R][k];
+      }
+    }
+    // R halo rows above and below the slab (wrapped, or zero outside)
+    const T* __restrict__ pl = xn + (int64_t)z * nxy;
+    for (int e = threadIdx.x; e < 2 * R * a.nx; e += blockDim.x) {
+      const int hr = e / a.nx, hx = e - hr * a.nx;
+      const int srow = hr < R ? hr : byl + hr;
+      int gy = hr < R ? y0 - R + hr : y0 + byl + hr - R;
+      const bool ok = map_coord(gy, a.ny, a.bcy);
+      const T v = ok ? __ldg(pl + (int64_t)gy * a.nx + hx) : T(0);
+      const int si = srow * W + hx + R;
+      s[si] = v;
+      if (perx && hx < R) s[si + a.nx] = v;
+      if (perx && hx >= a.nx - R) s[si - a.nx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      if ((own >> k) & 1u) {
+        const T* c = s + sidx[k];
+        T acc = a.dms * q[R][k];
+#pragma unroll
+        for (int p = 1; p <= R; ++p) {
+          const T sum = (c[p] + c[-p]) + (c[p * W] + c[-p * W]) + (q[R + p][k] + q[R - p][k]);
+          acc += a.off[p] * sum;
+        }
+        acc += vf[k] * q[R][k];
+        const T out = a.prev ? a.s_h * acc + a.s_p * pv[k] : a.s_h * acc;
+        a.y[(int64_t)n * a.ldy + gz + pofs[k]] = out;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 2 * R; ++j)
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) q[j][k] = q[j + 1][k];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) q[2 * R][k] = nq[k];
+  }
+}
+
+template <typename T>
+struct SlabPpt;
+template <>
+struct SlabPpt<float> { static constexpr int v = 2; };
+template <>
+struct SlabPpt<double> { static constexpr int v = 2; };
+
+}  // namespace
+
+template <typename T>
+cudaError_t apply_h_local(const Grid& g, const LapCoef& lc, const T* veff, const T* x,
+                          int64_t ldx, T* y, int64_t ldy, const T* prev, int64_t ldp, int ns,
+                          double shift, double s_h, double s_p, cudaStream_t st, bool* used) {
+  constexpr int PPT = SlabPpt<T>::v;
+  constexpr int R = kRadius;
+  *used = false;
+  const int maxpts = PPT * kSlabThreads;
+  if (g.nx < R || g.nx > maxpts || ns < 1 || ns > 65535) return cudaSuccess;
+  int by = std::min(g.ny, maxpts / g.nx);
+  const int nslab = (g.ny + by - 1) / by;
+  by = (g.ny + nslab - 1) / nslab;
+  const int threads = ((by * g.nx + PPT - 1) / PPT + 31) / 32 * 32;
+  const size_t smem = (size_t)(by + 2 * R) * (g.nx + 2 * R) * sizeof(T);
+  if (smem > 48 * 1024) return cudaSuccess;
+  // z chunks: enough CTAs to cover the SMs several times, each chunk at least
+  // 2R planes deep (its queue reads 2R planes beyond it)
+  const int64_t xy_ctas = (int64_t)nslab * ns;
+  int nzc = (int)std::min<int64_t>((8 * sm_count() + xy_ctas - 1) / xy_ctas, 1 << 20);
+  nzc = std::max(1, std::min(nzc, std::max(1, g.nz / (2 * R))));
+  const int bz = (g.nz + nzc - 1) / nzc;
+  nzc = (g.nz + bz - 1) / bz;
+  SlabArgs<T> a;
+  a.x = x; a.ldx = ldx; a.y = y; a.ldy = ldy; a.prev = prev; a.ldp = ldp; a.veff = veff;
+  a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.bcx = g.bc[0]; a.bcy = g.bc[1]; a.bcz = g.bc[2];
+  a.by = by;
+  a.bz = bz;
+  a.dms = T(lc.diag - shift);
+  for (int p = 0; p <= R; ++p) a.off[p] = T(lc.off[p]);
+  a.s_h = T(s_h);
+  a.s_p = T(s_p);
+  note_launch();
+  k_apply_h_slab<T, PPT><<<dim3(nslab, ns, nzc), threads, smem, st>>>(a);
+  *used = true;
+  return cudaGetLastError();
+}
+
+template cudaError_t apply_h_local<float>(const Grid&, const LapCoef&, const float*, const float*,
+                                          int64_t, float*, int64_t, const float*, int64_t, int,
+                                          double, double, double, cudaStream_t, bool*);
+template cudaError_t apply_h_local<double>(const Grid&, const LapCoef&, const double*,
+                                           const double*, int64_t, double*, int64_t,
+                                           const double*, int64_t, int, double, double, double,
+                                           cudaStream_t, bool*);
+
+// ---------------------------------------------------------------------------
 // K2: nonlocal coefficients D[n][k] = gamma_k h^3 sum_t chi_k(t) x_n(t).  One
 // CTA per (atom, group of kNlOrb orbitals): threads stride over the atom's
 // support points, load the point's projector values once and apply them to
