@@ -30,11 +30,11 @@ sys.path.insert(0, ROOT)
 METRIC = "CheFSI step time & Hpsi GB/s; mixed-FP32/batched vs FP64 speedup at <=1e-6 Ha"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per orbital of one ring-stencil launch of a filter
-# degree on the 96^3 bulk grid (ncu captures at a smaller orbital count, scaled
-# by orbitals: every orbital is one independent pass over the grid), or None
-# where no capture of the current kernel exists
-RING64_DRAM_BYTES_PER_ORBITAL = None
-RING32_DRAM_BYTES_PER_ORBITAL = None
+# degree on the 96^3 bulk grid, from ncu captures at Ns = 64 scaled by orbitals
+# (every orbital is one independent pass over the grid): FP64 (1006.27 +
+# 417.48) MB / 64, FP32 (491.28 + 189.31) MB / 64 (profiles/k_apply_h_ring_*)
+RING64_DRAM_BYTES_PER_ORBITAL = (1006.271e6 + 417.475e6) / 64
+RING32_DRAM_BYTES_PER_ORBITAL = (491.276e6 + 189.307e6) / 64
 # FLOP per point and orbital of one H application (finite-difference stencil,
 # Veff and recurrence), the count the roofline of the FP64 stencil uses
 STENCIL_FLOP_PER_POINT = 84
@@ -48,7 +48,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="bulk96",
-                   help="bulk96 (96^3 bulk, Ns 1300), bulk24 (24^3, Ns 40) or slab64x64x160")
+                   help="bulk96 (96^3 bulk, Ns 1300), bulk24 (24^3, Ns 40), member36 (36^3, "
+                        "Ns 150: one system of the batched set's size range) or slab64x64x160")
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")

@@ -236,7 +236,13 @@ def electrons_for(ns: int) -> int:
 # ---------------------------------------------------------------------------
 WORKLOADS = {
     "bulk24": dict(name="24^3 periodic, h=0.5, 8 random atoms, Ns=40, m=20", seed_offset=1000,
-                   shape=(24, 24, 24), h=0.5, bc=(PERIODIC,) * 3, ns=40, degree=20, steps=1),
+                   shape=(24, 24, 24), h=0.5, bc=(PERIODIC,) * 3, ns=40, degree=20, steps=1,
+                   natoms=8),
+    # one system of the batched set's size range (N^3 with N not a multiple of
+    # 16, so the generic slab stencil runs): a single-handle profiling case
+    "member36": dict(name="36^3 periodic, h=0.5, 24 random atoms, Ns=150, m=20",
+                     seed_offset=1500, shape=(36, 36, 36), h=0.5, bc=(PERIODIC,) * 3, ns=150,
+                     degree=20, steps=1, natoms=24),
     "bulk96": dict(name="96^3 periodic bulk, h=0.4, 216 atoms (6^3 jittered SC), Ns=1300, m=20",
                    seed_offset=2000, shape=(96, 96, 96), h=0.4, bc=(PERIODIC,) * 3, ns=1300,
                    degree=20, steps=3),
@@ -260,14 +266,14 @@ def workload_seed(workload: str, index: int = 0) -> int:
 
 def make_workload_system(workload: str) -> System:
     """The synthetic system of a named workload: the 24^3 bulk with 8 random
-    atoms, the 96^3 bulk with 216 atoms on a jittered simple-cubic lattice, the
+    atoms, the 36^3 batch-member case with 24 random atoms, the 96^3 bulk with 216 atoms on a jittered simple-cubic lattice, the
     64 x 64 x 160 slab with 600 atoms in the central 60 % of z, or the reduced
     32 x 32 x 80 slab (75 atoms) built the same way."""
     c = WORKLOADS[workload]
     seed = workload_seed(workload)
     shape, h, bc = c["shape"], c["h"], c["bc"]
-    if workload == "bulk24":
-        return random_system(shape, h, bc, 8, seed, name=c["name"])
+    if workload in ("bulk24", "member36"):
+        return random_system(shape, h, bc, c["natoms"], seed, name=c["name"])
     rng = np.random.default_rng(seed + 500)
     if workload == "bulk96":
         pos = jittered_lattice((6, 6, 6), 6.4, (3.2, 3.2, 3.2), 0.5, rng)

@@ -27,6 +27,9 @@ def test_workload_parameters():
     assert (w["bulk24"]["ns"], w["bulk24"]["degree"]) == (40, 20)
     assert (w["bulk96"]["ns"], w["bulk96"]["degree"]) == (1300, 20)
     assert (w["slab64x64x160"]["ns"], w["slab64x64x160"]["degree"]) == (4800, 24)
+    m36 = synth.make_workload_system("member36")
+    assert m36.shape == (36, 36, 36) and m36.natoms == 24 and w["member36"]["ns"] == 150
+    assert 36 % 16 != 0  # a grid the TMA ring does not fit (nx not a multiple of 16)
     assert w["slab64x64x160"]["bc"] == (synth.PERIODIC, synth.PERIODIC, synth.DIRICHLET)
     seeds = {synth.workload_seed(k) for k in w}
     assert len(seeds) == len(w)
