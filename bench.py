@@ -32,7 +32,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per orbital of one ring-stencil launch of a filter
 # degree on the 96^3 bulk grid, from ncu captures at Ns = 64 scaled by orbitals
 # (every orbital is one independent pass over the grid): FP64 (1006.27 +
-# 417.48) MB / 64, FP32 (491.28 + 189.31) MB / 64 (profiles/k_apply_h_ring_*)
+# 417.48) MB / 64, FP32 (491.28 + 189.31) MB / 64 (the ring-kernel captures)
 RING64_DRAM_BYTES_PER_ORBITAL = (1006.271e6 + 417.475e6) / 64
 RING32_DRAM_BYTES_PER_ORBITAL = (491.276e6 + 189.307e6) / 64
 # FLOP per point and orbital of one H application (finite-difference stencil,

@@ -13,6 +13,12 @@
 // written as FP64 (one FP64 add per point).  Veff and the grouped projector
 // values come as pair tables made at handle creation; the CTA's nonlocal
 // coefficients D are converted when they are staged in shared memory.
+//
+// The pair operations are the published error-free transformations: the sum
+// of two numbers as TwoSum (Knuth, TAOCP vol. 2, Sec. 4.2.2) or FastTwoSum
+// when the order of magnitudes is known (Dekker 1971), the product as an exact
+// TwoProduct by one FMA for the rounding error, followed by the usual
+// renormalisation of hi + lo.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
