@@ -392,7 +392,7 @@ int sparc_batch_get_info(sparc_batch b, int64_t* launches_per_step);
  * positive.  1 <= ns[i] <= member i's ns_max.  Members with ns[i] <= 512 are
  * solved together, one launch per cluster size: one thread-block cluster per
  * member runs the steps of sparc_subspace_eig (Cholesky, reduction to
- * standard form, Householder tridiagonalisation, multisection, inverse
+ * standard form, Householder tridiagonalisation, bisection, inverse
  * iteration with Cholesky-QR, back-transformation) with cluster barriers
  * between them; larger members use sparc_subspace_eig's solver one after
  * another.  Uses each member's eigensolver workspace.  Synchronous.  Errors:

@@ -446,7 +446,9 @@ __device__ int sturm(const double* __restrict__ d, const double* __restrict__ e2
 // group evaluate Sturm counts at 8 interior points of [lo, hi] at once, and the
 // interval shrinks 9-fold per round (bisection's 2-fold per count, with 8 times
 // the parallelism for the latency-bound count recurrence).  Stops at the same
-// relative width as plain bisection: 2 eps max(|lo|, |hi|).
+// relative width as plain bisection: 2 eps max(|lo|, |hi|).  The whole-GPU
+// eigensolver takes this form: with Ns eigenvalues spread over all SMs the
+// count recurrence's latency, not the FP64 pipe, bounds the step.
 constexpr int kMsLanes = 8;
 __global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e2, int n,
                          const double* __restrict__ scal, double* __restrict__ lam) {
@@ -471,6 +473,27 @@ __global__ void k_bisect(const double* __restrict__ d, const double* __restrict_
     hi = nhi;
   }
   if (g < n && l == 0) lam[j] = 0.5 * (lo + hi);
+}
+
+// Eigenvalue j by plain bisection on the Sturm count: one count per halving,
+// the fewest counts per bit.  The batched eigensolver takes this form: there
+// one SM (or a few) holds all of a problem's eigenvalues, so the FP64 pipe,
+// not the recurrence's latency, bounds the step.  Stops at the same relative
+// width, when the midpoint no longer moves, or after 96 halvings.
+__device__ double bisect_eig(const double* __restrict__ d, const double* __restrict__ e2, int n,
+                             const double* __restrict__ scal, int j) {
+  double lo = scal[0], hi = scal[1];
+  const double pivmin = scal[2];
+  for (int it = 0; it < 96; ++it) {
+    if (hi - lo <= 2.0 * 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (sturm(d, e2, n, mid, pivmin) > j)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
 }
 
 // Cluster bookkeeping: clus[j] = first index of j's cluster, clus[n + j] = its size.
@@ -1310,7 +1333,7 @@ __global__ void __launch_bounds__(kEbThreads, 1)
     if (n >= 2) P.e[n - 2] = A[(n - 1) + (int64_t)(n - 2) * n];
   }
   team_sync();
-  // 4. eigenvalues of T: Gershgorin interval (first CTA), then multisection
+  // 4. eigenvalues of T: Gershgorin interval (first CTA), then bisection
   double* e2 = P.tau + n;
   if (rank == 0) {
     double lo = 1e300, hi = -1e300, emax = 0.0;
@@ -1352,24 +1375,9 @@ __global__ void __launch_bounds__(kEbThreads, 1)
   }
   team_sync();
   {
-    // one thread per eigenvalue (plain bisection: the fewest Sturm counts per
-    // bit, which is what counts here, where the FP64 pipe is the limit),
-    // eigenvalues dealt round-robin over the cluster's CTAs; stops at the
-    // multisection's relative width, or when the midpoint no longer moves
-    const double pivmin = P.scal[2];
-    for (int j = (int)(rank + csize * threadIdx.x); j < n; j += t.nthr) {
-      double lo = P.scal[0], hi = P.scal[1];
-      for (int it = 0; it < 192; ++it) {
-        if (hi - lo <= 2.0 * 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
-        const double mid = 0.5 * (lo + hi);
-        if (!(mid > lo && mid < hi)) break;
-        if (sturm(P.d, e2, n, mid, pivmin) > j)
-          hi = mid;
-        else
-          lo = mid;
-      }
-      P.lam[j] = 0.5 * (lo + hi);
-    }
+    // one thread per eigenvalue, dealt round-robin over the cluster's CTAs
+    for (int j = (int)(rank + csize * threadIdx.x); j < n; j += t.nthr)
+      P.lam[j] = bisect_eig(P.d, e2, n, P.scal, j);
   }
   team_sync();
   if (t.lead) {  // clusters of nearly equal eigenvalues (as k_clusters)
