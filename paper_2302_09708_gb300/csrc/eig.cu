@@ -815,18 +815,109 @@ __global__ void k_copy_scaled(const double* __restrict__ A, int64_t lda, int m, 
   }
 }
 
-// X = L^-1 for a lower-triangular n x n block (n <= 128): thread j forms
-// column j by forward substitution on e_j; the upper triangle is zeroed
-__global__ void k_trinv_leaf(const double* __restrict__ L, int64_t ldl, int n, double* X,
-                             int64_t ldx) {
-  const int j = threadIdx.x;
-  if (j >= n) return;
-  for (int i = 0; i < j; ++i) X[i + (int64_t)j * ldx] = 0.0;
-  for (int i = j; i < n; ++i) {
-    double a = i == j ? 1.0 : 0.0;
-    for (int k = j; k < i; ++k) a -= L[i + (int64_t)k * ldl] * X[k + (int64_t)j * ldx];
-    X[i + (int64_t)j * ldx] = a / L[i + (int64_t)i * ldl];
+// Leaf kernels of the tensor-core mode: one CTA of kLeafThreads works on an
+// n x n block (n <= 128) held whole in shared memory.
+constexpr int kLeafThreads = 512;
+constexpr int kLeafMax = 128;
+constexpr int kLeafCols = 16;  // columns of L staged per load
+
+// X = L^-1 for a lower-triangular n x n block: forward substitution on the
+// columns of I, right-looking (step k divides row k by L(k,k) and removes it
+// from the rows below), so each entry sees the same operations in the same
+// order as column-by-column substitution; the upper triangle is zeroed
+__global__ void __launch_bounds__(kLeafThreads)
+    k_trinv_leaf(const double* __restrict__ L, int64_t ldl, int n, double* X, int64_t ldx) {
+  extern __shared__ double leaf_sm[];
+  double* xs = leaf_sm;          // n x n, row-major
+  double* lc = leaf_sm + n * n;  // kLeafCols staged columns of L
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * n; e += nt) xs[e] = (e / n == e % n) ? 1.0 : 0.0;
+  for (int k0 = 0; k0 < n; k0 += kLeafCols) {
+    const int kc = min(kLeafCols, n - k0);
+    __syncthreads();
+    for (int e = tid; e < kc * n; e += nt) {
+      const int c = e / n, i = e - c * n;
+      lc[e] = i >= k0 + c ? L[i + (int64_t)(k0 + c) * ldl] : 0.0;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kc; ++kk) {
+      const int k = k0 + kk;
+      const double* lk = lc + kk * n;
+      for (int c = tid; c <= k; c += nt) xs[k * n + c] /= lk[k];
+      __syncthreads();
+      const int rows = n - k - 1, cols = k + 1;
+      for (int e = tid; e < rows * cols; e += nt) {
+        const int i = k + 1 + e / cols, c = e % cols;
+        xs[i * n + c] -= lk[i] * xs[k * n + c];
+      }
+      __syncthreads();
+    }
   }
+  for (int e = tid; e < n * n; e += nt) {
+    const int c = e / n, i = e - c * n;
+    X[i + (int64_t)c * ldx] = c <= i ? xs[i * n + c] : 0.0;
+  }
+}
+
+// Cholesky of the n x n diagonal block at A (lda) in place (lower triangle),
+// right-looking, in the operation order of k_potrf_diag; a non-positive or
+// non-finite pivot records NOT_SPD (and continues with 1)
+__global__ void __launch_bounds__(kLeafThreads)
+    k_potrf_leaf(double* A, int64_t lda, int n, int* status) {
+  extern __shared__ double leaf_sm[];
+  __shared__ double piv;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * n; e += nt) {
+    const int j = e / n, i = e - j * n;
+    leaf_sm[e] = i >= j ? A[i + (int64_t)j * lda] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      double d = leaf_sm[k + k * n];
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicCAS(status, 0, ST_NOT_SPD);
+        d = 1.0;
+      }
+      piv = sqrt(d);
+      leaf_sm[k + k * n] = piv;
+    }
+    __syncthreads();
+    for (int i = k + 1 + tid; i < n; i += nt) leaf_sm[i + k * n] /= piv;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = k + 1 + e % m, j = k + 1 + e / m;
+      if (j <= i) leaf_sm[i + j * n] -= leaf_sm[i + k * n] * leaf_sm[j + k * n];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * n; e += nt) {
+    const int j = e / n, i = e - j * n;
+    if (i >= j) A[i + (int64_t)j * lda] = leaf_sm[e];
+  }
+}
+
+cudaError_t trinv_leaf(const double* L, int64_t ldl, int n, double* X, int64_t ldx,
+                       cudaStream_t st) {
+  static unsigned long long bits = 0;
+  const size_t smem = (size_t)(kLeafMax * kLeafMax + kLeafCols * kLeafMax) * sizeof(double);
+  cudaError_t e = smem_limit_once(&bits, (const void*)k_trinv_leaf, (int)smem);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  k_trinv_leaf<<<1, kLeafThreads, (size_t)(n * n + kLeafCols * n) * sizeof(double), st>>>(
+      L, ldl, n, X, ldx);
+  return cudaGetLastError();
+}
+
+cudaError_t potrf_leaf(double* A, int64_t lda, int n, int* status, cudaStream_t st) {
+  static unsigned long long bits = 0;
+  const size_t smem = (size_t)kLeafMax * kLeafMax * sizeof(double);
+  cudaError_t e = smem_limit_once(&bits, (const void*)k_potrf_leaf, (int)smem);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  k_potrf_leaf<<<1, kLeafThreads, (size_t)n * n * sizeof(double), st>>>(A, lda, n, status);
+  return cudaGetLastError();
 }
 
 cudaError_t copy_scaled(const double* A, int64_t lda, int m, int n, double* B, int64_t ldb,
@@ -846,10 +937,7 @@ cudaError_t gemm_tc(const EigGemm& g, const double* A, int64_t lda, int m, int k
 // X (ldx) = L^-1 for lower-triangular L (n x n, ldl); scratch: 2 n^2 doubles
 cudaError_t trinv_lower(const EigGemm& g, const double* L, int64_t ldl, int n, double* X,
                         int64_t ldx, double* scratch, cudaStream_t st) {
-  if (n <= 128) {
-    note_launch(), k_trinv_leaf<<<1, 128, 0, st>>>(L, ldl, n, X, ldx);
-    return cudaGetLastError();
-  }
+  if (n <= kLeafMax) return trinv_leaf(L, ldl, n, X, ldx, st);
   const int n1 = (n / 2 + 63) / 64 * 64, n2 = n - n1;
   cudaError_t e;
   if ((e = trinv_lower(g, L, ldl, n1, X, ldx, scratch, st)) != cudaSuccess) return e;
@@ -922,8 +1010,7 @@ cudaError_t backtransform_wy(const EigGemm& g, const double* Hv, double* X, int 
       return e;
     note_launch(), k_wy_tinv_t<<<(b * b + 255) / 256, 256, 0, st>>>(S, b, Lw);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    note_launch(), k_trinv_leaf<<<1, 128, 0, st>>>(Lw, b, b, TT, b);  // TT = T^T
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = trinv_leaf(Lw, b, b, TT, b, st)) != cudaSuccess) return e;  // TT = T^T
     if ((e = copy_scaled(TT, b, b, b, T, b, true, 1.0, st)) != cudaSuccess) return e;
     if ((e = tc_gemm_f64(Yt, b, b, nr, X + r0, n, n, W1, b, g.SA, g.SZ, g.esc, g.status, st)) !=
         cudaSuccess)
@@ -943,6 +1030,43 @@ cudaError_t backtransform_wy(const EigGemm& g, const double* Hv, double* X, int 
 
 // Whether the tensor-core mode runs for n: the GEMM's digit buffers must hold
 // six digits of an n x n operand (both factors) and its exponent tables.
+// Blocked Cholesky A = L L^T (tensor-core mode), panels of kLeafMax columns:
+// the diagonal block in shared memory (k_potrf_leaf); the panel below it
+// L21 = A21 L11^-T with the leaf inverse and a tensor-core GEMM; the trailing
+// matrix A22 -= L21 L21^T by a tensor-core GEMM and a subtraction.  The lower
+// triangle of A holds L on return (the strict upper triangle is left as it
+// was, except inside A22, where it is scratch).  big: (n - 128)^2 doubles;
+// small: 2 * 128^2 + 256 n doubles.
+cudaError_t cholesky_tc(const EigGemm& g, double* A, int n, int* status, double* big,
+                        double* small, cudaStream_t st) {
+  constexpr int nb = kLeafMax;
+  cudaError_t e;
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int jb = std::min(nb, n - j0), rem = n - j0 - jb;
+    double* A11 = A + j0 + (int64_t)j0 * n;
+    if ((e = potrf_leaf(A11, n, jb, status, st)) != cudaSuccess) return e;
+    if (rem == 0) break;
+    double* X11 = small;                       // L11^-1 (jb x jb)
+    double* Xt = X11 + nb * nb;                // L11^-T
+    double* P = Xt + nb * nb;                  // L21 (rem x jb)
+    double* Pt = P + (int64_t)rem * jb;        // L21^T (jb x rem)
+    double* A21 = A11 + jb;
+    double* A22 = A21 + (int64_t)jb * n;
+    if ((e = trinv_leaf(A11, n, jb, X11, jb, st)) != cudaSuccess) return e;
+    if ((e = copy_scaled(X11, jb, jb, jb, Xt, jb, true, 1.0, st)) != cudaSuccess) return e;
+    if ((e = gemm_tc(g, A21, n, rem, jb, Xt, P, rem, st)) != cudaSuccess) return e;
+    if ((e = copy_scaled(P, rem, rem, jb, A21, n, false, 1.0, st)) != cudaSuccess) return e;
+    if ((e = copy_scaled(P, rem, rem, jb, Pt, jb, true, 1.0, st)) != cudaSuccess) return e;
+    if ((e = tc_gemm_f64(P, rem, rem, jb, Pt, jb, rem, big, rem, g.SA, g.SZ, g.esc, g.status,
+                         st)) != cudaSuccess)
+      return e;
+    note_launch(), k_sub_block<<<(unsigned)(((int64_t)rem * rem + 255) / 256), 256, 0, st>>>(
+        A22, n, big, rem, rem, rem);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 bool tc_eig_fits(const EigGemm* g, int n) {
   if (!g || !g->SA || !g->SZ || !g->esc || n < kTcEigMin) return false;
   const size_t ldk = (size_t)(n + 7) / 8 * 8;
@@ -977,13 +1101,16 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
   int* st0 = w.status;
   int* st1 = w.status + 1;
   EK(cudaMemsetAsync(w.status, 0, 2 * sizeof(int), st));  // words 2, 3: GEMM / stencil waits
+  const bool tcm = tc_eig_fits(g, n) && w.X0 && w.X1;
   // 1. Ms = L L^T
   EK(cudaMemcpyAsync(w.W, Ms, nn * 8, cudaMemcpyDeviceToDevice, st));
-  EK(cholesky(w.W, n, st0, st));
+  if (tcm)
+    EK(cholesky_tc(*g, w.W, n, st0, w.X0, w.lu, st));
+  else
+    EK(cholesky(w.W, n, st0, st));
   EL(k_tril_copy<<<nb, 256, 0, st>>>(w.W, w.L, n));
   EL(k_transpose<<<tg, tb, 0, st>>>(w.L, w.V, n));  // V = L row-major (forward solves)
   // 2. A = sym(L^-1 (L^-1 Hs)^T)
-  const bool tcm = tc_eig_fits(g, n) && w.X0 && w.X1;
   if (tcm) {
     EK(trinv_lower(*g, w.L, n, n, w.X0, n, w.lu, st));           // X0 = L^-1
     EK(copy_scaled(w.X0, n, n, n, w.X1, n, true, 1.0, st));       // X1 = L^-T
@@ -1058,7 +1185,7 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
     double* G = w.lu + nn;
     EK(copy_scaled(VT, n, n, n, w.V, n, true, 1.0, st));            // V = VT^T
     EK(gemm_tc(*g, w.V, n, n, n, VT, G, n, st));                     // G = VT^T VT
-    EK(cholesky(G, n, st1, st));
+    EK(cholesky_tc(*g, G, n, st1, w.X0, w.lu + 2 * nn, st));
     EL(k_tril_copy<<<nb, 256, 0, st>>>(G, w.V, n));                  // V = R (lower)
     EK(trinv_lower(*g, w.V, n, n, w.X0, n, w.lu + 2 * nn, st));      // X0 = R^-1
     EK(copy_scaled(w.X0, n, n, n, G, n, true, 1.0, st));             // G = R^-T
