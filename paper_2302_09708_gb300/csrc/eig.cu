@@ -1141,7 +1141,8 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
     else
       per_sm = 0;  // the reflector would not fit in shared memory: per-step kernels
     if (coop && sms > 0 && per_sm > 0) {
-      int blocks = sms * std::min(per_sm, 2);
+      // one CTA per SM while the barrier dominates a step, two for large n
+      int blocks = sms * std::min(per_sm, n < 2048 ? 1 : 2);
       GridBar gb{reinterpret_cast<unsigned*>(w.status + 8), reinterpret_cast<unsigned*>(w.status + 9),
                  w.status + 4, wait_cycles()};
       EK(cudaMemsetAsync(w.status + 4, 0, sizeof(int), st));
