@@ -564,56 +564,60 @@ __device__ void tri_factor(const TriLU& F, const double* d, const double* e, dou
   F.pv(n - 1) = 0;
 }
 
-// Solve (T - sigma) x = b in place in column x (stride 1).
-__device__ void tri_solve(const TriLU& F, double* x) {
+// Solve (T - sigma) x = b in place in x (entry i at x[i sx]).
+__device__ void tri_solve(const TriLU& F, double* x, int64_t sx = 1) {
   const int n = F.n;
   for (int k = 0; k + 1 < n; ++k) {
     if (F.pv(k)) {
-      double t = x[k];
-      x[k] = x[k + 1];
-      x[k + 1] = t;
+      double t = x[k * sx];
+      x[k * sx] = x[(k + 1) * sx];
+      x[(k + 1) * sx] = t;
     }
-    x[k + 1] -= F.at(3, k) * x[k];
+    x[(k + 1) * sx] -= F.at(3, k) * x[k * sx];
   }
   for (int k = n - 1; k >= 0; --k) {
-    double s = x[k];
-    if (k + 1 < n) s -= F.at(1, k) * x[k + 1];
-    if (k + 2 < n) s -= F.at(2, k) * x[k + 2];
-    x[k] = s / F.at(0, k);
+    double s = x[k * sx];
+    if (k + 1 < n) s -= F.at(1, k) * x[(k + 1) * sx];
+    if (k + 2 < n) s -= F.at(2, k) * x[(k + 2) * sx];
+    x[k * sx] = s / F.at(0, k);
   }
 }
 
-__device__ void scale_maxabs(double* x, int n) {
+__device__ void scale_maxabs(double* x, int n, int64_t sx = 1) {
   double m = 0.0;
-  for (int i = 0; i < n; ++i) m = fmax(m, fabs(x[i]));
+  for (int i = 0; i < n; ++i) m = fmax(m, fabs(x[i * sx]));
   if (m > 0.0) {
     double inv = 1.0 / m;
-    for (int i = 0; i < n; ++i) x[i] *= inv;
+    for (int i = 0; i < n; ++i) x[i * sx] *= inv;
   }
 }
 
 constexpr int kInvIters = 3;
 
-// Thread per eigenvalue, singletons only: column j of V (column-major).
+// Thread per eigenvalue, singletons only: eigenvector j into the row-major
+// scratch Xr (entry i of vector j at Xr[i n + j], so that the threads of a
+// warp, which hold consecutive j, touch consecutive addresses); the caller
+// transposes Xr into the column-major V.
 __global__ void k_inviter_single(const double* __restrict__ d, const double* __restrict__ e,
                                  const double* __restrict__ lam, const double* __restrict__ scal,
                                  const int* __restrict__ clus, int n, double* lu, int* piv,
-                                 double* V) {
+                                 double* Xr) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n || clus[n + j] != 1) return;
   TriLU F{lu, piv, n, n, j};
   const double pivmin = fmax(2.2e-16 * scal[3], 1e-300);
   tri_factor(F, d, e, lam[j], pivmin);
-  double* x = V + (int64_t)j * n;
-  for (int i = 0; i < n; ++i) x[i] = start_value(0x5EEDull + j, i);
+  double* x = Xr + j;
+  const int64_t sx = n;
+  for (int i = 0; i < n; ++i) x[i * sx] = start_value(0x5EEDull + j, i);
   for (int it = 0; it < kInvIters; ++it) {
-    scale_maxabs(x, n);
-    tri_solve(F, x);
+    scale_maxabs(x, n, sx);
+    tri_solve(F, x, sx);
   }
   double s = 0.0;
-  for (int i = 0; i < n; ++i) s += x[i] * x[i];
+  for (int i = 0; i < n; ++i) s += x[i * sx] * x[i * sx];
   double inv = 1.0 / sqrt(s);
-  for (int i = 0; i < n; ++i) x[i] *= inv;
+  for (int i = 0; i < n; ++i) x[i * sx] *= inv;
 }
 
 // One CTA per cluster (launched for every j; only cluster starts of size > 1 work).
@@ -1178,8 +1182,11 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
   // 5. eigenvectors of T into W (column-major); factors in lu (4 n x n)
   EL(k_clusters<<<1, 32, 0, st>>>(lam, n, w.scal, w.clus));
   double* VT = w.W;
+  // (V is idle here: it holds the singletons' vectors row-major, then they
+  // are transposed into VT before the clusters are iterated there)
   EL(k_inviter_single<<<(n + 31) / 32, 32, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu,
-                                                    w.piv, VT));
+                                                    w.piv, w.V));
+  EL(k_transpose<<<tg, tb, 0, st>>>(w.V, VT, n));
   EL(k_inviter_cluster<<<n, 256, 0, st>>>(w.d, w.e, lam, w.scal, w.clus, n, w.lu, w.piv, VT));
   //    Cholesky-QR pass: G = VT^T VT = R R^T, Q = VT R^-T  (Q^T = R^-1 VT^T)
   if (tcm) {
