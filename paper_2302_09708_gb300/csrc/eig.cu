@@ -442,19 +442,21 @@ __device__ int sturm(const double* __restrict__ d, const double* __restrict__ e2
   return cnt;
 }
 
-// Eigenvalue j of the tridiagonal matrix by multisection: the 8 lanes of a
-// group evaluate Sturm counts at 8 interior points of [lo, hi] at once, and the
-// interval shrinks 9-fold per round (bisection's 2-fold per count, with 8 times
-// the parallelism for the latency-bound count recurrence).  Stops at the same
-// relative width as plain bisection: 2 eps max(|lo|, |hi|).  The whole-GPU
-// eigensolver takes this form: with Ns eigenvalues spread over all SMs the
-// count recurrence's latency, not the FP64 pipe, bounds the step.
-constexpr int kMsLanes = 8;
+// Eigenvalue j of the tridiagonal matrix by multisection: the L lanes of a
+// group evaluate Sturm counts at L interior points of [lo, hi] at once, and the
+// interval shrinks (L + 1)-fold per round (bisection's 2-fold per count, with
+// L times the parallelism for the latency-bound count recurrence).  Stops at
+// the same relative width as plain bisection: 2 eps max(|lo|, |hi|).  The
+// whole-GPU eigensolver takes this form: with few eigenvalues per SM the
+// count recurrence's latency bounds the step (L = 8); with many, the FP64
+// pipe does, and fewer counts per eigenvalue win (L = 4 from n = 2048).
+template <int L>
 __global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e2, int n,
                          const double* __restrict__ scal, double* __restrict__ lam) {
+  constexpr int kMsLanes = L;
   const int g = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kMsLanes);
   const int l = threadIdx.x % kMsLanes;
-  const unsigned gmask = 0xFFu << ((threadIdx.x & 31) & ~(kMsLanes - 1));
+  const unsigned gmask = ((1u << kMsLanes) - 1u) << ((threadIdx.x & 31) & ~(kMsLanes - 1));
   const int j = min(g, n - 1);  // surplus groups repeat the last eigenvalue, unwritten
   double lo = scal[0], hi = scal[1];
   const double pivmin = scal[2];
@@ -1178,7 +1180,10 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
   // 4. eigenvalues of T (ascending)
   double* e2 = w.tau + n;
   EL(k_gersh<<<1, 1024, 0, st>>>(w.d, w.e, n, e2, w.scal));
-  EL(k_bisect<<<(n * kMsLanes + 127) / 128, 128, 0, st>>>(w.d, e2, n, w.scal, lam));
+  if (n < 2048)
+    EL(k_bisect<8><<<(n * 8 + 127) / 128, 128, 0, st>>>(w.d, e2, n, w.scal, lam));
+  else
+    EL(k_bisect<4><<<(n * 4 + 127) / 128, 128, 0, st>>>(w.d, e2, n, w.scal, lam));
   // 5. eigenvectors of T into W (column-major); factors in lu (4 n x n)
   EL(k_clusters<<<1, 32, 0, st>>>(lam, n, w.scal, w.clus));
   double* VT = w.W;
