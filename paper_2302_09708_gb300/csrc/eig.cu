@@ -291,6 +291,8 @@ struct GridBar {
   long long cycles;  // bound of each barrier wait (SM clock cycles)
 };
 
+constexpr int kHouseThreads = 512;  // largest CTA (one per SM)
+
 // Returns false if the barrier timed out (in any block).
 __device__ bool grid_barrier(const GridBar& gb, unsigned nblocks, int* abort_sh) {
   __syncthreads();
@@ -319,7 +321,7 @@ __device__ bool grid_barrier(const GridBar& gb, unsigned nblocks, int* abort_sh)
   return *abort_sh == 0;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kHouseThreads)
     k_house_persistent(double* __restrict__ A, double* __restrict__ Hv, double* d, double* e,
                        double* __restrict__ p, int n, GridBar gb) {
   // every block forms the step's reflector itself, in shared memory (the
@@ -1138,17 +1140,22 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
     EK(cudaGetDevice(&dev));
     EK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     const int sms = sm_count();
+    // one CTA per SM (fewest arrivals per grid barrier): 256 threads while the
+    // barriers dominate a step (measured: Ns = 1300 78 ms, 88 ms with 512 or
+    // with two CTAs of 256 per SM), 512 once the rank-2 updates do (Ns = 4800:
+    // 895 ms, 926 ms with two CTAs of 256, 1036 with one)
+    const int hthreads = n < 2048 ? 256 : kHouseThreads;
     const size_t vbytes = (size_t)n * sizeof(double);
     if (vbytes > 48 * 1024)
       EK(cudaFuncSetAttribute(k_house_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)std::min<size_t>(vbytes, 200 * 1024)));
     if (vbytes <= 200 * 1024)
-      EK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_house_persistent, 256, vbytes));
+      EK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_house_persistent, hthreads,
+                                                       vbytes));
     else
       per_sm = 0;  // the reflector would not fit in shared memory: per-step kernels
     if (coop && sms > 0 && per_sm > 0) {
-      // one CTA per SM while the barrier dominates a step, two for large n
-      int blocks = sms * std::min(per_sm, n < 2048 ? 1 : 2);
+      int blocks = sms * std::min(per_sm, 1);
       GridBar gb{reinterpret_cast<unsigned*>(w.status + 8), reinterpret_cast<unsigned*>(w.status + 9),
                  w.status + 4, wait_cycles()};
       EK(cudaMemsetAsync(w.status + 4, 0, sizeof(int), st));
@@ -1161,7 +1168,7 @@ cudaError_t gen_eig(EigWork& w, const double* Hs, const double* Ms, int n, doubl
       note_launch();
       // a refused cooperative launch (e.g. not enough co-resident blocks)
       // falls back to the per-step kernels below
-      if (cudaLaunchCooperativeKernel((void*)k_house_persistent, dim3(blocks), dim3(256), args,
+      if (cudaLaunchCooperativeKernel((void*)k_house_persistent, dim3(blocks), dim3(hthreads), args,
                                       vbytes, st) == cudaSuccess)
         coop_done = true;
       else
