@@ -254,6 +254,11 @@ int ring_shape(sparc_context* c, const T* x, int64_t ldx, int ns, cudaStream_t s
 // coefficients of y in c->D (the next recurrence step's D) and sets
 // *next_done.  Without tiles (the double-FP32 stencils, the mixed form's FP64
 // Yt) the generic stencil adds the nonlocal term point by point.
+// Projector entries per grid point above which the FP64 H application in
+// double-FP32 arithmetic leaves the nonlocal term to the tiled pass instead of
+// adding it point by point (bulk of the benchmark: 1.7; the 10-deep slab: 9.7)
+constexpr double kDenseNonlocal = 4.0;
+
 template <typename T>
 int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T* prev,
           int64_t ldp, int ns, double shift, double s_h, double s_p, cudaStream_t st,
@@ -272,7 +277,29 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
   const bool split = !has_nl || tiles_usable<T>(c);
   const bool ring = split && !df && c->ring_enabled &&
                     ring_applicable<T>(c->grid, x, ldx, y, ldy, prev, ldp, veff);
-  if (df) {
+  if (df && split && has_nl && c->nl_density > kDenseNonlocal) {
+    // overlapping projectors (many entries per point): the double-FP32 ring
+    // without its pull-add, then the tiled FP64 nonlocal pass
+    if (!d_ready) CK(c, nl_coefficients<T>(nl, h3, x, ldx, ns, D, st, true));
+    Nonlocal<double> local = c->nl64;
+    local.kp = 0;
+    bool used = false;
+    CK(c, apply_h_ring_df(c->grid, c->lap, c->veff_df, local, nullptr, (const double*)x, ldx,
+                          (double*)y, ldy, (const double*)prev, ldp, ns, shift, s_h, s_p,
+                          c->eig.status + 3, st, &used));
+    if (used) {
+      const NlTiles<T>& t = tiles_of<T>(c);
+      T* part = want_next ? (T*)c->part : nullptr;
+      CK(c, nl_apply<T>(t, D, nl.kp, y, ldy, ns, s_h, part, st));
+      if (want_next) {
+        CK(c, nl_reduce<T>(t, part, ns, nl.kp, nl.gamma, h3, D, st));
+        if (next_done) *next_done = true;
+      }
+      return SPARC_OK;
+    }
+    // the ring does not fit: the split generic form below, D already
+    // projector-major
+  } else if (df) {
     // the double-FP32 ring reads D orbital-major; where it does not fit the
     // grid, the split form follows (projector-major D) or, without tiles, the
     // fused generic stencil
@@ -701,6 +728,7 @@ int create_impl(const sparc_grid* g, const double* veff, const sparc_nonlocal* n
     nent += (nl->supp_ptr[J + 1] - nl->supp_ptr[J]) * nl->nproj[J];
   }
   ARG(c, nent < (int64_t)1 << 31, "too many projector entries");
+  c->nl_density = (double)nent / (double)std::max<int64_t>(nd, 1);
   for (int64_t i = 0; i < nd; ++i) pull_ptr[i + 1] += pull_ptr[i];
   std::vector<int> pull_k(nent > 0 ? nent : 1);
   std::vector<double> pull_chi(nent > 0 ? nent : 1);

@@ -427,5 +427,6 @@ struct sparc_context {
   double* Y64 = nullptr;     // mixed handles: FP64 Yt = H Xt of a step (ld x ns_max)
   float2* veff_df = nullptr; // Veff as (hi, lo) FP32 pairs for the double-FP32 stencil
   bool df_stencil = false;   // FP64 H x in double-FP32 arithmetic (mixed Yt; reserved[0] bit 2)
+  double nl_density = 0.0;   // projector entries per grid point (pull table size / Nd)
   std::string err;
 };

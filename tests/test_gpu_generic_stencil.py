@@ -93,3 +93,30 @@ def test_step_ragged_slab_vs_oracle(precision):
         occ = rf > 1e-6
         assert np.max(np.abs(lam - rlam)[occ]) < 1e-6
     h.close()
+
+
+def test_dense_projectors_double_fp32_vs_oracle():
+    """FP64 blocks in double-FP32 arithmetic (options bit 2) on a system whose
+    projectors overlap many deep (more than four entries per grid point): the
+    ring runs without its point-by-point nonlocal add and the tiled FP64 pass
+    adds the nonlocal term (and, in the filter, the next degree's
+    coefficients).  H x within 1e-12 and the filter within 1e-11 of the
+    oracle, as the other double-FP32 parity tests."""
+    s = synth.random_system((32, 32, 40), 0.35, (0, 0, 1), 30, seed=72)
+    assert s.supp_ptr[-1] * 4 > 4 * s.nd  # > 4 projector entries per point
+    o = oracle.Oracle(s)
+    ns = 4
+    X = np.random.default_rng(4).standard_normal((ns, s.nd))
+    h = sparc.Handle(s, "fp64", ns_max=ns, options_flags=4)
+    Y = h.hpsi(torch.from_numpy(X).to(DEV)).cpu().numpy()
+    ref = o.hpsi(X)
+    assert np.max(np.abs(Y - ref)) / np.max(np.abs(ref)) < 1e-12
+    a0, b, *_ = o.lanczos(24, 0)
+    a = a0 + 0.1 * (b - a0)
+    Xd = torch.from_numpy(X).to(DEV)
+    h.cheb_filter(Xd, 8, a, b, a0)
+    got = Xd.cpu().numpy()
+    ref = o.cheb_filter(X, 8, a, b, a0)
+    for n in range(ns):
+        assert np.max(np.abs(got[n] - ref[n])) < 1e-11 * np.max(np.abs(ref[n]))
+    h.close()
