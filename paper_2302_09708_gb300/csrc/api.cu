@@ -358,11 +358,16 @@ int hstep(sparc_context* c, const T* x, int64_t ldx, T* y, int64_t ldy, const T*
     // the ring kernel declined after all: the generic local stencil follows
   }
   if (split) {
-    // local part only (slab stencil, or the tiled one on grids it does not
-    // fit); the tiled pass adds the nonlocal term
+    // local part only (slab stencil, in double-FP32 arithmetic where the
+    // handle asks for it, or the tiled one on grids it does not fit); the
+    // tiled pass adds the nonlocal term
     bool used = false;
-    CK(c, apply_h_local<T>(c->grid, c->lap, veff, x, ldx, y, ldy, prev, ldp, ns, shift, s_h, s_p,
-                           st, &used));
+    if (df)
+      CK(c, apply_h_local_df(c->grid, c->lap, c->veff_df, (const double*)x, ldx, (double*)y, ldy,
+                             (const double*)prev, ldp, ns, shift, s_h, s_p, st, &used));
+    if (!used)
+      CK(c, apply_h_local<T>(c->grid, c->lap, veff, x, ldx, y, ldy, prev, ldp, ns, shift, s_h,
+                             s_p, st, &used));
     if (!used) {
       Nonlocal<T> local = nl;
       local.kp = 0;

@@ -479,6 +479,34 @@ __global__ void k_bisect(const double* __restrict__ d, const double* __restrict_
   if (g < n && l == 0) lam[j] = 0.5 * (lo + hi);
 }
 
+// Eigenvalue j by multisection on the Sturm count in a group of L lanes (the
+// L lanes of the warp at (lane & ~(L - 1))): the interval shrinks (L + 1)-fold
+// per round.  Every lane of the group must call it with the same j; lane l of
+// the group returns the result.
+template <int L>
+__device__ double multisect_eig(const double* __restrict__ d, const double* __restrict__ e2,
+                                int n, const double* __restrict__ scal, int j) {
+  const int lane = threadIdx.x & 31;
+  const int l = lane & (L - 1);
+  const unsigned gmask = ((1u << L) - 1u) << (lane & ~(L - 1));
+  double lo = scal[0], hi = scal[1];
+  const double pivmin = scal[2];
+  for (int it = 0; it < 96; ++it) {
+    if (hi - lo <= 2.0 * 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
+    const double step = (hi - lo) / (L + 1);
+    const double x = lo + (l + 1) * step;
+    const bool above = sturm(d, e2, n, x, pivmin) > j;
+    const unsigned b = __ballot_sync(gmask, above) & gmask;
+    const int first = b ? __ffs(b) - 1 - (lane & ~(L - 1)) : L;
+    const double nlo = first == 0 ? lo : lo + first * step;
+    const double nhi = first == L ? hi : lo + (first + 1) * step;
+    if (!(nlo >= lo && nhi <= hi && nlo < nhi)) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  return 0.5 * (lo + hi);
+}
+
 // Eigenvalue j by plain bisection on the Sturm count: one count per halving,
 // the fewest counts per bit.  The batched eigensolver takes this form: there
 // one SM (or a few) holds all of a problem's eigenvalues, so the FP64 pipe,
@@ -1375,9 +1403,9 @@ __device__ double cta_sum(double v, double* red) {
   __syncthreads();
   if (lane == 0) red[wid] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-  return s;
+  // every warp sums the warps' partials by shuffles (the same order in each)
+  const double w = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+  return warp_sum_d(w);
 }
 
 __global__ void __launch_bounds__(kEbThreads, 1)
@@ -1444,12 +1472,20 @@ __global__ void __launch_bounds__(kEbThreads, 1)
       P.d[k] = col[k];
       P.e[k] = xn > 0.0 ? alpha : 0.0;
     }
-    for (int i = k + 1 + t.warp; i < n; i += t.nwarps) {  // p = A v, warp per row
-      const double* row = A + (int64_t)i * n;
-      double s2 = 0.0;
-      for (int j = k + 1 + t.lane; j < n; j += 32) s2 += row[j] * vsh[j];
-      s2 = warp_sum_d(s2);
-      if (t.lane == 0) p[i] = s2;
+    // p = A v, warp per row, four rows at a time (their loads overlap)
+    for (int i0 = k + 1 + 4 * t.warp; i0 < n; i0 += 4 * t.nwarps) {
+      double s4[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int j = k + 1 + t.lane; j < n; j += 32) {
+        const double vj = vsh[j];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (i0 + r < n) s4[r] += A[(int64_t)(i0 + r) * n + j] * vj;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const double v = warp_sum_d(s4[r]);
+        if (t.lane == 0 && i0 + r < n) p[i0 + r] = v;
+      }
     }
     team_sync();
     acc = 0.0;
@@ -1522,9 +1558,26 @@ __global__ void __launch_bounds__(kEbThreads, 1)
   }
   team_sync();
   {
-    // one thread per eigenvalue, dealt round-robin over the cluster's CTAs
-    for (int j = (int)(rank + csize * threadIdx.x); j < n; j += t.nthr)
-      P.lam[j] = bisect_eig(P.d, e2, n, P.scal, j);
+    // eigenvalues dealt round-robin over the cluster's CTAs, L lanes each:
+    // where a CTA holds few eigenvalues the Sturm recurrence's latency binds
+    // and multisection's fewer rounds win, where it holds many the FP64 pipe
+    // binds and bisection's fewer counts do
+    const int per_cta = (n + (int)csize - 1) / (int)csize;
+    const int L = per_cta > 96 ? 1 : per_cta > 48 ? 2 : 4;
+    const int groups = (int)blockDim.x / L;
+    for (int g0 = 0; g0 * (int)csize < n; g0 += groups) {
+      const int j = (int)rank + (int)csize * (g0 + (int)threadIdx.x / L);
+      if (j < n) {
+        double v;
+        if (L == 4)
+          v = multisect_eig<4>(P.d, e2, n, P.scal, j);
+        else if (L == 2)
+          v = multisect_eig<2>(P.d, e2, n, P.scal, j);
+        else
+          v = bisect_eig(P.d, e2, n, P.scal, j);
+        if ((threadIdx.x & (L - 1)) == 0) P.lam[j] = v;
+      }
+    }
   }
   team_sync();
   if (t.lead) {  // clusters of nearly equal eigenvalues (as k_clusters)

@@ -106,6 +106,13 @@ template <typename T>
 cudaError_t apply_h_local(const Grid& g, const LapCoef& lc, const T* veff, const T* x,
                           int64_t ldx, T* y, int64_t ldy, const T* prev, int64_t ldp, int ns,
                           double shift, double s_h, double s_p, cudaStream_t st, bool* used);
+// The same in double-FP32 arithmetic for FP64 blocks (stencil_df.cu), the
+// local part of the FP64 H application where the double-FP32 ring does not
+// fit the grid (veff_df: Veff as pairs).
+cudaError_t apply_h_local_df(const Grid& g, const LapCoef& lc, const float2* veff_df,
+                             const double* x, int64_t ldx, double* y, int64_t ldy,
+                             const double* prev, int64_t ldp, int ns, double shift, double s_h,
+                             double s_p, cudaStream_t st, bool* used);
 // TMA plane-ring form (stencil_tma.cu) of the local part only:
 // y = s_h ((-1/2 Lap + Veff - shift) x) + s_p prev; the nonlocal term follows
 // with nl_apply.  *used = false when the grid or the buffers do not fit it.

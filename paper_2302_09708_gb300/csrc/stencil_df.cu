@@ -528,4 +528,182 @@ cudaError_t apply_h_ring_df(const Grid& g, const LapCoef& lc, const float2* veff
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Generic local stencil in double-FP32 arithmetic, by y-slabs of whole rows,
+// for FP64 blocks on grids the ring does not fit (any nx >= R): the slab
+// structure of stencil.cu's k_apply_h_slab (register z queue, own rows and the
+// halo rows in shared memory with repeated ghost columns) with the per-point
+// operation order of k_apply_h_ring_df (neighbour sums in the error-free
+// accumulator, coefficient products by acc_fma, Veff, then the recurrence);
+// the nonlocal term follows with the tiled pass.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kSlabDfThreads = 256;
+constexpr int kSlabDfPpt = 2;  // points per thread
+
+struct SlabArgsDF {
+  const double* x;
+  int64_t ldx;
+  double* y;
+  int64_t ldy;
+  const double* prev;
+  int64_t ldp;
+  const float2* veff;  // Veff as pairs
+  int nx, ny, nz, bcx, bcy, bcz;
+  int by, bz;
+  df dms;  // diagonal - shift
+  df off[R + 1];
+  df s_h, s_p;
+};
+
+__global__ void __launch_bounds__(kSlabDfThreads, 2) k_apply_h_slab_df(const SlabArgsDF a) {
+  constexpr int PPT = kSlabDfPpt;
+  extern __shared__ __align__(16) uint8_t slabdf_raw[];
+  df* const s = reinterpret_cast<df*>(slabdf_raw);
+  const int W = a.nx + 2 * R;
+  const int n = blockIdx.y;
+  const int y0 = blockIdx.x * a.by;
+  const int byl = min(a.by, a.ny - y0);
+  const int npts = byl * a.nx;
+  const int z0 = blockIdx.z * a.bz, z1 = min(z0 + a.bz, a.nz);
+  const int64_t nxy = (int64_t)a.nx * a.ny;
+  const double* __restrict__ xn = a.x + (int64_t)n * a.ldx;
+  const bool perx = a.bcx == SPARC_PERIODIC;
+  for (int e = threadIdx.x; e < (a.by + 2 * R) * W; e += blockDim.x) s[e] = df{0.f, 0.f};
+
+  int pofs[PPT], sidx[PPT];
+  unsigned own = 0, dup_r = 0, dup_l = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int p = threadIdx.x + k * blockDim.x;
+    pofs[k] = 0;
+    sidx[k] = R * W + R;
+    if (p < npts) {
+      const int ry = p / a.nx, rx = p - ry * a.nx;
+      pofs[k] = (y0 + ry) * a.nx + rx;
+      sidx[k] = (ry + R) * W + rx + R;
+      own |= 1u << k;
+      if (perx && rx < R) dup_r |= 1u << k;
+      if (perx && rx >= a.nx - R) dup_l |= 1u << k;
+    }
+  }
+  auto wrap = [](int& c, int nn, int bc) {
+    if (c >= 0 && c < nn) return true;
+    if (bc == SPARC_DIRICHLET) return false;
+    c %= nn;
+    if (c < 0) c += nn;
+    return true;
+  };
+  df q[2 * R + 1][PPT];
+  auto load_q = [&](int zz, df(&d)[PPT]) {
+    const bool ok = wrap(zz, a.nz, a.bcz);
+    const double* __restrict__ pl = xn + (int64_t)zz * nxy;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+      d[k] = (ok && ((own >> k) & 1u)) ? d2df(__ldg(pl + pofs[k])) : df{0.f, 0.f};
+  };
+#pragma unroll
+  for (int j = 0; j < 2 * R + 1; ++j) load_q(z0 - R + j, q[j]);
+
+  for (int z = z0; z < z1; ++z) {
+    const int64_t gz = (int64_t)z * nxy;
+    float2 vf[PPT];
+    double pv[PPT];
+    df nq[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const bool o = (own >> k) & 1u;
+      vf[k] = o ? __ldg(a.veff + gz + pofs[k]) : make_float2(0.f, 0.f);
+      pv[k] = (o && a.prev) ? a.prev[(int64_t)n * a.ldp + gz + pofs[k]] : 0.0;
+    }
+    load_q(z + R + 1, nq);
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      if ((own >> k) & 1u) {
+        s[sidx[k]] = q[R][k];
+        if ((dup_r >> k) & 1u) s[sidx[k] + a.nx] = q[R][k];
+        if ((dup_l >> k) & 1u) s[sidx[k] - a.nx] = q[R][k];
+      }
+    }
+    const double* __restrict__ pl = xn + gz;
+    for (int e = threadIdx.x; e < 2 * R * a.nx; e += blockDim.x) {
+      const int hr = e / a.nx, hx = e - hr * a.nx;
+      const int srow = hr < R ? hr : byl + hr;
+      int gy = hr < R ? y0 - R + hr : y0 + byl + hr - R;
+      const bool ok = wrap(gy, a.ny, a.bcy);
+      const df v = ok ? d2df(__ldg(pl + (int64_t)gy * a.nx + hx)) : df{0.f, 0.f};
+      const int si = srow * W + hx + R;
+      s[si] = v;
+      if (perx && hx < R) s[si + a.nx] = v;
+      if (perx && hx >= a.nx - R) s[si - a.nx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      if ((own >> k) & 1u) {
+        const df* c = s + sidx[k];
+        const df c0 = mul(a.dms, q[R][k]);
+        acc_t acc = {c0.h, c0.l};
+#pragma unroll
+        for (int p = 1; p <= R; ++p) {
+          acc_t sm = {c[p * W].h, c[p * W].l};
+          acc_add(sm, c[-p * W]);
+          acc_add(sm, q[R + p][k]);
+          acc_add(sm, q[R - p][k]);
+          acc_add(sm, c[-p]);
+          acc_add(sm, c[p]);
+          acc_fma(acc, a.off[p], sm);
+        }
+        const df h = fma(df{vf[k].x, vf[k].y}, q[R][k], normalise(acc));
+        df o = mul(a.s_h, h);
+        if (a.prev) o = fma(a.s_p, d2df(pv[k]), o);
+        a.y[(int64_t)n * a.ldy + gz + pofs[k]] = __dadd_rn(widen(o.h), widen(o.l));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 2 * R; ++j)
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) q[j][k] = q[j + 1][k];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) q[2 * R][k] = nq[k];
+  }
+}
+
+}  // namespace
+
+cudaError_t apply_h_local_df(const Grid& g, const LapCoef& lc, const float2* veff_df,
+                             const double* x, int64_t ldx, double* y, int64_t ldy,
+                             const double* prev, int64_t ldp, int ns, double shift, double s_h,
+                             double s_p, cudaStream_t st, bool* used) {
+  *used = false;
+  const int maxpts = kSlabDfPpt * kSlabDfThreads;
+  if (!veff_df || g.nx < R || g.nx > maxpts || ns < 1 || ns > 65535) return cudaSuccess;
+  int by = std::min(g.ny, maxpts / g.nx);
+  const int nslab = (g.ny + by - 1) / by;
+  by = (g.ny + nslab - 1) / nslab;
+  const int threads = ((by * g.nx + kSlabDfPpt - 1) / kSlabDfPpt + 31) / 32 * 32;
+  const size_t smem = (size_t)(by + 2 * R) * (g.nx + 2 * R) * sizeof(df);
+  if (smem > 48 * 1024) return cudaSuccess;
+  const int64_t xy_ctas = (int64_t)nslab * ns;
+  int nzc = (int)std::min<int64_t>((8 * sm_count() + xy_ctas - 1) / xy_ctas, 1 << 20);
+  nzc = std::max(1, std::min(nzc, std::max(1, g.nz / (2 * R))));
+  const int bz = (g.nz + nzc - 1) / nzc;
+  nzc = (g.nz + bz - 1) / bz;
+  SlabArgsDF a;
+  a.x = x; a.ldx = ldx; a.y = y; a.ldy = ldy; a.prev = prev; a.ldp = ldp; a.veff = veff_df;
+  a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.bcx = g.bc[0]; a.bcy = g.bc[1]; a.bcz = g.bc[2];
+  a.by = by;
+  a.bz = bz;
+  a.dms = host_df(lc.diag - shift);
+  for (int p = 0; p <= R; ++p) a.off[p] = host_df(lc.off[p]);
+  a.s_h = host_df(s_h);
+  a.s_p = host_df(s_p);
+  note_launch();
+  k_apply_h_slab_df<<<dim3(nslab, ns, nzc), threads, smem, st>>>(a);
+  *used = true;
+  return cudaGetLastError();
+}
+
 }  // namespace sparc
