@@ -1314,12 +1314,22 @@ __device__ __forceinline__ void team_sync() {
 // is read and updated in place, right-looking, one column per step).  Writes
 // the factor column-major into Lc and row-major into Lr (lower entries only).
 // Returns false, on every thread alike, at a non-positive or non-finite pivot.
-__device__ bool team_cholesky(double* S, double* Lc, double* Lr, int n, const Team& t) {
+// The pivot's square root and reciprocal are formed once per CTA (thread 0)
+// and shared through bc[0..1]: every warp computing them would cost the FP64
+// pipe as much as distinct values.
+__device__ bool team_cholesky(double* S, double* Lc, double* Lr, int n, const Team& t,
+                              double* bc) {
   for (int k = 0; k < n; ++k) {
     const double akk = S[k + (int64_t)k * n];
     if (!(akk > 0.0) || !isfinite(akk)) return false;
-    const double s = sqrt(akk);
-    const double linv = 1.0 / s;
+    if (threadIdx.x == 0) {
+      const double r = sqrt(akk);
+      bc[0] = r;
+      bc[1] = 1.0 / r;
+    }
+    __syncthreads();
+    const double s = bc[0];
+    const double linv = bc[1];
     for (int i = k + t.tid; i < n; i += t.nthr) {
       const double l = i == k ? s : S[i + (int64_t)k * n] * linv;
       Lc[i + (int64_t)k * n] = l;
@@ -1436,7 +1446,7 @@ __global__ void __launch_bounds__(kEbThreads, 1)
   // 1. Ms = L L^T (A <- Ms; factor into L column-major and V row-major)
   for (int64_t q = t.tid; q < nn; q += t.nthr) A[q] = P.Ms[q];
   team_sync();
-  if (!team_cholesky(A, L, V, n, t)) {
+  if (!team_cholesky(A, L, V, n, t, red + 16)) {
     if (t.lead) atomicCAS(P.status, 0, ST_NOT_SPD);
     return;
   }
@@ -1456,7 +1466,10 @@ __global__ void __launch_bounds__(kEbThreads, 1)
     const double* col = A + (int64_t)k * n;
     double acc = 0.0;
     for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) acc += col[i] * col[i];
-    const double xn = sqrt(cta_sum(acc, red));
+    const double xx = cta_sum(acc, red);  // (every warp holds the same sum)
+    if (threadIdx.x == 0) red[16] = sqrt(xx);
+    __syncthreads();
+    const double xn = red[16];
     const double x0 = col[k + 1];
     const double alpha = x0 >= 0.0 ? -xn : xn;
     double vn2 = 0.0;
@@ -1464,7 +1477,10 @@ __global__ void __launch_bounds__(kEbThreads, 1)
       const double v = col[i] - (i == k + 1 ? alpha : 0.0);
       vn2 += v * v;
     }
-    const double vn = sqrt(cta_sum(vn2, red));
+    const double vv = cta_sum(vn2, red);
+    if (threadIdx.x == 0) red[17] = sqrt(vv);
+    __syncthreads();
+    const double vn = red[17];
     for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
       vsh[i] = (xn > 0.0 && vn > 0.0) ? (col[i] - (i == k + 1 ? alpha : 0.0)) / vn : 0.0;
     __syncthreads();
@@ -1672,7 +1688,7 @@ __global__ void __launch_bounds__(kEbThreads, 1)
     __syncwarp();
   }
   team_sync();
-  if (!team_cholesky(G, lu, lu + 2 * nn, n, t)) {
+  if (!team_cholesky(G, lu, lu + 2 * nn, n, t, red + 16)) {
     if (t.lead) atomicCAS(P.status + 1, 0, ST_NUMERIC);
     return;
   }
