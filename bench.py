@@ -32,9 +32,14 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per orbital of one ring-stencil launch of a filter
 # degree on the 96^3 bulk grid, from ncu captures at Ns = 64 scaled by orbitals
 # (every orbital is one independent pass over the grid): FP64 (1006.27 +
-# 417.48) MB / 64, FP32 (491.28 + 189.31) MB / 64 (the ring-kernel captures)
+# 417.48) MB / 64, FP32 (491.28 + 189.31) MB / 64 (the ring-kernel captures),
+# each of the thread shape named beside it (the roofline's traffic is null
+# when the tuner picked another shape)
 RING64_DRAM_BYTES_PER_ORBITAL = (1006.271e6 + 417.475e6) / 64
+RING64_CAPTURED_SHAPE = 0
 RING32_DRAM_BYTES_PER_ORBITAL = (491.276e6 + 189.307e6) / 64
+RING32_CAPTURED_SHAPE = 0
+RING_CAPTURED_ND = 96 ** 3  # the grid of both captures
 # FLOP per point and orbital of one H application (finite-difference stencil,
 # Veff and recurrence), the count the roofline of the FP64 stencil uses
 STENCIL_FLOP_PER_POINT = 84
@@ -344,7 +349,7 @@ def main():
     # launch by the library's events), against the FP64 pipe (FP64 arithmetic)
     # or HBM (FP32)
     pk = peaks()
-    roof = stencil_roofline(stage, nd, ns, prec, pk, dev)
+    roof = stencil_roofline(stage, nd, ns, prec, pk, dev, tuning)
     roof["filter_stage_share"] = st_ms["filter_ms"] / st_ms["total_ms"]
 
     clocks = clk.summary()
@@ -462,21 +467,28 @@ def fp64_peak_tflops(pk, dev):
         "(FP64 pipe; no measured FP64 peak exists)")
 
 
-def stencil_roofline(stage, nd, ns, prec, pk, dev):
+def stencil_roofline(stage, nd, ns, prec, pk, dev, tuning=None):
     """Roofline object of the ring stencil: achieved = algorithmic work of one
     launch / its average duration (library events over the timed steps).  FP64:
     84 Nd Ns FLOP per launch against the FP64 pipe; FP32: 12 Nd Ns bytes (read
-    Y_i and Y_(i-1), write Y_(i+1)) against measured HBM."""
+    Y_i and Y_(i-1), write Y_(i+1)) against measured HBM.  traffic: the ncu
+    DRAM bytes per orbital x Ns, only for the grid and thread shape they were
+    captured on (else null)."""
     runs = [s for s in stage if s.get("stencil_launches", 0) > 0]
     if not runs:
         return {"kernel": "generic stencil (no ring launches)", "achieved": None, "frac": None}
     per_launch_ms = statistics.median(s["stencil_ms"] / s["stencil_launches"] for s in runs)
     nl_ms = statistics.median(s["nonlocal_ms"] / s["stencil_launches"] for s in runs)
+    shape = tuning.get("shape") if tuning else None
+
+    def captured(per_orbital, shape_captured):
+        return bool(per_orbital) and nd == RING_CAPTURED_ND and shape == shape_captured
     if prec == "fp64":
         flop = STENCIL_FLOP_PER_POINT * nd * ns
         peak, src = fp64_peak_tflops(pk, dev)
         ach = flop / (per_launch_ms / 1e3) / 1e12
-        traffic = RING64_DRAM_BYTES_PER_ORBITAL * ns if RING64_DRAM_BYTES_PER_ORBITAL else None
+        traffic = (RING64_DRAM_BYTES_PER_ORBITAL * ns
+                   if captured(RING64_DRAM_BYTES_PER_ORBITAL, RING64_CAPTURED_SHAPE) else None)
         return {"kernel": "k_apply_h_ring<double> (local stencil, one filter degree)",
                 "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "peak_source": src, "traffic": traffic,
@@ -486,7 +498,8 @@ def stencil_roofline(stage, nd, ns, prec, pk, dev):
     byts = 12 * nd * ns
     peak = pk.get("hbm_gbs", 6688.8)
     ach = byts / (per_launch_ms / 1e3) / 1e9
-    traffic = RING32_DRAM_BYTES_PER_ORBITAL * ns if RING32_DRAM_BYTES_PER_ORBITAL else None
+    traffic = (RING32_DRAM_BYTES_PER_ORBITAL * ns
+               if captured(RING32_DRAM_BYTES_PER_ORBITAL, RING32_CAPTURED_SHAPE) else None)
     return {"kernel": "k_apply_h_ring<float> (local stencil, one filter degree)",
             "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "traffic": traffic,
@@ -576,7 +589,8 @@ def run_variants(system, X0, ns, m, args, dev, stream, h64):
             filt_bytes = (2 + 3 * (m - 1)) * system.nd * ns * es
             out[key] = {"what": what, "ms_per_step": t * 1e3, "stage_ms": st,
                         "filter_GBps": filt_bytes / (st["filter_ms"] / 1e3) / 1e9,
-                        "roofline": stencil_roofline(stage, system.nd, ns, prec, peaks(), dev),
+                        "roofline": stencil_roofline(stage, system.nd, ns, prec, peaks(), dev,
+                                                     hv.tuning()),
                         "stencil_tuning": hv.tuning(),
                         "ritz_err_vs_fp64_gpu_per_step": errs, "ritz_err_occupied": err_occ,
                         "density_l1_per_electron_vs_fp64_gpu": dens_l1}
@@ -624,7 +638,8 @@ def run_slab(args, dev, stream):
     filt_bytes = (2 + 3 * (m - 1)) * system.nd * ns * 4
     out = {"workload": cfg["name"], "ms_per_step": t, "steps": steps, "stage_ms": st,
            "filter_GBps": filt_bytes / (st["filter_ms"] / 1e3) / 1e9,
-           "roofline": stencil_roofline(stage, system.nd, ns, "mixed", peaks(), dev),
+           "roofline": stencil_roofline(stage, system.nd, ns, "mixed", peaks(), dev,
+                                        h.tuning()),
            "stencil_tuning": h.tuning(), "setup_s": setup_s,
            "start": "seeded torch.randn on the device / sqrt(Nd)"}
     h.close()

@@ -119,7 +119,9 @@ typedef struct {
                     the shapes that fit the grid on the first filter or H x call
                     with a given ns (that call waits for its stream); k >= 1 =
                     shape k - 1 always (see sparc_get_tuning).  The shapes give
-                    bit-identical results.                                     */
+                    bit-identical results.  Shapes (planes per step, threads):
+                    FP64 blocks 0 (2, 384), 1 (1, 576); FP32 blocks 0 (4, 384),
+                    1 (1, 576), 2 (2, 512).                                    */
   int reserved;  /* must be 0                                                  */
   int64_t timeout_cycles; /* bound of every device-side wait, in SM clock cycles
                     (0 = 4e9, about two seconds); a wait that runs out stops its

@@ -179,9 +179,11 @@ bool tiles_usable(const sparc_context* c) {
 // Thread shape of the ring stencil for ns orbitals of type T: the fixed one,
 // one tuned before for this ns, or the fastest of the shapes that fit the grid
 // timed now: one warm-up and two timed launches each, reading the call's own
-// input block x (ldx) and writing a transient buffer, so no live data is
-// touched.  The shapes give bit-identical results.  Tuning waits for the
-// stream; during a stream capture the first shape is used untimed.
+// input block x (ldx) both as the operand and as the recurrence's previous
+// block (as every filter degree after the first reads one) and writing a
+// transient buffer, so no live data is touched.  The shapes give bit-identical
+// results.  Tuning waits for the stream; during a stream capture the first
+// shape is used untimed.
 template <typename T>
 int ring_shape(sparc_context* c, const T* x, int64_t ldx, int ns, cudaStream_t st, int* shape) {
   *shape = 0;
@@ -217,7 +219,7 @@ int ring_shape(sparc_context* c, const T* x, int64_t ldx, int ns, cudaStream_t s
     for (int rep = 0; rep < 3; ++rep) {
       bool used = false;
       CK(c, cudaEventRecord(c->ev_tune[0], st));
-      CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, ldx, y, c->ld, nullptr, 0, ns, 0.0, 1.0,
+      CK(c, apply_h_ring<T>(c->grid, c->lap, veff, x, ldx, y, c->ld, x, ldx, ns, 0.0, 1.0,
                             0.0, c->wait_cycles, c->eig.status + 3, st, s_, false, &used));
       CK(c, cudaEventRecord(c->ev_tune[1], st));
       CK(c, cudaEventSynchronize(c->ev_tune[1]));

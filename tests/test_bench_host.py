@@ -49,3 +49,23 @@ def test_measured_peaks_file_is_read():
         assert pk.get("hbm_gbs", 0) > 1000 and pk.get("bf16_tflops", 0) > 100
     else:
         assert pk == {}
+
+
+def test_stencil_roofline_traffic_only_for_the_captured_grid_and_shape():
+    """The ncu DRAM bytes are reported only for the grid and thread shape they
+    were captured on; achieved = 12 Nd Ns bytes / the median launch time."""
+    nd, ns = bench.RING_CAPTURED_ND, 1300
+    stage = [{"stencil_launches": 20, "stencil_ms": 20 * 5.0, "nonlocal_ms": 20 * 1.0}]
+    pk = {"hbm_gbs": 6000.0}
+    r = bench.stencil_roofline(stage, nd, ns, "mixed", pk, None,
+                               {"shape": bench.RING32_CAPTURED_SHAPE})
+    assert abs(r["achieved"] - 12 * nd * ns / 5e-3 / 1e9) < 1e-6 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12
+    assert abs(r["traffic"] - bench.RING32_DRAM_BYTES_PER_ORBITAL * ns) < 1.0
+    other = bench.stencil_roofline(stage, nd, ns, "mixed", pk, None,
+                                   {"shape": bench.RING32_CAPTURED_SHAPE + 3})
+    assert other["traffic"] is None and other["achieved"] == r["achieved"]
+    slab = bench.stencil_roofline(stage, 64 * 64 * 160, ns, "mixed", pk, None,
+                                  {"shape": bench.RING32_CAPTURED_SHAPE})
+    assert slab["traffic"] is None
+    assert bench.stencil_roofline(stage, nd, ns, "mixed", pk, None)["traffic"] is None
