@@ -162,6 +162,8 @@ PY_MUTANTS = [
     ("occupations_bisection_direction", oracle, "if c < ne:", "if c > ne:", [OCC, OCC_CLOSED]),
     ("occupations_fermi_sign", oracle, "return 1.0 / (1.0 + np.exp(t)), mu",
      "return 1.0 / (1.0 + np.exp(-t)), mu", [OCC, OCC_CLOSED]),
+    ("density_grid_power", oracle, 'return 2.0 * np.einsum("n,ni->i", f, X * X) / h ** 3',
+     'return 2.0 * np.einsum("n,ni->i", f, X * X) / h ** 2', [OCC]),
     ("density_spin_factor", oracle, 'return 2.0 * np.einsum("n,ni->i", f, X * X) / h ** 3',
      'return np.einsum("n,ni->i", f, X * X) / h ** 3', [OCC]),
     ("project_result_transposed", oracle, "return Hs.T.copy(), Ms.T.copy()",
@@ -189,6 +191,18 @@ PY_MUTANTS = [
      "return theta[0], theta[-1], alpha, beta, theta[-1]", [K_LANCZOS]),
     ("k_filter_sigma_recurrence_sign", kpoint, "sigma_new = 1.0 / (tau - sigma)",
      "sigma_new = 1.0 / (tau + sigma)", [K_FILTER]),
+    ("k_laplacian_sign", kpoint, "Y += (-0.5 / self.h ** 2) * lap",
+     "Y += (0.5 / self.h ** 2) * lap", [K_PLANE]),
+    ("k_veff_dropped", kpoint,
+     "Y = Y.reshape(ns, self.nd) + self.system.veff[None, :] * X[:, : self.nd]",
+     "Y = Y.reshape(ns, self.nd)", [K_DENSE]),
+    ("k_dirichlet_ghost_read", kpoint, "f = (q == 0).astype(np.float64)", "f = np.ones(n)",
+     [K_DENSE_D]),
+    ("k_lanczos_three_term_dropped", kpoint, "w = self.hpsi(v)[0] - bprev * vp",
+     "w = self.hpsi(v)[0]", [K_LANCZOS]),
+    ("k_rotation_transposed", kpoint,
+     "return np.asarray(Z).T @ np.asarray(Xt, dtype=np.complex128)",
+     "return np.asarray(Z) @ np.asarray(Xt, dtype=np.complex128)", [K_STEP]),
     ("gradient_weight_sign", forces, "w[p] = (-1) ** (p + 1) * factorial(n) ** 2",
      "w[p] = (-1) ** p * factorial(n) ** 2", [F_WEIGHTS]),
     ("gradient_dirichlet_ghost_read", forces, "mask = ((j >= 0) & (j < n)).astype(np.float64)",
@@ -200,6 +214,8 @@ PY_MUTANTS = [
     ("force_sign", forces, "F[J, d] = -4.0 * np.sum(", "F[J, d] = 4.0 * np.sum(", [F_DENSE]),
     ("force_gradient_axis", forces, "g = h3 * (grads[d][:, idx] @ chi)",
      "g = h3 * (grads[0][:, idx] @ chi)", [F_DENSE]),
+    ("force_coefficient_from_gradient", forces, "c = h3 * (X[:, idx] @ chi)",
+     "c = h3 * (grads[0][:, idx] @ chi)", [F_DENSE]),
 ]
 
 
