@@ -260,3 +260,40 @@ def test_lanczos_full_krylov_gives_exact_extremes():
     assert abs(a0 - ev[0]) < 1e-8 * np.max(np.abs(ev))
     assert abs(tmax - ev[-1]) < 1e-8 * np.max(np.abs(ev))
     assert b >= ev[-1] - 1e-8
+
+
+def test_chefsi_step_depends_only_on_the_span_of_the_start():
+    """The filter is linear and Rayleigh-Ritz sees only the span of its input,
+    so a start block X0 and X0 rotated by any orthogonal Q (any basis of the
+    same span) give the same Ritz values and the same subspace."""
+    s = synth.random_system((13, 14, 13), 0.5, (0, 1, 0), 3, seed=41)
+    o = oracle.Oracle(s)
+    a0, b, a = _cold_bounds(o)
+    ns = 9
+    X0 = synth.random_orbitals(s.nd, ns, seed=12)
+    Q, _ = np.linalg.qr(np.random.default_rng(13).standard_normal((ns, ns)))
+    X1, lam1 = o.chefsi_step(X0, 10, a, b, a0)
+    X2, lam2 = o.chefsi_step(Q.T @ X0, 10, a, b, a0)
+    np.testing.assert_allclose(lam2, lam1, atol=1e-10)
+    # the same span: the projector onto one basis reproduces the other
+    P = X1.T @ X1
+    assert np.linalg.norm(X2.T - P @ X2.T) < 1e-8
+
+
+def test_chefsi_step_is_shift_covariant():
+    """Veff + sigma with every bound moved by sigma leaves (H - c)/e unchanged,
+    so the filtered block is the same and the Ritz values move by exactly
+    sigma (to rounding)."""
+    import dataclasses
+    s = synth.random_system((13, 13, 14), 0.5, (0, 0, 1), 2, seed=43)
+    sigma = 0.37
+    t = dataclasses.replace(s, veff=s.veff + sigma)
+    o, ot = oracle.Oracle(s), oracle.Oracle(t)
+    a0, b, a = _cold_bounds(o)
+    X0 = synth.random_orbitals(s.nd, 8, seed=14)
+    X1, lam1 = o.chefsi_step(X0, 12, a, b, a0)
+    X2, lam2 = ot.chefsi_step(X0, 12, a + sigma, b + sigma, a0 + sigma)
+    np.testing.assert_allclose(lam2 - sigma, lam1, atol=1e-10)
+    Xf1 = o.cheb_filter(X0, 12, a, b, a0)
+    Xf2 = ot.cheb_filter(X0, 12, a + sigma, b + sigma, a0 + sigma)
+    assert np.max(np.abs(Xf2 - Xf1)) < 1e-10 * np.max(np.abs(Xf1))
