@@ -215,3 +215,27 @@ def test_force_is_minus_energy_derivative(monkeypatch):
         e[d] = delta
         Ffd[d] = -(energy(system_at(R0 + e)) - energy(system_at(R0 - e))) / (2 * delta)
     assert np.max(np.abs(F - Ffd)) < 2e-8 * np.max(np.abs(F)), (F, Ffd)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_forces_covariant_under_a_lattice_translation(axis):
+    """Periodic grid: moving every atom by one grid spacing along an axis and
+    rolling the orbitals by one point the same way leaves every force
+    unchanged (the projector tables, Veff and the gradient stencil all move
+    with the lattice)."""
+    shape, h = (13, 14, 12), 0.5
+    L = np.array(shape) * h
+    rng = np.random.default_rng(21)
+    pos = rng.uniform(0.1, 0.9, size=(3, 3)) * (L - h)
+    step = np.zeros(3)
+    step[axis] = h
+    s = synth.random_system(shape, h, (P, P, P), 3, seed=17, positions=pos)
+    t = synth.random_system(shape, h, (P, P, P), 3, seed=17, positions=pos + step)
+    ns = 4
+    X = rng.standard_normal((ns, s.nd))
+    Xt = np.roll(X.reshape(ns, shape[2], shape[1], shape[0]), 1, axis=3 - axis).reshape(ns, -1)
+    f = np.array([1.0, 0.8, 0.5, 0.1])
+    F = forces.nonlocal_forces(s, X, f)
+    Ft = forces.nonlocal_forces(t, Xt, f)
+    assert np.max(np.abs(F)) > 1e-6
+    assert np.max(np.abs(Ft - F)) < 1e-12 * np.max(np.abs(F))
