@@ -307,3 +307,19 @@ def test_chefsi_steps_converge_to_brute_force():
         a = lam[-1]
     # the lowest states converge fastest; the top ones of the block lag
     assert np.max(np.abs(lam[:8] - ev[:8])) < 1e-8
+
+
+def test_complex_step_depends_only_on_the_span_of_the_start():
+    """As in the real step: a start block and the same block rotated by any
+    unitary U give the same Ritz values and the same subspace."""
+    s, ko, a0, b = _step_setup(seed=23)
+    ns, m = 8, 8
+    a = a0 + 0.1 * (b - a0)
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((ns, s.nd)) + 1j * rng.standard_normal((ns, s.nd))
+    U, _ = np.linalg.qr(rng.standard_normal((ns, ns)) + 1j * rng.standard_normal((ns, ns)))
+    X1, lam1 = ko.chefsi_step(X, m, a, b, a0)
+    X2, lam2 = ko.chefsi_step(U.T @ X, m, a, b, a0)
+    assert np.max(np.abs(lam2 - lam1)) < 1e-10 * np.max(np.abs(lam1))
+    P = X1.T @ X1.conj()  # projector onto span(X1) (columns X1.T)
+    assert np.linalg.norm(X2.T - P @ X2.T) < 1e-8
